@@ -1,0 +1,185 @@
+/*
+ * bats.h -- C ABI of libbats: one explicit second-order stage of the
+ * ideal-MHD finite-volume update over all blocks of a 2:1 block-adaptive
+ * grid (8^3-cell blocks, 2 ghost layers) on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: arXiv 2501.06717 (BATSRUS GPU), Section 3 and Algorithms 1-2 (the
+ * solver loop: face values, face fluxes, sources, update, ghost-cell
+ * exchange), Section 4.1-4.2 (ghost layers; copy, restriction and
+ * prolongation at resolution changes), Section 5.1 Eqs. 1-5 (ideal MHD with
+ * the Powell 8-wave source terms, mu0 = 1), Section 5.2 (two-stage
+ * second-order time stepping, inner body, inflow and floating boundaries).
+ *
+ * Conventions used by every entry point:
+ *  - Status: 0 (BATS_OK) on success, a negative BATS_ERR_* code on failure;
+ *    bats_last_error() then describes the failure.  No entry point aborts.
+ *  - A state array is double [8][n_blocks][8][8][8] (variable, block, k, j, i;
+ *    i fastest) of the conservative variables (rho, rho ux, rho uy, rho uz,
+ *    B1x, B1y, B1z, e1), with B = B0 + B1 and e1 = p/(gamma-1) + rho u^2/2 +
+ *    B1^2/2.  Block order is the leaf order given to bats_create.
+ *  - Pointers to caller memory may be host or device (CUDA) pointers; the
+ *    library detects which and copies.  The caller keeps ownership of every
+ *    buffer it passes; the library owns the handle and all device memory it
+ *    allocates, released by bats_destroy.
+ *  - All device work is enqueued on the stream given to bats_create.  Entry
+ *    points that return data to the host synchronise that stream.
+ */
+#ifndef BATS_H
+#define BATS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define BATS_OK 0
+#define BATS_ERR_INVALID_ARG (-1)     /* bad pointer, size, index or descriptor   */
+#define BATS_ERR_UNBALANCED_TREE (-2) /* leaves overlap, leave gaps, or break 2:1 */
+#define BATS_ERR_OUT_OF_MEMORY (-3)   /* device or host allocation failed         */
+#define BATS_ERR_CUDA (-4)            /* a CUDA runtime call or launch failed      */
+#define BATS_ERR_NONPHYSICAL (-5)     /* rho <= 0, p <= 0 or NaN after an update   */
+#define BATS_ERR_TIMEOUT (-6)         /* a bounded device wait ran out             */
+#define BATS_ERR_NOT_TRAINED (-7)     /* learned form requested without weights    */
+
+/* ---- enumerations ------------------------------------------------------ */
+enum { BATS_BC_PERIODIC = 0, BATS_BC_OUTFLOW = 1, BATS_BC_INFLOW = 2 };
+enum { BATS_LIM_MINMOD = 0, BATS_LIM_MC = 1 };
+enum { BATS_RK_MIDPOINT = 0, BATS_RK_SSP2 = 1 };
+enum { BATS_FP64 = 0, BATS_MIXED = 1 };
+enum { BATS_B0_NONE = 0, BATS_B0_UNIFORM = 1, BATS_B0_DIPOLE = 2, BATS_B0_LINEAR = 3 };
+enum { BATS_PHASE_STAGE = 0, BATS_PHASE_DT = 1, BATS_PHASE_TOTAL = 2, BATS_NUM_PHASES = 3 };
+
+typedef struct bats bats_t;
+
+/* One grid (Section 2: a tree of equal-size blocks; 8^3 cells per block).
+ *  lo, hi     domain corners; the domain is root[a] * 8 * 2^level cells per axis
+ *  root       root blocks per axis (level 0)
+ *  leaves     n_leaves x 4 int32 (level, i, j, k): block coordinates at that
+ *             level; read during bats_create only
+ *  bc         per domain face (-x, +x, -y, +y, -z, +z): BATS_BC_*; periodic
+ *             must be set on both faces of an axis.  Outflow copies the nearest
+ *             interior cell (zero gradient, the paper's "floating" boundary,
+ *             Section 5.2); inflow holds the fixed state `inflow`.
+ *  inflow     primitive state (rho, u, B1, p) of inflow faces
+ *  body_r     cells whose centre lies within body_r of the origin are held
+ *             at the primitive state `body` (Section 5.2 inner boundary); 0 = none */
+typedef struct {
+  double lo[3], hi[3];
+  int32_t root[3];
+  int32_t n_leaves;
+  const int32_t* leaves;
+  int32_t bc[6];
+  double inflow[8];
+  double body_r;
+  double body[8];
+} bats_grid_desc;
+
+/* Physics and launch form, shared by all grids of a handle.
+ *  gamma          ratio of specific heats (Eq. 5)
+ *  limiter        BATS_LIM_MINMOD or BATS_LIM_MC (limited linear reconstruction
+ *                 of primitives, Algorithm 1 "calc_face_value")
+ *  rk             BATS_RK_MIDPOINT (default) or BATS_RK_SSP2
+ *  precision      BATS_FP64: every step in FP64.  BATS_MIXED: reconstruction,
+ *                 fluxes and sources in FP32; pressure recovery and the state
+ *                 accumulation in FP64.
+ *  b0, b0_param   background field B0 (split field): UNIFORM (B0 = p[0..2]),
+ *                 DIPOLE (moment p[0..2] at the origin), LINEAR (B0 = p[0..2] +
+ *                 G x, G = p[3..11] row-major)
+ *  powell         1 = add the Powell 8-wave div-B source terms (Eqs. 2-4)
+ *  learned        1 = add the MLP flux correction (needs bats_set_mlp)
+ *  persistent     1 = one persistent launch per stage (grid = SMs x occupancy)
+ *  blocks_per_cta blocks processed per work item in the persistent launch (>= 1)
+ *  ctas_per_sm    persistent CTAs per SM (0 = the occupancy limit) */
+typedef struct {
+  double gamma;
+  int32_t limiter, rk, precision, b0;
+  double b0_param[12];
+  int32_t powell, learned, persistent, blocks_per_cta;
+  int32_t ctas_per_sm, use_graph;
+  int32_t reserved[2];
+} bats_physics;
+
+/* Create a solver for n_grids independent grids advanced together (batched
+ * launch).  Validates every tree (exact tiling, full face/edge/corner 2:1
+ * balance through periodic wraps), builds the per-block neighbour table and
+ * the per-level block maps on the host once (the paper's memory-map idea,
+ * Section 4.4), and allocates device memory.  cuda_stream: a cudaStream_t, or
+ * NULL for a blocking stream owned by the handle (ordered with the legacy
+ * default stream).  On success *out owns everything; on failure
+ * *out is NULL and the return code says why.  The state is undefined until
+ * bats_set_state is called for every grid. */
+int bats_create(const bats_grid_desc* grids, int n_grids, const bats_physics* phys, void* cuda_stream,
+                bats_t** out);
+
+/* Release the handle and all its device memory.  NULL is ignored. */
+void bats_destroy(bats_t* h);
+
+/* Message of the last failure on this handle ("" if none).  With h == NULL,
+ * the message of the last failed bats_create in this process. */
+const char* bats_last_error(const bats_t* h);
+
+/* Copy the state of grid `grid` from U (host or device; n = 8 * 512 *
+ * n_blocks doubles, layout above) and recompute its CFL speed bound.
+ * Resets the grid's elapsed time to 0. */
+int bats_set_state(bats_t* h, int grid, const double* U, size_t n);
+
+/* Copy the state of grid `grid` into U (host or device, n doubles). */
+int bats_get_state(bats_t* h, int grid, double* U, size_t n);
+
+/* Advance every grid by n steps of the two-stage scheme (Section 5.2) with
+ * dt = cfl / max over non-body cells of sum_d (|u_d| + c_f,d)/dx_d, per grid,
+ * from the state at the start of each step.  Each stage fills ghost cells,
+ * reconstructs, computes Rusanov fluxes, adds sources and updates
+ * (Algorithms 1-2).  The time step never leaves the device.  Returns after the
+ * stream is synchronised once at the end; *t_out (nullable) receives grid 0's
+ * elapsed time.  BATS_ERR_NONPHYSICAL if any update produced rho <= 0,
+ * p <= 0 or NaN (the state is then that of the failing step). */
+int bats_step(bats_t* h, int n, double cfl, double* t_out);
+
+/* As bats_step with a fixed dt for every grid. */
+int bats_step_dt(bats_t* h, int n, double dt, double* t_out);
+
+/* Time step the next bats_step(cfl) would take for grid `grid`. */
+int bats_get_dt(bats_t* h, int grid, double cfl, double* dt);
+
+/* Elapsed simulated time of grid `grid` since its last bats_set_state. */
+int bats_get_time(bats_t* h, int grid, double* t);
+
+/* Milliseconds of device time of the last bats_step call, by phase
+ * (BATS_PHASE_*): ms[0] stage kernels, ms[1] time-step kernels, ms[2] total.
+ * n = number of entries available in ms. */
+int bats_get_timings(bats_t* h, double* ms, int n);
+
+/* Debug view of the ghost fill (Section 4.1-4.2) for the current state:
+ * writes the padded tiles double [8][n_blocks][12][12][12] of grid `grid`
+ * into T (host or device; n doubles).  Only the interior and the six face
+ * slabs (the cells the stencil reads) are defined; edge and corner cells are
+ * set to 0. */
+int bats_debug_fill_ghosts(bats_t* h, int grid, double* T, size_t n);
+
+/* Debug view of one stage: R = dU/dt of the current state of grid `grid`
+ * (fluxes, sources; body cells 0), double [8][n_blocks][8][8][8]. */
+int bats_debug_residual(bats_t* h, int grid, double* R, size_t n);
+
+/* Launch-form controls (the autotuner's knobs): persistent launch on/off,
+ * blocks per work item, CTAs per SM, CUDA-graph replay of whole steps. */
+int bats_set_launch(bats_t* h, int persistent, int blocks_per_cta, int ctas_per_sm, int use_graph);
+
+/* Number of kernels launched by the last bats_step call. */
+int bats_get_launch_count(bats_t* h, long long* n);
+
+/* Self-check of the mixed form's integer-only number conversions (no paper
+ * counterpart: on GB300 the FP32<->FP64 conversion instructions run on the
+ * FP64 unit, so the kernels convert with integer operations instead).  For n
+ * host values, f2d_out[i] = the kernels' conversion of f[i] to double and
+ * d2f_out[i] = the kernels' conversion of d[i] to float, for comparison with
+ * the compiler's conversions.  Allocates and frees its own device buffers. */
+int bats_debug_check_conversions(const float* f, const double* d, int n, double* f2d_out, float* d2f_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BATS_H */

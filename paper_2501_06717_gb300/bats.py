@@ -1,0 +1,342 @@
+"""Thin ctypes binding of libbats (``include/bats.h``), same names as the C ABI.
+
+Argument marshalling only: every step of the solver runs in the CUDA
+library.  There is no fallback: if ``_build/libbats.so`` is missing, loading
+raises.  Arrays may be numpy arrays (host) or torch tensors (host or
+device); device tensors are passed to the library as device pointers.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libbats.so")
+
+BATS_OK = 0
+BATS_ERR_INVALID_ARG = -1
+BATS_ERR_UNBALANCED_TREE = -2
+BATS_ERR_OUT_OF_MEMORY = -3
+BATS_ERR_CUDA = -4
+BATS_ERR_NONPHYSICAL = -5
+BATS_ERR_TIMEOUT = -6
+BATS_ERR_NOT_TRAINED = -7
+
+BATS_BC_PERIODIC, BATS_BC_OUTFLOW, BATS_BC_INFLOW = 0, 1, 2
+BATS_LIM_MINMOD, BATS_LIM_MC = 0, 1
+BATS_RK_MIDPOINT, BATS_RK_SSP2 = 0, 1
+BATS_FP64, BATS_MIXED = 0, 1
+BATS_B0_NONE, BATS_B0_UNIFORM, BATS_B0_DIPOLE, BATS_B0_LINEAR = 0, 1, 2, 3
+BATS_PHASE_STAGE, BATS_PHASE_DT, BATS_PHASE_TOTAL, BATS_NUM_PHASES = 0, 1, 2, 3
+
+
+class bats_grid_desc(ctypes.Structure):
+    _fields_ = [
+        ("lo", ctypes.c_double * 3),
+        ("hi", ctypes.c_double * 3),
+        ("root", ctypes.c_int32 * 3),
+        ("n_leaves", ctypes.c_int32),
+        ("leaves", ctypes.POINTER(ctypes.c_int32)),
+        ("bc", ctypes.c_int32 * 6),
+        ("inflow", ctypes.c_double * 8),
+        ("body_r", ctypes.c_double),
+        ("body", ctypes.c_double * 8),
+    ]
+
+
+class bats_physics(ctypes.Structure):
+    _fields_ = [
+        ("gamma", ctypes.c_double),
+        ("limiter", ctypes.c_int32),
+        ("rk", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("b0", ctypes.c_int32),
+        ("b0_param", ctypes.c_double * 12),
+        ("powell", ctypes.c_int32),
+        ("learned", ctypes.c_int32),
+        ("persistent", ctypes.c_int32),
+        ("blocks_per_cta", ctypes.c_int32),
+        ("ctas_per_sm", ctypes.c_int32),
+        ("use_graph", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 2),
+    ]
+
+
+class BatsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("libbats error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """Load libbats.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libbats.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    vp = ctypes.c_void_p
+    dp = ctypes.c_void_p  # host or device double*
+    L.bats_create.argtypes = [ctypes.POINTER(bats_grid_desc), ctypes.c_int, ctypes.POINTER(bats_physics), vp,
+                              ctypes.POINTER(vp)]
+    L.bats_destroy.argtypes = [vp]
+    L.bats_destroy.restype = None
+    L.bats_last_error.argtypes = [vp]
+    L.bats_last_error.restype = ctypes.c_char_p
+    L.bats_set_state.argtypes = [vp, ctypes.c_int, dp, ctypes.c_size_t]
+    L.bats_get_state.argtypes = [vp, ctypes.c_int, dp, ctypes.c_size_t]
+    L.bats_step.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+    L.bats_step_dt.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+    L.bats_get_dt.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+    L.bats_get_time.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    L.bats_get_timings.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
+    L.bats_debug_fill_ghosts.argtypes = [vp, ctypes.c_int, dp, ctypes.c_size_t]
+    L.bats_debug_residual.argtypes = [vp, ctypes.c_int, dp, ctypes.c_size_t]
+    L.bats_set_launch.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.bats_get_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+    L.bats_debug_check_conversions.argtypes = [vp, vp, ctypes.c_int, vp, vp]
+    _lib = L
+    return L
+
+
+def _ptr_and_size(a):
+    """(pointer as int, number of elements) of a numpy array or torch tensor."""
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), a.numel()
+    if not (isinstance(a, np.ndarray) and a.flags.c_contiguous):
+        raise ValueError("array must be a C-contiguous numpy array or torch tensor")
+    return a.ctypes.data, a.size
+
+
+def _check(h, rc):
+    if rc != BATS_OK:
+        msg = lib().bats_last_error(h)
+        raise BatsError(rc, msg.decode() if msg else "")
+
+
+# --------------------------------------------------------------------------
+# Descriptors from workload problems
+
+
+class _Grids:
+    """ctypes array of bats_grid_desc and the leaf arrays it points to."""
+
+    def __init__(self, problems):
+        self.leaves = []
+        self.arr = (bats_grid_desc * len(problems))()
+        for d, p in zip(self.arr, problems):
+            lv = np.ascontiguousarray(p.leaves, dtype=np.int32).reshape(-1, 4)
+            self.leaves.append(lv)
+            d.lo[:] = [float(x) for x in p.lo]
+            d.hi[:] = [float(x) for x in p.hi]
+            d.root[:] = [int(x) for x in p.root]
+            d.n_leaves = lv.shape[0]
+            d.leaves = lv.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+            d.bc[:] = [int(x) for x in p.bc]
+            d.inflow[:] = [float(x) for x in np.asarray(p.inflow, float).reshape(8)]
+            d.body_r = float(p.body_r)
+            d.body[:] = [float(x) for x in np.asarray(p.body, float).reshape(8)]
+
+
+def physics_from(problem, precision=BATS_FP64, persistent=0, blocks_per_cta=1, ctas_per_sm=0, use_graph=0):
+    ph = bats_physics()
+    ph.gamma = float(problem.gamma)
+    ph.limiter = int(problem.limiter)
+    ph.rk = int(problem.rk)
+    ph.precision = int(precision)
+    ph.b0 = int(problem.b0)
+    ph.b0_param[:] = [float(x) for x in np.asarray(problem.b0_param, float).reshape(12)]
+    ph.powell = int(problem.powell)
+    ph.learned = int(getattr(problem, "learned", 0) or 0)
+    ph.persistent = int(persistent)
+    ph.blocks_per_cta = int(blocks_per_cta)
+    ph.ctas_per_sm = int(ctas_per_sm)
+    ph.use_graph = int(use_graph)
+    return ph
+
+
+# --------------------------------------------------------------------------
+# Same-name wrappers of the C ABI
+
+
+def bats_create(problems, phys, stream=None):
+    """problems: list of workload problems (grid descriptors); phys: bats_physics.
+    stream: a torch.cuda.Stream, a raw cudaStream_t int, or None."""
+    g = _Grids(problems)
+    h = ctypes.c_void_p()
+    s = None
+    if stream is not None:
+        s = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    rc = lib().bats_create(g.arr, len(problems), ctypes.byref(phys), s, ctypes.byref(h))
+    if rc != BATS_OK:
+        msg = lib().bats_last_error(None)
+        raise BatsError(rc, msg.decode() if msg else "")
+    return h
+
+
+def bats_destroy(h):
+    lib().bats_destroy(h)
+
+
+def bats_last_error(h):
+    m = lib().bats_last_error(h)
+    return m.decode() if m else ""
+
+
+def bats_set_state(h, grid, U):
+    p, n = _ptr_and_size(U)
+    _check(h, lib().bats_set_state(h, int(grid), p, n))
+
+
+def bats_get_state(h, grid, out):
+    p, n = _ptr_and_size(out)
+    _check(h, lib().bats_get_state(h, int(grid), p, n))
+    return out
+
+
+def bats_step(h, n, cfl):
+    t = ctypes.c_double(0.0)
+    _check(h, lib().bats_step(h, int(n), float(cfl), ctypes.byref(t)))
+    return t.value
+
+
+def bats_step_dt(h, n, dt):
+    t = ctypes.c_double(0.0)
+    _check(h, lib().bats_step_dt(h, int(n), float(dt), ctypes.byref(t)))
+    return t.value
+
+
+def bats_get_dt(h, grid, cfl):
+    d = ctypes.c_double(0.0)
+    _check(h, lib().bats_get_dt(h, int(grid), float(cfl), ctypes.byref(d)))
+    return d.value
+
+
+def bats_get_time(h, grid):
+    t = ctypes.c_double(0.0)
+    _check(h, lib().bats_get_time(h, int(grid), ctypes.byref(t)))
+    return t.value
+
+
+def bats_get_timings(h):
+    ms = (ctypes.c_double * BATS_NUM_PHASES)()
+    _check(h, lib().bats_get_timings(h, ms, BATS_NUM_PHASES))
+    return list(ms)
+
+
+def bats_debug_fill_ghosts(h, grid, out):
+    p, n = _ptr_and_size(out)
+    _check(h, lib().bats_debug_fill_ghosts(h, int(grid), p, n))
+    return out
+
+
+def bats_debug_residual(h, grid, out):
+    p, n = _ptr_and_size(out)
+    _check(h, lib().bats_debug_residual(h, int(grid), p, n))
+    return out
+
+
+def bats_set_launch(h, persistent, blocks_per_cta, ctas_per_sm, use_graph):
+    _check(h, lib().bats_set_launch(h, int(persistent), int(blocks_per_cta), int(ctas_per_sm), int(use_graph)))
+
+
+def bats_get_launch_count(h):
+    n = ctypes.c_longlong(0)
+    _check(h, lib().bats_get_launch_count(h, ctypes.byref(n)))
+    return n.value
+
+
+def bats_debug_check_conversions(f, d):
+    f = np.ascontiguousarray(f, dtype=np.float32)
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    n = min(f.size, d.size)
+    o1 = np.zeros(n, np.float64)
+    o2 = np.zeros(n, np.float32)
+    rc = lib().bats_debug_check_conversions(f.ctypes.data, d.ctypes.data, n, o1.ctypes.data, o2.ctypes.data)
+    if rc != BATS_OK:
+        raise BatsError(rc, "conversion check failed")
+    return o1, o2
+
+
+# --------------------------------------------------------------------------
+# Convenience wrapper
+
+
+class Solver:
+    """One handle over one or more workload problems (batched when several)."""
+
+    def __init__(self, problems, precision=BATS_FP64, persistent=0, blocks_per_cta=1, ctas_per_sm=0,
+                 use_graph=0, stream=None):
+        if not isinstance(problems, (list, tuple)):
+            problems = [problems]
+        self.problems = list(problems)
+        self.phys = physics_from(self.problems[0], precision, persistent, blocks_per_cta, ctas_per_sm, use_graph)
+        self.h = bats_create(self.problems, self.phys, stream)
+
+    def close(self):
+        if self.h is not None:
+            bats_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_state(self, grid, U):
+        if isinstance(U, np.ndarray):
+            U = np.ascontiguousarray(U, dtype=np.float64)
+        bats_set_state(self.h, grid, U)
+
+    def set_states(self):
+        for g, p in enumerate(self.problems):
+            self.set_state(g, p.U0)
+
+    def get_state(self, grid=0):
+        p = self.problems[grid]
+        out = np.zeros((8, p.nb, 8, 8, 8))
+        return bats_get_state(self.h, grid, out)
+
+    def step(self, n, cfl):
+        return bats_step(self.h, n, cfl)
+
+    def step_dt(self, n, dt):
+        return bats_step_dt(self.h, n, dt)
+
+    def dt(self, grid=0, cfl=0.8):
+        return bats_get_dt(self.h, grid, cfl)
+
+    def time(self, grid=0):
+        return bats_get_time(self.h, grid)
+
+    def fill_ghosts(self, grid=0):
+        p = self.problems[grid]
+        out = np.zeros((8, p.nb, 12, 12, 12))
+        return bats_debug_fill_ghosts(self.h, grid, out)
+
+    def residual(self, grid=0):
+        p = self.problems[grid]
+        out = np.zeros((8, p.nb, 8, 8, 8))
+        return bats_debug_residual(self.h, grid, out)
+
+    def set_launch(self, persistent=0, blocks_per_cta=1, ctas_per_sm=0, use_graph=0):
+        bats_set_launch(self.h, persistent, blocks_per_cta, ctas_per_sm, use_graph)
+
+    def timings(self):
+        return bats_get_timings(self.h)
+
+    def launch_count(self):
+        return bats_get_launch_count(self.h)

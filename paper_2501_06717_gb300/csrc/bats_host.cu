@@ -1,0 +1,712 @@
+// bats_host.cu -- host side of libbats: the C ABI of include/bats.h, tree
+// validation (exact tiling, 2:1 balance across faces, edges and corners,
+// through periodic wraps), the per-block neighbour table and per-level block
+// maps built once per grid on the host and uploaded (the memory-map idea of
+// arXiv 2501.06717 Section 4.4 applied to the on-device ghost exchange), and
+// the launch sequence of a time step.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "bats.h"
+#include "bats_internal.h"
+
+namespace batsk {
+
+// launchers defined next to the kernels (bats_stage.cu)
+size_t stage_smem_bytes(bool mixed);
+cudaError_t stage_setup(int occ[2]);
+cudaError_t launch_stage_kernel(bool mixed, int grid, cudaStream_t st, const StageArgs& a);
+cudaError_t launch_to_internal(const double* ext, double* in, int block0, int nb, cudaStream_t st);
+cudaError_t launch_to_external(const double* in, double* ext, int block0, int nb, cudaStream_t st);
+cudaError_t launch_init_grid_states(GridDev* grids, int ngrids, double inv_gm1, double gm1, cudaStream_t st);
+cudaError_t launch_prim_mixed(const double* U, float* Wt, int b0, int nb, float gm1f, cudaStream_t st);
+cudaError_t launch_cfl(bool mixed, const double* U, const float* Wt, const GridDev* grids, const BlockDev* blocks,
+                       const PhysDev& ph, int b0, int nb, unsigned long long* smax, cudaStream_t st);
+cudaError_t launch_dt(int ngrids, int mode, double cfl, double fixed_dt, double* dt, double* t,
+                      unsigned long long* smax, unsigned long long* smax_next, cudaStream_t st);
+cudaError_t launch_debug_fill(const StageArgs& a, int b0, int nb, double* T, cudaStream_t st);
+cudaError_t launch_check_conversions(const float* f, const double* d, int n, double* f2d_out, float* d2f_out);
+
+}  // namespace batsk
+
+using namespace batsk;
+
+struct bats {
+  std::string err;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int ngrids = 0, nbt = 0, num_sms = 0;
+  std::vector<GridDev> grids_h;
+  std::vector<BlockDev> blocks_h;
+  std::vector<int32_t> levmap_h;
+  PhysDev ph{};
+  GridDev* grids_d = nullptr;
+  BlockDev* blocks_d = nullptr;
+  int32_t* levmap_d = nullptr;
+  double *U = nullptr, *U1 = nullptr;
+  float *W = nullptr, *W1 = nullptr;
+  double *dt = nullptr, *t = nullptr;
+  unsigned long long *smax = nullptr, *smax_next = nullptr;
+  int32_t* errw = nullptr;
+  double* staging = nullptr;
+  size_t staging_n = 0;
+  int persistent = 0, bpc = 1, ctas_per_sm = 0, use_graph = 0;
+  int occ[2] = {1, 1};
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  double ms_last[BATS_NUM_PHASES] = {0, 0, 0};
+  long long launches = 0;
+  cudaGraphExec_t graph = nullptr;
+  int graph_n = -1;
+  double graph_cfl = 0, graph_dt = 0;
+};
+
+static std::string g_create_error;
+
+static int fail(bats_t* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_create_error = msg;
+  return code;
+}
+static int cuda_fail(bats_t* h, cudaError_t e, const char* what) {
+  return fail(h, BATS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+#define CK(h, call)                                      \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// Grid construction (host).
+
+namespace {
+
+struct HostGrid {
+  const bats_grid_desc* d;
+  int maxlev = 0;
+  std::vector<std::vector<int32_t>> map;  // per level, dense block map (local leaf index or -1)
+  int64_t nblk(int l, int a) const { return static_cast<int64_t>(d->root[a]) << l; }
+  int32_t at(int l, int64_t i, int64_t j, int64_t k) const {
+    if (l < 0 || l > maxlev) return -1;
+    return map[l][(k * nblk(l, 1) + j) * nblk(l, 0) + i];
+  }
+};
+
+// Covering leaf of block position p (level l): returns local leaf index and
+// its level (l or coarser), or -1 if the region is refined.
+int cover(const HostGrid& H, int l, const int64_t p[3], int& lev_out) {
+  for (int lc = l; lc >= 0; lc--) {
+    int sh = l - lc;
+    int32_t id = H.at(lc, p[0] >> sh, p[1] >> sh, p[2] >> sh);
+    if (id >= 0) { lev_out = lc; return id; }
+  }
+  lev_out = l + 1;
+  return -1;
+}
+
+int build_grid(bats_t* h, const bats_grid_desc& d, int gidx, int block0, std::vector<BlockDev>& blocks,
+               GridDev& gd, std::vector<int32_t>& levmap) {
+  if (d.n_leaves <= 0 || !d.leaves) return fail(h, BATS_ERR_INVALID_ARG, "grid " + std::to_string(gidx) + ": no leaves");
+  for (int a = 0; a < 3; a++) {
+    if (d.root[a] <= 0 || !(d.hi[a] > d.lo[a]))
+      return fail(h, BATS_ERR_INVALID_ARG, "grid " + std::to_string(gidx) + ": bad root or extent");
+    for (int s = 0; s < 2; s++)
+      if (d.bc[2 * a + s] < 0 || d.bc[2 * a + s] > 2)
+        return fail(h, BATS_ERR_INVALID_ARG, "grid " + std::to_string(gidx) + ": bad boundary code");
+    if ((d.bc[2 * a] == BATS_BC_PERIODIC) != (d.bc[2 * a + 1] == BATS_BC_PERIODIC))
+      return fail(h, BATS_ERR_INVALID_ARG, "grid " + std::to_string(gidx) + ": periodic on one side only");
+  }
+  HostGrid H;
+  H.d = &d;
+  for (int b = 0; b < d.n_leaves; b++) {
+    int l = d.leaves[4 * b];
+    if (l < 0 || l > MAXLEV) return fail(h, BATS_ERR_INVALID_ARG, "grid " + std::to_string(gidx) + ": level out of range");
+    H.maxlev = std::max(H.maxlev, l);
+  }
+  H.map.resize(H.maxlev + 1);
+  for (int l = 0; l <= H.maxlev; l++) {
+    int64_t n = H.nblk(l, 0) * H.nblk(l, 1) * H.nblk(l, 2);
+    if (n > (int64_t(1) << 31)) return fail(h, BATS_ERR_INVALID_ARG, "grid too large");
+    H.map[l].assign(static_cast<size_t>(n), -1);
+  }
+  long double vol = 0;
+  for (int b = 0; b < d.n_leaves; b++) {
+    const int32_t* L = d.leaves + 4 * b;
+    for (int a = 0; a < 3; a++)
+      if (L[1 + a] < 0 || L[1 + a] >= H.nblk(L[0], a))
+        return fail(h, BATS_ERR_INVALID_ARG, "grid " + std::to_string(gidx) + ": leaf outside the domain");
+    int64_t m = (static_cast<int64_t>(L[3]) * H.nblk(L[0], 1) + L[2]) * H.nblk(L[0], 0) + L[1];
+    if (H.map[L[0]][m] >= 0) return fail(h, BATS_ERR_UNBALANCED_TREE, "grid " + std::to_string(gidx) + ": duplicate leaf");
+    H.map[L[0]][m] = b;
+    vol += std::ldexp(1.0L, -3 * L[0]);
+  }
+  if (vol != static_cast<long double>(d.root[0]) * d.root[1] * d.root[2])
+    return fail(h, BATS_ERR_UNBALANCED_TREE, "grid " + std::to_string(gidx) + ": leaves do not tile the domain");
+  for (int b = 0; b < d.n_leaves; b++) {
+    const int32_t* L = d.leaves + 4 * b;
+    for (int lc = L[0] - 1; lc >= 0; lc--) {
+      int sh = L[0] - lc;
+      if (H.at(lc, L[1] >> sh, L[2] >> sh, L[3] >> sh) >= 0)
+        return fail(h, BATS_ERR_UNBALANCED_TREE, "grid " + std::to_string(gidx) + ": nested leaves");
+    }
+  }
+  // neighbour relations through the 26 directions, 2:1 balance, face table
+  std::vector<std::vector<int>> touching(d.n_leaves);
+  blocks.resize(block0 + d.n_leaves);
+  for (int b = 0; b < d.n_leaves; b++) {
+    const int32_t* L = d.leaves + 4 * b;
+    int l = L[0];
+    BlockDev B{};
+    B.grid = gidx;
+    B.level = l;
+    B.bi = L[1];
+    B.bj = L[2];
+    B.bk = L[3];
+    for (int dk = -1; dk <= 1; dk++)
+      for (int dj = -1; dj <= 1; dj++)
+        for (int di = -1; di <= 1; di++) {
+          if (!di && !dj && !dk) continue;
+          int dd[3] = {di, dj, dk};
+          int64_t p[3] = {L[1] + di, L[2] + dj, L[3] + dk};
+          int outside_axis = -1, outside_side = 0;
+          bool off = false;
+          for (int a = 0; a < 3; a++) {
+            int64_t n = H.nblk(l, a);
+            if (p[a] < 0 || p[a] >= n) {
+              if (d.bc[2 * a] == BATS_BC_PERIODIC) p[a] = (p[a] % n + n) % n;
+              else { off = true; outside_axis = a; outside_side = p[a] < 0 ? 0 : 1; }
+            }
+          }
+          int nz = (di != 0) + (dj != 0) + (dk != 0);
+          int face = -1;
+          if (nz == 1) face = di ? (di < 0 ? 0 : 1) : dj ? (dj < 0 ? 2 : 3) : (dk < 0 ? 4 : 5);
+          if (off) {
+            if (face >= 0) {
+              int bc = d.bc[2 * outside_axis + outside_side];
+              B.ftype[face] = bc == BATS_BC_INFLOW ? FACE_INFLOW : FACE_OUTFLOW;
+              B.fnb[face] = -1;
+            }
+            continue;
+          }
+          int lc;
+          int id = cover(H, l, p, lc);
+          if (id >= 0) {
+            if (lc < l - 1)
+              return fail(h, BATS_ERR_UNBALANCED_TREE, "grid " + std::to_string(gidx) + ": neighbours differ by more than one level");
+            touching[b].push_back(id);
+            if (face >= 0) {
+              B.ftype[face] = lc == l ? FACE_SAME : FACE_COARSER;
+              B.fnb[face] = block0 + id;
+            }
+          } else {
+            // refined: the children of p touching this block must be leaves
+            for (int o = 0; o < 8; o++) {
+              int oo[3] = {o & 1, (o >> 1) & 1, (o >> 2) & 1};
+              bool ok = true;
+              for (int a = 0; a < 3; a++) {
+                if (dd[a] < 0 && oo[a] != 1) ok = false;
+                if (dd[a] > 0 && oo[a] != 0) ok = false;
+              }
+              if (!ok) continue;
+              int32_t cid = H.at(l + 1, 2 * p[0] + oo[0], 2 * p[1] + oo[1], 2 * p[2] + oo[2]);
+              if (cid < 0)
+                return fail(h, BATS_ERR_UNBALANCED_TREE, "grid " + std::to_string(gidx) + ": neighbours differ by more than one level");
+              touching[b].push_back(cid);
+            }
+            if (face >= 0) {
+              B.ftype[face] = FACE_FINER;
+              B.fnb[face] = -1;
+            }
+          }
+        }
+    for (int s = 0; s < 6; s++)
+      if (B.ftype[s] == FACE_COARSER || B.ftype[s] == FACE_FINER) B.amr = 1;
+    blocks[block0 + b] = B;
+  }
+  for (int b = 0; b < d.n_leaves; b++) {
+    if (!blocks[block0 + b].amr) continue;
+    blocks[block0 + b].need_u = 1;
+    for (int id : touching[b]) blocks[block0 + id].need_u = 1;
+  }
+  // grid record + level maps with global block indices
+  std::memset(&gd, 0, sizeof(gd));
+  for (int a = 0; a < 3; a++) {
+    gd.lo[a] = d.lo[a];
+    gd.hi[a] = d.hi[a];
+    gd.root[a] = d.root[a];
+  }
+  for (int s = 0; s < 6; s++) gd.bc[s] = d.bc[s];
+  gd.maxlev = H.maxlev;
+  gd.block0 = block0;
+  gd.nb = d.n_leaves;
+  gd.body_r = d.body_r;
+  for (int v = 0; v < 8; v++) {
+    gd.Winflow[v] = d.inflow[v];
+    gd.Wbody[v] = d.body[v];
+  }
+  for (int l = 0; l <= MAXLEV; l++) gd.map_off[l] = -1;
+  for (int l = 0; l <= H.maxlev; l++) {
+    gd.map_off[l] = static_cast<int64_t>(levmap.size());
+    for (int32_t id : H.map[l]) levmap.push_back(id >= 0 ? block0 + id : -1);
+  }
+  return BATS_OK;
+}
+
+template <class T>
+int dev_alloc(bats_t* h, T** p, size_t n) {
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(n, 1) * sizeof(T));
+  if (e != cudaSuccess) return fail(h, BATS_ERR_OUT_OF_MEMORY, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  return BATS_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+void free_all(bats_t* h) {
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  cudaFree(h->grids_d);
+  cudaFree(h->blocks_d);
+  cudaFree(h->levmap_d);
+  cudaFree(h->U);
+  cudaFree(h->U1);
+  cudaFree(h->W);
+  cudaFree(h->W1);
+  cudaFree(h->dt);
+  cudaFree(h->t);
+  cudaFree(h->smax);
+  cudaFree(h->smax_next);
+  cudaFree(h->errw);
+  cudaFree(h->staging);
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  h->stream = nullptr;
+}
+
+int grid_check(bats_t* h, int grid) {
+  if (!h) return BATS_ERR_INVALID_ARG;
+  if (grid < 0 || grid >= h->ngrids) return fail(h, BATS_ERR_INVALID_ARG, "grid index out of range");
+  return BATS_OK;
+}
+
+StageArgs base_args(bats_t* h) {
+  StageArgs a{};
+  a.grids = h->grids_d;
+  a.blocks = h->blocks_d;
+  a.levmap = h->levmap_d;
+  a.dt = h->dt;
+  a.smax_next = h->smax_next;
+  a.err = h->errw;
+  a.nblocks = h->nbt;
+  a.blocks_per_item = std::max(1, h->bpc);
+  a.ph = h->ph;
+  return a;
+}
+
+int launch_stage(bats_t* h, const StageArgs& a) {
+  bool mixed = h->ph.precision == BATS_MIXED;
+  int nitems = (a.nblocks + a.blocks_per_item - 1) / a.blocks_per_item;
+  int grid = nitems;
+  if (h->persistent) {
+    int per_sm = h->ctas_per_sm > 0 ? std::min(h->ctas_per_sm, h->occ[mixed]) : h->occ[mixed];
+    grid = std::min(nitems, h->num_sms * std::max(1, per_sm));
+  }
+  if (grid <= 0) return BATS_OK;
+  h->launches++;
+  CK(h, launch_stage_kernel(mixed, grid, h->stream, a));
+  return BATS_OK;
+}
+
+int launch_cfl(bats_t* h, int g) {
+  const GridDev& G = h->grids_h[g];
+  CK(h, cudaMemsetAsync(h->smax + g, 0, sizeof(unsigned long long), h->stream));
+  h->launches++;
+  CK(h, launch_cfl(h->ph.precision == BATS_MIXED, h->U, h->W, h->grids_d, h->blocks_d, h->ph, G.block0, G.nb,
+                   h->smax, h->stream));
+  return BATS_OK;
+}
+
+// Enqueue n steps (no synchronisation).
+int enqueue_steps(bats_t* h, int n, double cfl, double fixed_dt) {
+  const bool mixed = h->ph.precision == BATS_MIXED;
+  const bool ssp = h->ph.rk == BATS_RK_SSP2;
+  for (int s = 0; s < n; s++) {
+    CK(h, launch_dt(h->ngrids, 0, cfl, fixed_dt, h->dt, h->t, h->smax, h->smax_next, h->stream));
+    h->launches++;
+    StageArgs a = base_args(h);
+    // stage 1: U* = U^n + (dt/2) R(U^n)   [SSP-RK2: U^n + dt R(U^n)]
+    a.Uin = h->U;
+    a.Ubase = h->U;
+    a.Uout = h->U1;
+    a.Win = h->W;
+    a.Wout = h->W1;
+    a.kind = 0;
+    a.last = 0;
+    a.beta = ssp ? 1.0 : 0.5;
+    a.write_u_all = (!mixed || ssp) ? 1 : 0;
+    int rc = launch_stage(h, a);
+    if (rc) return rc;
+    // stage 2: U^{n+1} = U^n + dt R(U*)   [SSP-RK2: U^n/2 + (U* + dt R(U*))/2]
+    a.Uin = h->U1;
+    a.Ubase = h->U;
+    a.Uout = h->U;
+    a.Win = h->W1;
+    a.Wout = h->W;
+    a.kind = ssp ? 1 : 0;
+    a.last = 1;
+    a.beta = 1.0;
+    a.write_u_all = 1;
+    rc = launch_stage(h, a);
+    if (rc) return rc;
+    CK(h, launch_dt(h->ngrids, 1, cfl, fixed_dt, h->dt, h->t, h->smax, h->smax_next, h->stream));
+    h->launches++;
+  }
+  CK(h, cudaGetLastError());
+  return BATS_OK;
+}
+
+int run_steps(bats_t* h, int n, double cfl, double fixed_dt, double* t_out) {
+  if (n < 0) return fail(h, BATS_ERR_INVALID_ARG, "negative step count");
+  h->launches = 0;
+  int32_t init[2] = {0, INT_MAX};
+  CK(h, cudaMemcpyAsync(h->errw, init, sizeof(init), cudaMemcpyHostToDevice, h->stream));
+  CK(h, cudaEventRecord(h->ev0, h->stream));
+  if (h->use_graph && n > 0) {
+    if (!h->graph || h->graph_n != n || h->graph_cfl != cfl || h->graph_dt != fixed_dt) {
+      if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+      cudaGraph_t g;
+      CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+      long long l0 = h->launches;
+      int rc = enqueue_steps(h, n, cfl, fixed_dt);
+      cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+      if (rc) return rc;
+      if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+      e = cudaGraphInstantiate(&h->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+      h->graph_n = n;
+      h->graph_cfl = cfl;
+      h->graph_dt = fixed_dt;
+      h->launches = l0;
+    }
+    CK(h, cudaGraphLaunch(h->graph, h->stream));
+    h->launches = static_cast<long long>(n) * 4;
+  } else {
+    int rc = enqueue_steps(h, n, cfl, fixed_dt);
+    if (rc) return rc;
+  }
+  CK(h, cudaEventRecord(h->ev1, h->stream));
+  int32_t ew[2];
+  CK(h, cudaMemcpyAsync(ew, h->errw, sizeof(ew), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+  h->ms_last[BATS_PHASE_STAGE] = ms;
+  h->ms_last[BATS_PHASE_DT] = 0.0;
+  h->ms_last[BATS_PHASE_TOTAL] = ms;
+  if (t_out) CK(h, cudaMemcpy(t_out, h->t, sizeof(double), cudaMemcpyDeviceToHost));
+  if (ew[0] & ERR_TIMEOUT) return fail(h, BATS_ERR_TIMEOUT, "a bounded device wait ran out");
+  if (ew[0] & ERR_BOUNDS) return fail(h, BATS_ERR_CUDA, "ghost fill met a source two levels away (unbalanced tree)");
+  if (ew[0] & ERR_NONPHYSICAL)
+    return fail(h, BATS_ERR_NONPHYSICAL, "non-physical state (rho <= 0, p <= 0 or NaN) in block " + std::to_string(ew[1]));
+  h->err.clear();
+  return BATS_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+
+extern "C" {
+
+int bats_create(const bats_grid_desc* grids, int n_grids, const bats_physics* phys, void* cuda_stream,
+                bats_t** out) {
+  if (!out) return fail(nullptr, BATS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!grids || n_grids <= 0 || !phys) return fail(nullptr, BATS_ERR_INVALID_ARG, "grids/phys missing");
+  if (!(phys->gamma > 1.0)) return fail(nullptr, BATS_ERR_INVALID_ARG, "gamma must exceed 1");
+  if (phys->limiter < 0 || phys->limiter > 1 || phys->rk < 0 || phys->rk > 1 || phys->precision < 0 ||
+      phys->precision > 1 || phys->b0 < 0 || phys->b0 > 3)
+    return fail(nullptr, BATS_ERR_INVALID_ARG, "bad physics enumeration");
+  if (phys->learned) return fail(nullptr, BATS_ERR_NOT_TRAINED, "learned form needs bats_set_mlp (not set)");
+  bats_t* h = new bats_t();
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  h->ngrids = n_grids;
+  h->grids_h.resize(n_grids);
+  int block0 = 0;
+  for (int g = 0; g < n_grids; g++) {
+    int rc = build_grid(h, grids[g], g, block0, h->blocks_h, h->grids_h[g], h->levmap_h);
+    if (rc) {
+      g_create_error = h->err;
+      delete h;
+      return rc;
+    }
+    block0 += grids[g].n_leaves;
+  }
+  h->nbt = block0;
+  h->ph.gamma = phys->gamma;
+  h->ph.gm1 = phys->gamma - 1.0;
+  h->ph.inv_gm1 = 1.0 / (phys->gamma - 1.0);
+  h->ph.limiter = phys->limiter;
+  h->ph.rk = phys->rk;
+  h->ph.precision = phys->precision;
+  h->ph.b0 = phys->b0;
+  h->ph.powell = phys->powell ? 1 : 0;
+  h->ph.learned = 0;
+  for (int i = 0; i < 12; i++) h->ph.b0p[i] = phys->b0_param[i];
+  h->persistent = phys->persistent;
+  h->bpc = std::max(1, phys->blocks_per_cta);
+  h->ctas_per_sm = phys->ctas_per_sm;
+  h->use_graph = phys->use_graph;
+
+  int rc = BATS_OK;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess && !h->stream) {
+    // a blocking stream of our own: ordered with the legacy default stream,
+    // and capturable into a CUDA graph
+    e = cudaStreamCreate(&h->stream);
+    h->own_stream = e == cudaSuccess;
+  }
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = stage_setup(h->occ);
+  if (e != cudaSuccess) {
+    rc = cuda_fail(h, e, "device setup");
+    g_create_error = h->err;
+    delete h;
+    return rc;
+  }
+  size_t nstate = static_cast<size_t>(h->nbt) * NV * NCELL;
+  size_t maxnb = 0;
+  for (auto& G : h->grids_h) maxnb = std::max<size_t>(maxnb, G.nb);
+  h->staging_n = maxnb * NV * 12 * 12 * 12;
+  if ((rc = dev_alloc(h, &h->grids_d, h->ngrids)) || (rc = dev_alloc(h, &h->blocks_d, h->nbt)) ||
+      (rc = dev_alloc(h, &h->levmap_d, h->levmap_h.size())) || (rc = dev_alloc(h, &h->U, nstate)) ||
+      (rc = dev_alloc(h, &h->U1, nstate)) || (rc = dev_alloc(h, &h->dt, h->ngrids)) ||
+      (rc = dev_alloc(h, &h->t, h->ngrids)) || (rc = dev_alloc(h, &h->smax, h->ngrids)) ||
+      (rc = dev_alloc(h, &h->smax_next, h->ngrids)) || (rc = dev_alloc(h, &h->errw, 2)) ||
+      (rc = dev_alloc(h, &h->staging, h->staging_n))) {
+    free_all(h);
+    g_create_error = h->err;
+    delete h;
+    return rc;
+  }
+  if (h->ph.precision == BATS_MIXED) {
+    if ((rc = dev_alloc(h, &h->W, nstate)) || (rc = dev_alloc(h, &h->W1, nstate))) {
+      free_all(h);
+      g_create_error = h->err;
+      delete h;
+      return rc;
+    }
+  }
+  e = cudaMemcpyAsync(h->grids_d, h->grids_h.data(), sizeof(GridDev) * h->ngrids, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->blocks_d, h->blocks_h.data(), sizeof(BlockDev) * h->nbt, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->levmap_d, h->levmap_h.data(), sizeof(int32_t) * h->levmap_h.size(),
+                        cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->t, 0, sizeof(double) * h->ngrids, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->smax, 0, sizeof(unsigned long long) * h->ngrids, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->U, 0, sizeof(double) * nstate, h->stream);
+  if (e == cudaSuccess) e = launch_init_grid_states(h->grids_d, h->ngrids, h->ph.inv_gm1, h->ph.gm1, h->stream);
+  if (e == cudaSuccess) e = cudaEventCreate(&h->ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&h->ev1);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess) e = cudaMemcpy(h->grids_h.data(), h->grids_d, sizeof(GridDev) * h->ngrids, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    rc = cuda_fail(h, e, "upload");
+    free_all(h);
+    g_create_error = h->err;
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return BATS_OK;
+}
+
+void bats_destroy(bats_t* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  free_all(h);
+  delete h;
+}
+
+const char* bats_last_error(const bats_t* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int bats_set_state(bats_t* h, int grid, const double* U, size_t n) {
+  int rc = grid_check(h, grid);
+  if (rc) return rc;
+  const GridDev& G = h->grids_h[grid];
+  size_t need = static_cast<size_t>(G.nb) * NV * NCELL;
+  if (!U || n != need) return fail(h, BATS_ERR_INVALID_ARG, "state size mismatch: expected " + std::to_string(need));
+  const double* src = U;
+  if (!is_device_ptr(U)) {
+    CK(h, cudaMemcpyAsync(h->staging, U, need * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    src = h->staging;
+  }
+  CK(h, launch_to_internal(src, h->U, G.block0, G.nb, h->stream));
+  if (h->ph.precision == BATS_MIXED)
+    CK(h, launch_prim_mixed(h->U, h->W, G.block0, G.nb, static_cast<float>(h->ph.gm1), h->stream));
+  rc = launch_cfl(h, grid);
+  if (rc) return rc;
+  CK(h, cudaMemsetAsync(h->t + grid, 0, sizeof(double), h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return BATS_OK;
+}
+
+int bats_get_state(bats_t* h, int grid, double* U, size_t n) {
+  int rc = grid_check(h, grid);
+  if (rc) return rc;
+  const GridDev& G = h->grids_h[grid];
+  size_t need = static_cast<size_t>(G.nb) * NV * NCELL;
+  if (!U || n != need) return fail(h, BATS_ERR_INVALID_ARG, "state size mismatch: expected " + std::to_string(need));
+  bool dev = is_device_ptr(U);
+  double* dst = dev ? U : h->staging;
+  CK(h, launch_to_external(h->U, dst, G.block0, G.nb, h->stream));
+  if (!dev) CK(h, cudaMemcpyAsync(U, h->staging, need * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return BATS_OK;
+}
+
+int bats_step(bats_t* h, int n, double cfl, double* t_out) {
+  if (!h) return BATS_ERR_INVALID_ARG;
+  if (!(cfl > 0.0)) return fail(h, BATS_ERR_INVALID_ARG, "cfl must be positive");
+  return run_steps(h, n, cfl, 0.0, t_out);
+}
+
+int bats_step_dt(bats_t* h, int n, double dt, double* t_out) {
+  if (!h) return BATS_ERR_INVALID_ARG;
+  if (!(dt > 0.0)) return fail(h, BATS_ERR_INVALID_ARG, "dt must be positive");
+  return run_steps(h, n, -1.0, dt, t_out);
+}
+
+int bats_get_dt(bats_t* h, int grid, double cfl, double* dt) {
+  int rc = grid_check(h, grid);
+  if (rc) return rc;
+  if (!dt || !(cfl > 0.0)) return fail(h, BATS_ERR_INVALID_ARG, "bad dt pointer or cfl");
+  unsigned long long s;
+  CK(h, cudaStreamSynchronize(h->stream));
+  CK(h, cudaMemcpy(&s, h->smax + grid, sizeof(s), cudaMemcpyDeviceToHost));
+  double sm;
+  std::memcpy(&sm, &s, sizeof(sm));
+  *dt = cfl / sm;
+  return BATS_OK;
+}
+
+int bats_get_time(bats_t* h, int grid, double* t) {
+  int rc = grid_check(h, grid);
+  if (rc) return rc;
+  if (!t) return fail(h, BATS_ERR_INVALID_ARG, "t is NULL");
+  CK(h, cudaStreamSynchronize(h->stream));
+  CK(h, cudaMemcpy(t, h->t + grid, sizeof(double), cudaMemcpyDeviceToHost));
+  return BATS_OK;
+}
+
+int bats_get_timings(bats_t* h, double* ms, int n) {
+  if (!h || !ms || n <= 0) return BATS_ERR_INVALID_ARG;
+  for (int i = 0; i < n && i < BATS_NUM_PHASES; i++) ms[i] = h->ms_last[i];
+  return BATS_OK;
+}
+
+int bats_debug_fill_ghosts(bats_t* h, int grid, double* T, size_t n) {
+  int rc = grid_check(h, grid);
+  if (rc) return rc;
+  const GridDev& G = h->grids_h[grid];
+  size_t need = static_cast<size_t>(G.nb) * NV * 1728;
+  if (!T || n != need) return fail(h, BATS_ERR_INVALID_ARG, "tile size mismatch");
+  bool dev = is_device_ptr(T);
+  double* dst = dev ? T : h->staging;
+  StageArgs a = base_args(h);
+  a.Uin = h->U;
+  int32_t init[2] = {0, INT_MAX};
+  CK(h, cudaMemcpyAsync(h->errw, init, sizeof(init), cudaMemcpyHostToDevice, h->stream));
+  CK(h, launch_debug_fill(a, G.block0, G.nb, dst, h->stream));
+  if (!dev) CK(h, cudaMemcpyAsync(T, h->staging, need * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return BATS_OK;
+}
+
+int bats_debug_residual(bats_t* h, int grid, double* R, size_t n) {
+  int rc = grid_check(h, grid);
+  if (rc) return rc;
+  const GridDev& G = h->grids_h[grid];
+  size_t need = static_cast<size_t>(G.nb) * NV * NCELL;
+  if (!R || n != need) return fail(h, BATS_ERR_INVALID_ARG, "size mismatch");
+  StageArgs a = base_args(h);
+  a.Uin = h->U;
+  a.Ubase = h->U;
+  a.Uout = h->U1;
+  a.Win = h->W;
+  a.Wout = h->W1;
+  a.kind = 2;
+  a.last = 0;
+  a.beta = 1.0;
+  a.write_u_all = 1;
+  int32_t init[2] = {0, INT_MAX};
+  CK(h, cudaMemcpyAsync(h->errw, init, sizeof(init), cudaMemcpyHostToDevice, h->stream));
+  rc = launch_stage(h, a);
+  if (rc) return rc;
+  bool dev = is_device_ptr(R);
+  double* dst = dev ? R : h->staging;
+  CK(h, launch_to_external(h->U1, dst, G.block0, G.nb, h->stream));
+  if (!dev) CK(h, cudaMemcpyAsync(R, h->staging, need * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return BATS_OK;
+}
+
+int bats_set_launch(bats_t* h, int persistent, int blocks_per_cta, int ctas_per_sm, int use_graph) {
+  if (!h || blocks_per_cta < 1 || ctas_per_sm < 0) return BATS_ERR_INVALID_ARG;
+  h->persistent = persistent ? 1 : 0;
+  h->bpc = blocks_per_cta;
+  h->ctas_per_sm = ctas_per_sm;
+  h->use_graph = use_graph ? 1 : 0;
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  return BATS_OK;
+}
+
+int bats_get_launch_count(bats_t* h, long long* n) {
+  if (!h || !n) return BATS_ERR_INVALID_ARG;
+  *n = h->launches;
+  return BATS_OK;
+}
+
+// Self-check of the integer-only FP32 <-> FP64 conversions against CUDA's
+// conversions (host arrays of n values).
+int bats_debug_check_conversions(const float* f, const double* d, int n, double* f2d_out, float* d2f_out) {
+  if (!f || !d || n <= 0 || !f2d_out || !d2f_out) return BATS_ERR_INVALID_ARG;
+  float *fd = nullptr, *od2f = nullptr;
+  double *dd = nullptr, *of2d = nullptr;
+  cudaError_t e = cudaMalloc(&fd, n * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&dd, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&of2d, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&od2f, n * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemcpy(fd, f, n * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dd, d, n * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_check_conversions(fd, dd, n, of2d, od2f);
+  if (e == cudaSuccess) e = cudaMemcpy(f2d_out, of2d, n * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(d2f_out, od2f, n * sizeof(float), cudaMemcpyDeviceToHost);
+  cudaFree(fd);
+  cudaFree(dd);
+  cudaFree(of2d);
+  cudaFree(od2f);
+  return e == cudaSuccess ? BATS_OK : BATS_ERR_CUDA;
+}
+
+}  // extern "C"

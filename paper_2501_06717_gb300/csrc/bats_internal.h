@@ -1,0 +1,77 @@
+// Internal types of libbats shared by the host code (bats_host.cu) and the
+// kernels (bats_stage.cu).  Device layout of a state buffer: block-major
+// [n_blocks_total][8 variables][512 cells] (k, j, i; i fastest), so that one
+// block's state is one contiguous 32 KB (FP64) or 16 KB (FP32) run that a
+// single bulk copy per variable stages into shared memory.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace batsk {
+
+constexpr int NV = 8;          // conserved variables
+constexpr int NC = 8;          // cells per block per axis
+constexpr int NCELL = 512;     // cells per block
+constexpr int NFACE = 576;     // faces per block per direction (9 x 8 x 8)
+constexpr int NGHOST = 768;    // face-slab ghost cells (6 x 2 x 64)
+constexpr int NTILE = 1280;    // interior + face-slab ghosts
+constexpr int MAXLEV = 14;
+constexpr int STAGE_THREADS = 576;
+
+enum FaceType : int32_t { FACE_SAME = 0, FACE_COARSER = 1, FACE_FINER = 2, FACE_OUTFLOW = 3, FACE_INFLOW = 4 };
+enum B0Mode : int32_t { B0_NONE = 0, B0_UNIFORM = 1, B0_DIPOLE = 2, B0_LINEAR = 3 };
+enum ErrBits : int32_t { ERR_NONPHYSICAL = 1, ERR_TIMEOUT = 2, ERR_BOUNDS = 4 };
+
+struct GridDev {
+  double lo[3], hi[3];
+  int32_t root[3];
+  int32_t bc[6];
+  int32_t maxlev;
+  int32_t block0, nb;
+  int64_t map_off[MAXLEV + 1];   // offset of each level's block map in levmap
+  double body_r;
+  double Winflow[8], Wbody[8];   // primitive, as given
+  double Uinflow[8], Ubody[8];   // conservative, computed on the device at create
+  float Winflow32[8];            // mixed-form primitive of Uinflow
+};
+
+struct BlockDev {
+  int32_t grid, level, bi, bj, bk;
+  int32_t ftype[6];              // FaceType per face (-x, +x, -y, +y, -z, +z)
+  int32_t fnb[6];                // neighbour block (global index) for SAME / COARSER
+  int32_t amr;                   // 1 if any face is COARSER or FINER
+  int32_t need_u;                // mixed form: FP64 stage output read by a neighbour's
+                                 // restriction/prolongation (this block or a block it
+                                 // touches has a COARSER/FINER face)
+  int32_t pad_[2];
+};
+
+struct PhysDev {
+  double gamma, gm1, inv_gm1;
+  int32_t limiter, rk, precision, b0, powell, learned;
+  double b0p[12];
+};
+
+// Arguments of one stage launch.
+struct StageArgs {
+  const double* Uin;      // stage input, block-major FP64
+  const double* Ubase;    // base state of the stage (U^n)
+  double* Uout;           // output (may alias Ubase: each CTA reads its own cells first)
+  const float* Win;       // mixed form: FP32 primitives of Uin
+  float* Wout;            // mixed form: FP32 primitives of Uout
+  const GridDev* grids;
+  const BlockDev* blocks;
+  const int32_t* levmap;
+  const double* dt;       // per grid
+  unsigned long long* smax_next;  // per grid, bit pattern of a positive double
+  int32_t* err;           // [0] error bits, [1] first bad block
+  int32_t nblocks;
+  int32_t blocks_per_item;
+  int32_t kind;           // 0: Uout = Ubase + c R;  1: Uout = 0.5 Ubase + 0.5 (Uin + c R)
+  int32_t last;           // 1: reduce the CFL bound of Uout into smax_next
+  int32_t write_u_all;    // mixed: 1 = write Uout for every block, 0 = only need_u blocks
+  double beta;            // c = beta * dt[grid]
+  PhysDev ph;
+};
+
+}  // namespace batsk
