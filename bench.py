@@ -1,0 +1,363 @@
+#!/usr/bin/env python3
+"""Throughput of the fused MHD stage on GB300: cell-updates/s.
+
+One "step" is one full time step (two fused stages: ghost fill, primitive
+recovery, limited reconstruction, Rusanov fluxes, Powell/B0 sources,
+conservative update, CFL reduction) over every block of the workload.  A
+cell-update is one cell advanced by one full step.
+
+Default workload: 64 independent periodic block-adaptive grids of uneven size
+(64..4096 blocks of 8^3 cells, log-uniform, seed 20250112) with smooth random
+states, the mixed-precision form (FP32 reconstruction/fluxes/sources, FP64
+pressure recovery and accumulation), one persistent launch per stage captured
+in a CUDA graph with autotuned blocks per CTA.  The state (about 2 GB) is far
+larger than L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--precision mixed|fp64] [--workload batched|blast|magnetosphere]
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs its own batch of
+64 grids (seed offset by rank): weak scaling, no data-path collective.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, HERE)
+
+from paper_2501_06717_gb300 import workloads as W  # noqa: E402
+
+METRIC = "cell-updates/s/GB300"
+UNIT = "cell-updates/s"
+BYTES_PER_CELL_UPDATE = 320  # FP64 state: stage 1 reads U^n, writes U*; stage 2 reads U*, U^n, writes U^{n+1}
+
+# DRAM traffic of one k_stage launch per cell, from the ncu capture summarised
+# in profiles/ (None until a capture of the current kernel source exists).
+NCU_TRAFFIC = {
+    # precision: (bytes per cell per launch, sha256 of bats_stage.cu at capture)
+}
+
+
+def _peaks():
+    p = os.path.join(HERE, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _kernel_sha():
+    with open(os.path.join(HERE, "paper_2501_06717_gb300", "csrc", "bats_stage.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def make_workload(name, rank=0, processes=None, grids=64):
+    if name == "batched":
+        probs = W.batched_grids(seed=20250112 + rank, processes=processes)[:grids]
+        return probs, "%d independent periodic block-adaptive grids, 64-4096 blocks of 8^3 cells " \
+            "(log-uniform, seed %d), smooth Fourier states" % (len(probs), 20250112 + rank)
+    if name == "blast":
+        return [W.blast()], "spherical MHD blast, 4^3 roots on [-1,1]^3 refined inside r<0.4 (120 blocks)"
+    if name == "magnetosphere":
+        return [W.magnetosphere()], "magnetosphere-like grid, 5 levels, dipole B0, body r=2.5 (3872 blocks)"
+    raise ValueError(name)
+
+
+# --------------------------------------------------------------------------
+# CPU oracle timing (test infrastructure; the baseline, not the target)
+
+
+def oracle_sample(problems, seconds):
+    """Run the oracle one step per grid over the workload's grids in order
+    until `seconds` of CPU work; returns (cells, elapsed, grids used)."""
+    from oracle import oracle as O
+    O.build()
+    cells = 0
+    t0 = time.perf_counter()
+    used = 0
+    for p in problems:
+        O.run(p, p.U0, 1, cfl=p.cfl)
+        cells += p.ncells
+        used += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    return cells, time.perf_counter() - t0, used
+
+
+def cpu_baseline(problems, seconds):
+    from oracle import oracle as O
+    cells, el, used = oracle_sample(problems, seconds)
+    return {"value": cells / el, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": "%d of %d grids (%d cells), 1 step each, FP64 C oracle with OpenMP over blocks, %.1f s"
+                      % (used, len(problems), cells, el)}
+
+
+def run_reference(args, rank, world):
+    """The oracle timed as the reference arm on the same workload, each step a
+    bounded sample (the first grids of the workload)."""
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    problems, desc = make_workload(args.workload, 0, processes=min(16, os.cpu_count() or 1), grids=args.grids)
+    O.build()
+    # size the sample for about 2.5 s per step
+    t0 = time.perf_counter()
+    O.run(problems[0], problems[0].U0, 1, cfl=problems[0].cfl)
+    rate = problems[0].ncells / max(time.perf_counter() - t0, 1e-6)
+    budget = rate * 2.5
+    sample, cells = [], 0
+    for p in problems:
+        sample.append(p)
+        cells += p.ncells
+        if cells >= budget:
+            break
+    states = [p.U0.copy() for p in sample]
+    for _ in range(args.warmup):
+        for i, p in enumerate(sample):
+            states[i], _, _ = O.run(p, states[i], 1, cfl=p.cfl)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        for i, p in enumerate(sample):
+            states[i], _, _ = O.run(p, states[i], 1, cfl=p.cfl)
+        times.append(time.perf_counter() - t0)
+    el = sum(times)
+    value = cells * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": desc, "sample_grids": len(sample), "sample_cells": cells},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                             "sample": "first %d grids (%d cells) of the workload per step" % (len(sample), cells)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# Clocks during the timed region
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "50",
+                 "-i", str(gpu_index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--workload", default="batched", choices=["batched", "blast", "magnetosphere"])
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--grids", type=int, default=64, help="first N grids of the batched workload")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and "RANK" not in os.environ:
+        raise SystemExit("--gpus > 1 needs torchrun (one process per GPU)")
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+
+    # inputs and the CPU baseline before any CUDA call (spawned pool only)
+    problems, desc = make_workload(args.workload, rank, processes=min(16, os.cpu_count() or 1), grids=args.grids)
+    cpu = cpu_baseline(problems, args.cpu_seconds) if (rank == 0 and world == 1 and args.cpu_seconds > 0) else None
+
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2501_06717_gb300 import autotune, bats
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    prec = bats.BATS_MIXED if args.precision == "mixed" else bats.BATS_FP64
+    stream = torch.cuda.Stream()
+    cells = sum(p.ncells for p in problems)
+    cfl = problems[0].cfl
+    solver = bats.Solver(problems, precision=prec, stream=stream)
+    solver.set_states()
+
+    # warm-up: autotune the launch form, then W steps, then build the graph
+    tune = None
+    if not args.no_autotune:
+        tune = autotune.autotune(solver, cfl, steps=2)
+    else:
+        solver.set_launch(1, 1, 0, 1)
+    for _ in range(args.warmup):
+        solver.step(1, cfl)
+    solver.step(args.steps, cfl)  # captures the K-step graph
+
+    torch.cuda.synchronize()
+    barrier()
+    clocks = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ
+                          else os.environ["CUDA_VISIBLE_DEVICES"].split(",")[local])
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        solver.step(args.steps, cfl)
+        ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    launches = solver.launch_count()
+    # mean stage-kernel launch duration: the same K steps launched eagerly, with
+    # CUDA events around each step's two stage launches (graph replay carries
+    # no per-kernel events)
+    solver.set_launch(*(tune[0] if tune else (1, 1, 0)), 0)
+    solver.step(args.steps, cfl)
+    stage_ms = solver.timings()[bats.BATS_PHASE_STAGE]
+    stage_total_ms = solver.timings()[bats.BATS_PHASE_TOTAL]
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        c = torch.tensor([float(cells)], device="cuda")
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        total_cells = c.item()
+    else:
+        total_cells = cells
+    value = total_cells * args.steps / (ms * 1e-3)
+
+    # roofline of the dominant kernel (k_stage): algorithmic bytes per launch
+    # (160 B per cell on average over the two stages) / mean launch duration
+    nlaunch = 2 * args.steps
+    per_launch_ms = stage_ms / nlaunch
+    alg_bytes = BYTES_PER_CELL_UPDATE / 2 * cells
+    achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
+    peak, peak_kind = _peaks()
+    tr = NCU_TRAFFIC.get(args.precision)
+    traffic = tr[0] * cells if (tr and tr[1] == _kernel_sha()) else None
+
+    # end to end through the public API with host buffers: per step, the
+    # state goes in from pinned host memory and comes back out
+    host = [torch.from_numpy(np.ascontiguousarray(p.U0)).pin_memory() for p in problems] if args.e2e_steps else []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        for g in range(len(problems)):
+            bats.bats_set_state(solver.h, g, host[g])
+        solver.step(1, cfl)
+        for g in range(len(problems)):
+            bats.bats_get_state(solver.h, g, host[g])
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    state_bytes = cells * 8 * 8
+    e2e = {"value": cells * args.e2e_steps / e2e_s * (total_cells / cells) if args.e2e_steps else None, "unit": UNIT,
+           "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes}
+
+    # the plain FP64 path on the same workload, for the mixed-vs-FP64 comparison
+    fp64 = None
+    if prec == bats.BATS_MIXED and args.fp64_steps > 0:
+        solver.close()
+        s64 = bats.Solver(problems, precision=bats.BATS_FP64, stream=stream, persistent=1, blocks_per_cta=1)
+        s64.set_states()
+        s64.step(2, cfl)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s64.step(args.fp64_steps, cfl)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fp64 = cells * args.fp64_steps / (e0.elapsed_time(e1) * 1e-3)
+        s64.close()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if prec == bats.BATS_MIXED else "f64", "data": "synthetic",
+            "config": {"workload": desc, "blocks": sum(p.nb for p in problems), "cells_per_gpu": cells,
+                       "precision": args.precision,
+                       "launch": {"persistent_blocks_per_cta_ctas_per_sm": list(tune[0]) if tune else [1, 1, 0],
+                                  "cuda_graph": True},
+                       "l2": "inputs larger than L2 (state %.2f GB per GPU, L2 129 MB); no flush" %
+                             (2 * state_bytes / 1e9),
+                       "cfl": cfl},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "k_stage<%s>" % ("true" if prec == bats.BATS_MIXED else "false"),
+                         "peak_source": peak_kind, "bytes_per_launch": alg_bytes,
+                         "mean_launch_ms": per_launch_ms},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "fp64_value": fp64,
+            "stage_share": stage_ms / stage_total_ms if stage_total_ms > 0 else None,
+        }
+        if tune:
+            line["autotune_ms_per_stage"] = {"%d/%d/%d" % c: m for c, m in tune[1]}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -60,6 +60,8 @@ struct bats {
   int persistent = 0, bpc = 1, ctas_per_sm = 0, use_graph = 0;
   int occ[2] = {1, 1};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::vector<cudaEvent_t> stage_ev;   // pairs around the two stage launches of each step
+  int timed_steps = 0;
   double ms_last[BATS_NUM_PHASES] = {0, 0, 0};
   long long launches = 0;
   cudaGraphExec_t graph = nullptr;
@@ -251,7 +253,30 @@ int build_grid(bats_t* h, const bats_grid_desc& d, int gidx, int block0, std::ve
     gd.Winflow[v] = d.inflow[v];
     gd.Wbody[v] = d.body[v];
   }
-  for (int l = 0; l <= MAXLEV; l++) gd.map_off[l] = -1;
+  for (int l = 0; l <= MAXLEV; l++) {
+    gd.map_off[l] = -1;
+    for (int a = 0; a < 3; a++) {
+      double ncell = static_cast<double>((static_cast<int64_t>(d.root[a]) << l) * NC);
+      gd.dx[l][a] = (d.hi[a] - d.lo[a]) / ncell;
+      gd.idx[l][a] = 1.0 / gd.dx[l][a];
+      gd.dxf[l][a] = static_cast<float>(gd.dx[l][a]);
+      gd.idxf[l][a] = static_cast<float>(gd.idx[l][a]);
+    }
+  }
+  for (int a = 0; a < 3; a++) gd.lof[a] = static_cast<float>(d.lo[a]);
+  // blocks with a cell centre inside the body (same FP64 centre formula as the kernels)
+  if (d.body_r > 0.0) {
+    for (int b = 0; b < d.n_leaves; b++) {
+      BlockDev& B = blocks[block0 + b];
+      for (int c = 0; c < NCELL && !B.body; c++) {
+        int ci = c & 7, cj = (c >> 3) & 7, ck = c >> 6;
+        double x = d.lo[0] + ((static_cast<double>(B.bi * NC) + ci) + 0.5) * gd.dx[B.level][0];
+        double y = d.lo[1] + ((static_cast<double>(B.bj * NC) + cj) + 0.5) * gd.dx[B.level][1];
+        double z = d.lo[2] + ((static_cast<double>(B.bk * NC) + ck) + 0.5) * gd.dx[B.level][2];
+        if (x * x + y * y + z * z < d.body_r * d.body_r) B.body = 1;
+      }
+    }
+  }
   for (int l = 0; l <= H.maxlev; l++) {
     gd.map_off[l] = static_cast<int64_t>(levmap.size());
     for (int32_t id : H.map[l]) levmap.push_back(id >= 0 ? block0 + id : -1);
@@ -269,7 +294,7 @@ int dev_alloc(bats_t* h, T** p, size_t n) {
 bool is_device_ptr(const void* p) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-    cudaGetLastError();
+    cudaGetLastError();  // clear: an unregistered host pointer is not an error here
     return false;
   }
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
@@ -292,6 +317,8 @@ void free_all(bats_t* h) {
   cudaFree(h->staging);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
+  for (cudaEvent_t e : h->stage_ev) cudaEventDestroy(e);
+  h->stage_ev.clear();
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   h->stream = nullptr;
 }
@@ -339,13 +366,33 @@ int launch_cfl(bats_t* h, int g) {
   return BATS_OK;
 }
 
-// Enqueue n steps (no synchronisation).
-int enqueue_steps(bats_t* h, int n, double cfl, double fixed_dt) {
+constexpr int kMaxTimedSteps = 256;
+
+int ensure_stage_events(bats_t* h, int n) {
+  int want = 2 * std::min(n, kMaxTimedSteps);
+  while (static_cast<int>(h->stage_ev.size()) < want) {
+    cudaEvent_t e;
+    CK(h, cudaEventCreate(&e));
+    h->stage_ev.push_back(e);
+  }
+  return BATS_OK;
+}
+
+// Enqueue n steps (no synchronisation).  The two stage launches of each of
+// the first kMaxTimedSteps steps are bracketed by an event pair.
+int enqueue_steps(bats_t* h, int n, double cfl, double fixed_dt, bool timed) {
   const bool mixed = h->ph.precision == BATS_MIXED;
   const bool ssp = h->ph.rk == BATS_RK_SSP2;
+  if (timed) {
+    int rc0 = ensure_stage_events(h, n);
+    if (rc0) return rc0;
+  }
+  h->timed_steps = timed ? std::min(n, kMaxTimedSteps) : 0;
+  const int ntimed = h->timed_steps;
   for (int s = 0; s < n; s++) {
     CK(h, launch_dt(h->ngrids, 0, cfl, fixed_dt, h->dt, h->t, h->smax, h->smax_next, h->stream));
     h->launches++;
+    if (s < ntimed) CK(h, cudaEventRecord(h->stage_ev[2 * s], h->stream));
     StageArgs a = base_args(h);
     // stage 1: U* = U^n + (dt/2) R(U^n)   [SSP-RK2: U^n + dt R(U^n)]
     a.Uin = h->U;
@@ -371,6 +418,7 @@ int enqueue_steps(bats_t* h, int n, double cfl, double fixed_dt) {
     a.write_u_all = 1;
     rc = launch_stage(h, a);
     if (rc) return rc;
+    if (s < ntimed) CK(h, cudaEventRecord(h->stage_ev[2 * s + 1], h->stream));
     CK(h, launch_dt(h->ngrids, 1, cfl, fixed_dt, h->dt, h->t, h->smax, h->smax_next, h->stream));
     h->launches++;
   }
@@ -381,6 +429,7 @@ int enqueue_steps(bats_t* h, int n, double cfl, double fixed_dt) {
 int run_steps(bats_t* h, int n, double cfl, double fixed_dt, double* t_out) {
   if (n < 0) return fail(h, BATS_ERR_INVALID_ARG, "negative step count");
   h->launches = 0;
+  CK(h, cudaGetLastError());  // report (and clear) anything left from an earlier call
   int32_t init[2] = {0, INT_MAX};
   CK(h, cudaMemcpyAsync(h->errw, init, sizeof(init), cudaMemcpyHostToDevice, h->stream));
   CK(h, cudaEventRecord(h->ev0, h->stream));
@@ -390,7 +439,7 @@ int run_steps(bats_t* h, int n, double cfl, double fixed_dt, double* t_out) {
       cudaGraph_t g;
       CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
       long long l0 = h->launches;
-      int rc = enqueue_steps(h, n, cfl, fixed_dt);
+      int rc = enqueue_steps(h, n, cfl, fixed_dt, false);
       cudaError_t e = cudaStreamEndCapture(h->stream, &g);
       if (rc) return rc;
       if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
@@ -404,8 +453,9 @@ int run_steps(bats_t* h, int n, double cfl, double fixed_dt, double* t_out) {
     }
     CK(h, cudaGraphLaunch(h->graph, h->stream));
     h->launches = static_cast<long long>(n) * 4;
+    h->timed_steps = 0;
   } else {
-    int rc = enqueue_steps(h, n, cfl, fixed_dt);
+    int rc = enqueue_steps(h, n, cfl, fixed_dt, true);
     if (rc) return rc;
   }
   CK(h, cudaEventRecord(h->ev1, h->stream));
@@ -413,9 +463,17 @@ int run_steps(bats_t* h, int n, double cfl, double fixed_dt, double* t_out) {
   CK(h, cudaMemcpyAsync(ew, h->errw, sizeof(ew), cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
   float ms = 0.f;
-  cudaEventElapsedTime(&ms, h->ev0, h->ev1);
-  h->ms_last[BATS_PHASE_STAGE] = ms;
-  h->ms_last[BATS_PHASE_DT] = 0.0;
+  CK(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+  double stage_ms = 0.0;
+  for (int s = 0; s < h->timed_steps && n > 0; s++) {
+    float m = 0.f;
+    CK(h, cudaEventElapsedTime(&m, h->stage_ev[2 * s], h->stage_ev[2 * s + 1]));
+    stage_ms += m;
+  }
+  if (h->timed_steps > 0 && n > h->timed_steps) stage_ms *= static_cast<double>(n) / h->timed_steps;
+  // replayed graphs carry no per-stage events: the stage time is unmeasured
+  h->ms_last[BATS_PHASE_STAGE] = h->timed_steps > 0 ? stage_ms : -1.0;
+  h->ms_last[BATS_PHASE_DT] = h->timed_steps > 0 ? ms - stage_ms : -1.0;
   h->ms_last[BATS_PHASE_TOTAL] = ms;
   if (t_out) CK(h, cudaMemcpy(t_out, h->t, sizeof(double), cudaMemcpyDeviceToHost));
   if (ew[0] & ERR_TIMEOUT) return fail(h, BATS_ERR_TIMEOUT, "a bounded device wait ran out");
@@ -461,6 +519,9 @@ int bats_create(const bats_grid_desc* grids, int n_grids, const bats_physics* ph
   h->ph.gamma = phys->gamma;
   h->ph.gm1 = phys->gamma - 1.0;
   h->ph.inv_gm1 = 1.0 / (phys->gamma - 1.0);
+  h->ph.gammaf = static_cast<float>(h->ph.gamma);
+  h->ph.gm1f = static_cast<float>(h->ph.gm1);
+  h->ph.inv_gm1f = static_cast<float>(h->ph.inv_gm1);
   h->ph.limiter = phys->limiter;
   h->ph.rk = phys->rk;
   h->ph.precision = phys->precision;

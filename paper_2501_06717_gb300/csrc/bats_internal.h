@@ -33,6 +33,10 @@ struct GridDev {
   double Winflow[8], Wbody[8];   // primitive, as given
   double Uinflow[8], Ubody[8];   // conservative, computed on the device at create
   float Winflow32[8];            // mixed-form primitive of Uinflow
+  // per-level geometry, computed once on the host: dx = (hi - lo) / cells
+  double dx[MAXLEV + 1][3], idx[MAXLEV + 1][3];
+  float dxf[MAXLEV + 1][3], idxf[MAXLEV + 1][3];
+  float lof[3];
 };
 
 struct BlockDev {
@@ -43,11 +47,13 @@ struct BlockDev {
   int32_t need_u;                // mixed form: FP64 stage output read by a neighbour's
                                  // restriction/prolongation (this block or a block it
                                  // touches has a COARSER/FINER face)
-  int32_t pad_[2];
+  int32_t body;                  // 1 if some cell centre lies inside the inner body
+  int32_t pad_;
 };
 
 struct PhysDev {
   double gamma, gm1, inv_gm1;
+  float gammaf, gm1f, inv_gm1f, padf_;
   int32_t limiter, rk, precision, b0, powell, learned;
   double b0p[12];
 };

@@ -471,7 +471,7 @@ __device__ __forceinline__ void fill_ghost(const StageArgs& a, const GhostCtx& c
     double u[8];
     ghost_value(cx, B.level, g, u);
     if constexpr (MIXED) {
-      prim_mixed(u, static_cast<float>(a.ph.gm1), w);
+      prim_mixed(u, a.ph.gm1f, w);
     } else {
 #pragma unroll
       for (int v = 0; v < NV; v++) w[v] = u[v];
@@ -499,11 +499,13 @@ __global__ void __launch_bounds__(STAGE_THREADS, MIXED ? 2 : 1) k_stage(const St
   R* sT = reinterpret_cast<R*>(smem_raw);       // [8][1280] tile
   R* sF = sT + NV * NTILE;                       // [12][576] face values
   __shared__ uint64_t bar;
-  __shared__ double sred[STAGE_THREADS / 32];
+  __shared__ R sred[STAGE_THREADS / 32];
 
   const int tid = threadIdx.x;
   const PhysDev& ph = a.ph;
-  const R gamma = R(ph.gamma), inv_gm1 = R(ph.inv_gm1);
+  R gamma, inv_gm1;
+  if constexpr (MIXED) { gamma = ph.gammaf; inv_gm1 = ph.inv_gm1f; }
+  else { gamma = ph.gamma; inv_gm1 = ph.inv_gm1; }
   const bool has_b0 = ph.b0 != B0_NONE;
 
   if (tid == 0) mbar_init(&bar, 1);
@@ -545,17 +547,20 @@ __global__ void __launch_bounds__(STAGE_THREADS, MIXED ? 2 : 1) k_stage(const St
         __syncthreads();
       }
 
-      // block geometry
-      double dxd[3], lo_blk[3];
-#pragma unroll
-      for (int d = 0; d < 3; d++) {
-        double ncell = static_cast<double>((static_cast<int64_t>(G.root[d]) << B.level) * NC);
-        dxd[d] = (G.hi[d] - G.lo[d]) / ncell;
+      // block geometry (per-level spacing precomputed on the host); positions
+      // in the compute precision: FP64 for the FP64 form, FP32 for the mixed
+      const int lev = B.level;
+      R idx0, idx1, idx2, dxr0, dxr1, dxr2, lor0, lor1, lor2;
+      if constexpr (MIXED) {
+        idx0 = G.idxf[lev][0]; idx1 = G.idxf[lev][1]; idx2 = G.idxf[lev][2];
+        dxr0 = G.dxf[lev][0]; dxr1 = G.dxf[lev][1]; dxr2 = G.dxf[lev][2];
+        lor0 = G.lof[0]; lor1 = G.lof[1]; lor2 = G.lof[2];
+      } else {
+        idx0 = G.idx[lev][0]; idx1 = G.idx[lev][1]; idx2 = G.idx[lev][2];
+        dxr0 = G.dx[lev][0]; dxr1 = G.dx[lev][1]; dxr2 = G.dx[lev][2];
+        lor0 = G.lo[0]; lor1 = G.lo[1]; lor2 = G.lo[2];
       }
-      lo_blk[0] = static_cast<double>(B.bi * NC);
-      lo_blk[1] = static_cast<double>(B.bj * NC);
-      lo_blk[2] = static_cast<double>(B.bk * NC);
-      const R idx0 = R(1.0 / dxd[0]), idx1 = R(1.0 / dxd[1]), idx2 = R(1.0 / dxd[2]);
+      const int gb0 = B.bi * NC, gb1 = B.bj * NC, gb2 = B.bk * NC;
 
       // per-cell accumulators (threads < 512 own cell tid)
       const int ci = tid & 7, cj = (tid >> 3) & 7, ck = tid >> 6;
@@ -597,9 +602,9 @@ __global__ void __launch_bounds__(STAGE_THREADS, MIXED ? 2 : 1) k_stage(const St
             // increasing order
             const int cc0 = d == 0 ? f : ta, cc1 = d == 1 ? f : (d == 0 ? ta : tb), cc2 = d == 2 ? f : tb;
             R xf[3];
-            xf[0] = R(G.lo[0] + ((lo_blk[0] + static_cast<double>(cc0)) + (d == 0 ? 0.0 : 0.5)) * dxd[0]);
-            xf[1] = R(G.lo[1] + ((lo_blk[1] + static_cast<double>(cc1)) + (d == 1 ? 0.0 : 0.5)) * dxd[1]);
-            xf[2] = R(G.lo[2] + ((lo_blk[2] + static_cast<double>(cc2)) + (d == 2 ? 0.0 : 0.5)) * dxd[2]);
+            xf[0] = lor0 + (R(gb0 + cc0) + (d == 0 ? R(0) : R(0.5))) * dxr0;
+            xf[1] = lor1 + (R(gb1 + cc1) + (d == 1 ? R(0) : R(0.5))) * dxr1;
+            xf[2] = lor2 + (R(gb2 + cc2) + (d == 2 ? R(0) : R(0.5))) * dxr2;
             b0_at<R>(ph, xf, B0f);
           }
           B0r[0] = d == 0 ? B0f[0] : (d == 1 ? B0f[1] : B0f[2]);
@@ -659,18 +664,20 @@ __global__ void __launch_bounds__(STAGE_THREADS, MIXED ? 2 : 1) k_stage(const St
       R smax_loc = R(0);
       if (tid < NCELL) {
         const int c = tid;
-        double xc[3];
-        xc[0] = G.lo[0] + ((lo_blk[0] + ci) + 0.5) * dxd[0];
-        xc[1] = G.lo[1] + ((lo_blk[1] + cj) + 0.5) * dxd[1];
-        xc[2] = G.lo[2] + ((lo_blk[2] + ck) + 0.5) * dxd[2];
-        const bool in_body = G.body_r > 0.0 &&
-                             (xc[0] * xc[0] + xc[1] * xc[1] + xc[2] * xc[2]) < G.body_r * G.body_r;
+        bool in_body = false;
+        if (B.body) {  // FP64, the same centre formula as the host and the oracle
+          double x = G.lo[0] + ((static_cast<double>(gb0) + ci) + 0.5) * G.dx[lev][0];
+          double y = G.lo[1] + ((static_cast<double>(gb1) + cj) + 0.5) * G.dx[lev][1];
+          double z = G.lo[2] + ((static_cast<double>(gb2) + ck) + 0.5) * G.dx[lev][2];
+          in_body = (x * x + y * y + z * z) < G.body_r * G.body_r;
+        }
         R Wc[8];
 #pragma unroll
         for (int v = 0; v < NV; v++) Wc[v] = sT[v * NTILE + c];
         R B0c[3] = {R(0), R(0), R(0)};
         if (has_b0) {
-          R xr[3] = {R(xc[0]), R(xc[1]), R(xc[2])};
+          R xr[3] = {lor0 + (R(gb0 + ci) + R(0.5)) * dxr0, lor1 + (R(gb1 + cj) + R(0.5)) * dxr1,
+                     lor2 + (R(gb2 + ck) + R(0.5)) * dxr2};
           b0_at<R>(ph, xr, B0c);
         }
         R S[8] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
@@ -714,7 +721,7 @@ __global__ void __launch_bounds__(STAGE_THREADS, MIXED ? 2 : 1) k_stage(const St
         if (need_w && a.kind != 2) {
           if constexpr (MIXED) {
             double p64;
-            prim_mixed(Uo, static_cast<float>(ph.gm1), Wn, &p64);
+            prim_mixed(Uo, ph.gm1f, Wn, &p64);
             bad |= !(p64 > 0.0);
           } else {
             prim64(Uo, ph.gm1, Wn);
@@ -745,23 +752,33 @@ __global__ void __launch_bounds__(STAGE_THREADS, MIXED ? 2 : 1) k_stage(const St
           for (int e = 0; e < 3; e++) {
             R bn = Bt[e], bt1 = Bt[(e + 1) % 3], bt2 = Bt[(e + 2) % 3];
             R cf;
-            if constexpr (MIXED) cf = fast_speed_n<R>(gamma, Wn[0], Wn[7], bn, bt1, bt2);
-            else cf = fast_speed_exact(ph.gamma, Wn[0], Wn[7], bn, bt1, bt2);
-            s = s + Ops<R>::div_(Ops<R>::abs_(Wn[1 + e]) + cf, R(dxd[e]));
+            if constexpr (MIXED) {
+              cf = fast_speed_n<R>(gamma, Wn[0], Wn[7], bn, bt1, bt2);
+              s = s + (Ops<R>::abs_(Wn[1 + e]) + cf) * (e == 0 ? idx0 : (e == 1 ? idx1 : idx2));
+            } else {
+              cf = fast_speed_exact(ph.gamma, Wn[0], Wn[7], bn, bt1, bt2);
+              s = s + (Ops<R>::abs_(Wn[1 + e]) + cf) / (e == 0 ? dxr0 : (e == 1 ? dxr1 : dxr2));
+            }
           }
           smax_loc = s;
         }
       }
       if (a.last && a.kind != 2) {
-        double m = static_cast<double>(smax_loc);
+        R m = smax_loc;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        for (int o = 16; o > 0; o >>= 1) {
+          R q = __shfl_xor_sync(0xffffffffu, m, o);
+          m = q > m ? q : m;
+        }
         if ((tid & 31) == 0) sred[tid >> 5] = m;
         __syncthreads();
         if (tid == 0) {
-          double mm = 0.0;
-          for (int w = 0; w < STAGE_THREADS / 32; w++) mm = fmax(mm, sred[w]);
-          if (mm > 0.0) atomicMax(&a.smax_next[B.grid], static_cast<unsigned long long>(__double_as_longlong(mm)));
+          R mm = R(0);
+          for (int w = 0; w < STAGE_THREADS / 32; w++) mm = sred[w] > mm ? sred[w] : mm;
+          double md;
+          if constexpr (MIXED) md = f2d_int(mm);
+          else md = mm;
+          if (md > 0.0) atomicMax(&a.smax_next[B.grid], static_cast<unsigned long long>(__double_as_longlong(md)));
         }
       }
       __syncthreads();

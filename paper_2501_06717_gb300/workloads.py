@@ -347,11 +347,26 @@ def fast_wave(m=6, nsteps=500, amplitude=1.0):
     return _finish(prob, W)
 
 
-def _fourier(rng, x, y, z, nmodes=8, kmax=4):
-    """Sum of seeded cosine modes with integer wave vectors |k_i| <= kmax on
-    the unit cube; returns (value, d/dx, d/dy, d/dz) and the amplitude sum."""
-    val = np.zeros_like(x)
-    grad = [np.zeros_like(x) for _ in range(3)]
+def _axis_coords(lo, hi, root, leaves):
+    """Per-block cell-centre coordinates along each axis: 3 arrays [nb][8]."""
+    leaves = np.asarray(leaves).reshape(-1, 4)
+    out = []
+    for a in range(3):
+        dx = (hi[a] - lo[a]) / ((root[a] * NC) * (2.0 ** leaves[:, 0]))
+        g = leaves[:, 1 + a][:, None] * NC + np.arange(NC)[None, :]
+        out.append(lo[a] + (g + 0.5) * dx[:, None])
+    return out
+
+
+def _fourier(rng, xs, nmodes=8, kmax=4):
+    """Sum of seeded cosine modes a cos(2 pi k.x + phi) with integer wave
+    vectors |k_i| <= kmax on the unit cube, evaluated at cell centres from the
+    per-axis coordinates xs (the modes are separable: e^{i k.x} is a product
+    of per-axis factors).  Returns (value, gradient (3), amplitude sum,
+    gradient bound), arrays [nb][8][8][8]."""
+    nb = xs[0].shape[0]
+    val = np.zeros((nb, NC, NC, NC))
+    grad = [np.zeros((nb, NC, NC, NC)) for _ in range(3)]
     asum = 0.0
     gsum = 0.0
     for _ in range(nmodes):
@@ -360,11 +375,15 @@ def _fourier(rng, x, y, z, nmodes=8, kmax=4):
             k[0] = 1
         a = rng.uniform(0.2, 1.0)
         ph = rng.uniform(0, 2 * math.pi)
-        arg = 2 * math.pi * (k[0] * x + k[1] * y + k[2] * z) + ph
-        val += a * np.cos(arg)
-        s = -a * np.sin(arg) * 2 * math.pi
+        ex = np.exp(2j * math.pi * k[0] * xs[0])
+        ey = np.exp(2j * math.pi * k[1] * xs[1])
+        ez = np.exp(2j * math.pi * k[2] * xs[2]) * np.exp(1j * ph)
+        E = (ez[:, :, None] * ey[:, None, :])[:, :, :, None] * ex[:, None, None, :]
+        val += a * E.real
+        s = -a * 2 * math.pi * E.imag
         for c in range(3):
-            grad[c] += s * k[c]
+            if k[c]:
+                grad[c] += s * k[c]
         asum += a
         gsum += a * 2 * math.pi * float(np.abs(k).max())
     return val, grad, asum, gsum
@@ -379,35 +398,43 @@ def random_smooth_grid(n_target, seed):
     r = 4 if n_target < 512 else (8 if n_target < 4096 else 16)
     root = (r, r, r)
     lo, hi = (0.0,) * 3, (1.0,) * 3
-    leaves = uniform_leaves(root)
+    L = np.array(uniform_leaves(root), dtype=np.int64)
     guard = 0
-    while len(leaves) < n_target and guard < 200:
+    while L.shape[0] < n_target and guard < 200:
         guard += 1
         cen = rng.uniform(0, 1, size=3)
         rad = rng.uniform(0.05, 0.25)
         maxl = int(rng.integers(1, 3))
-
-        def inside(b0, b1, cen=cen, rad=rad):
-            q = np.clip(cen, b0, b1) - cen
-            return float(np.sqrt(np.sum(q * q))) < rad
-
-        new = refine_where(leaves, inside, lo, hi, root, maxl)
-        if len(new) > n_target * 1.25 and len(leaves) > n_target * 0.5:
+        # nearest point of each leaf's box to the sphere centre (unit cube)
+        w = 1.0 / (r * (2.0 ** L[:, 0]))
+        b0 = L[:, 1:] * w[:, None]
+        q = np.clip(cen[None, :], b0, b0 + w[:, None]) - cen[None, :]
+        hit = (np.sqrt((q * q).sum(1)) < rad) & (L[:, 0] < maxl)
+        n_new = L.shape[0] + 7 * int(hit.sum())
+        if n_new > n_target * 1.25 and L.shape[0] > n_target * 0.5:
             continue
-        leaves = balance(new, root, (True,) * 3)
+        kids = L[hit]
+        ch = np.repeat(kids, 8, axis=0)
+        o = np.tile(np.arange(8), kids.shape[0])
+        ch[:, 0] += 1
+        ch[:, 1] = 2 * ch[:, 1] + (o & 1)
+        ch[:, 2] = 2 * ch[:, 2] + ((o >> 1) & 1)
+        ch[:, 3] = 2 * ch[:, 3] + ((o >> 2) & 1)
+        L = np.concatenate([L[~hit], ch])
+    leaves = balance([tuple(int(v) for v in lf) for lf in L], root, (True,) * 3)
     leaves = as_leaf_array(morton_sort(leaves))
     prob = Problem("random_smooth", lo, hi, root, leaves, (BC_PERIODIC,) * 6, gamma=5.0 / 3.0,
                    limiter=LIM_MINMOD, cfl=0.8, nsteps=20)
-    x, y, z = cell_centres(lo, hi, root, leaves)
-    srho, _, a1, _ = _fourier(rng, x, y, z)
-    sp, _, a2, _ = _fourier(rng, x, y, z)
+    xs = _axis_coords(lo, hi, root, leaves)
+    srho, _, a1, _ = _fourier(rng, xs)
+    sp, _, a2, _ = _fourier(rng, xs)
     rho = 1.25 + 0.75 * srho / a1
     p = 1.25 + 0.75 * sp / a2
     u = []
     for _ in range(3):
-        s, _, a, _ = _fourier(rng, x, y, z)
+        s, _, a, _ = _fourier(rng, xs)
         u.append(s / a)
-    A = [_fourier(rng, x, y, z) for _ in range(3)]
+    A = [_fourier(rng, xs) for _ in range(3)]
     # B = curl A, normalised by a bound on each component's magnitude
     bx = A[2][1][1] - A[1][1][2]
     by = A[0][1][2] - A[2][1][0]
@@ -417,12 +444,22 @@ def random_smooth_grid(n_target, seed):
     return _finish(prob, W)
 
 
-def batched_grids(n_grids=64, seed=20250112, lo_blocks=64, hi_blocks=4096):
+def _smooth_grid_job(args):
+    return random_smooth_grid(*args)
+
+
+def batched_grids(n_grids=64, seed=20250112, lo_blocks=64, hi_blocks=4096, processes=None):
     """n_grids independent grids with log-uniform leaf targets in
-    [lo_blocks, hi_blocks]."""
+    [lo_blocks, hi_blocks].  Each grid depends only on its own seed, so the
+    result does not depend on `processes` (a spawn-context pool when > 1)."""
     rng = np.random.default_rng(seed)
     targets = np.exp(rng.uniform(math.log(lo_blocks), math.log(hi_blocks), size=n_grids)).astype(int)
-    return [random_smooth_grid(int(t), seed * 1000 + i) for i, t in enumerate(targets)]
+    jobs = [(int(t), seed * 1000 + i) for i, t in enumerate(targets)]
+    if processes and processes > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(processes) as pool:
+            return pool.map(_smooth_grid_job, jobs, chunksize=1)
+    return [random_smooth_grid(*j) for j in jobs]
 
 
 def _line_problem(name, axis, ncells, transverse_blocks=1, bc=BC_PERIODIC, length=1.0, gamma=5.0 / 3.0,

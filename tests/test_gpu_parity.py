@@ -287,3 +287,21 @@ def test_device_tensors_in_and_out(B):
         B.bats_get_state(s.h, 0, out)
         host = s.get_state(0)
     assert np.array_equal(out.cpu().numpy(), host)
+
+
+def test_graph_replay_of_many_steps(B):
+    """A 60-step graph, replayed twice, equals 120 eager steps (bitwise), and
+    eager runs report per-stage event timings."""
+    q = W.orszag_tang()
+    with B.Solver(q, precision=B.BATS_MIXED) as s:
+        s.set_state(0, q.U0)
+        s.step(120, 0.8)
+        ref = s.get_state(0)
+        ms = s.timings()
+        assert ms[B.BATS_PHASE_STAGE] > 0 and ms[B.BATS_PHASE_TOTAL] >= ms[B.BATS_PHASE_STAGE]
+    with B.Solver(q, precision=B.BATS_MIXED, persistent=1, use_graph=1) as s:
+        s.set_state(0, q.U0)
+        s.step(60, 0.8)
+        s.step(60, 0.8)
+        assert np.array_equal(s.get_state(0), ref)
+        assert s.launch_count() == 4 * 60
