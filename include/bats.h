@@ -182,6 +182,47 @@ int bats_get_launch_count(bats_t* h, long long* n);
  * the compiler's conversions.  Allocates and frees its own device buffers. */
 int bats_debug_check_conversions(const float* f, const double* d, int n, double* f2d_out, float* d2f_out);
 
+/* ---- stepping without device allocation --------------------------------
+ * No counterpart in the paper: an addition for callers that cannot allocate
+ * device memory when they step -- code whose device memory is owned by an
+ * external manager, or a runtime that forbids cudaMalloc after start-up.
+ * bats_create allocates the state, stage buffers and tables of a handle;
+ * bats_step_noalloc instead advances one grid held in the caller's own
+ * buffer, and keeps everything else it needs (a block-major copy of the
+ * state, the intermediate stage state, the block and level tables, the
+ * time-step and error words) in one fixed array in device memory that the
+ * library reserves when it is loaded, about 8 MB, held by every GPU that
+ * loads the library until the process exits.  It allocates nothing: no
+ * device memory and no host heap (the tables are built in about 80 KB of the
+ * caller's stack).
+ *
+ * Limits: at most BATS_NOALLOC_MAX_BLOCKS blocks, and the per-level block
+ * maps (sum over levels 0..max of the number of block positions,
+ * root[0]*root[1]*root[2]*8^level) at most BATS_NOALLOC_MAX_MAP_ENTRIES;
+ * larger grids are rejected with BATS_ERR_INVALID_ARG and a message.  FP64
+ * form only (phys->precision must be BATS_FP64, learned 0); the launch fields
+ * of phys are ignored.
+ *
+ * Arguments: grid, phys as for bats_create (one grid); U the state, host or
+ * device, n = 8 * 512 * n_leaves doubles in the layout above, read and then
+ * overwritten with the state after `steps` steps; cfl > 0 selects the CFL
+ * time step, otherwise the fixed dt > 0 is used; *t_out (nullable) receives
+ * the elapsed time; cuda_stream a cudaStream_t or NULL (legacy default
+ * stream); err/err_len (nullable) receive a message on failure.  Returns after
+ * synchronising the stream.
+ *
+ * The first call on a device (per process) looks up the device address of
+ * the array and sets the stage kernel's shared-memory limit; make that first
+ * call before any CUDA stream capture.  All calls share the one array, which
+ * keeps the previous call's contents (each call rewrites what it reads first
+ * and clears its counters), so calls whose GPU work overlaps -- from two
+ * threads, or on two streams without ordering -- race and corrupt each
+ * other's results: serialise them. */
+#define BATS_NOALLOC_MAX_BLOCKS 128
+#define BATS_NOALLOC_MAX_MAP_ENTRIES 16384
+int bats_step_noalloc(const bats_grid_desc* grid, const bats_physics* phys, double* U, size_t n, int steps,
+                      double cfl, double dt, double* t_out, void* cuda_stream, char* err, size_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

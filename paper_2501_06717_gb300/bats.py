@@ -99,6 +99,9 @@ def lib():
     L.bats_set_launch.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     L.bats_get_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     L.bats_debug_check_conversions.argtypes = [vp, vp, ctypes.c_int, vp, vp]
+    L.bats_step_noalloc.argtypes = [ctypes.POINTER(bats_grid_desc), ctypes.POINTER(bats_physics), dp,
+                                    ctypes.c_size_t, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                    ctypes.POINTER(ctypes.c_double), vp, ctypes.c_char_p, ctypes.c_size_t]
     _lib = L
     return L
 
@@ -262,6 +265,29 @@ def bats_debug_check_conversions(f, d):
     if rc != BATS_OK:
         raise BatsError(rc, "conversion check failed")
     return o1, o2
+
+
+BATS_NOALLOC_MAX_BLOCKS = 128
+BATS_NOALLOC_MAX_MAP_ENTRIES = 16384
+
+
+def bats_step_noalloc(problem, phys, U, steps, cfl=None, dt=None, stream=None):
+    """Advance one grid held in the caller's buffer U (numpy array or torch
+    tensor, host or device; overwritten) without any device allocation; see
+    include/bats.h.  Returns the elapsed time."""
+    g = _Grids([problem])
+    p, n = _ptr_and_size(U)
+    t = ctypes.c_double(0.0)
+    buf = ctypes.create_string_buffer(256)
+    s = None
+    if stream is not None:
+        s = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    rc = lib().bats_step_noalloc(g.arr, ctypes.byref(phys), p, n, int(steps),
+                                 float(cfl) if cfl else -1.0, float(dt) if dt else 0.0,
+                                 ctypes.byref(t), s, buf, len(buf))
+    if rc != BATS_OK:
+        raise BatsError(rc, buf.value.decode())
+    return t.value
 
 
 # --------------------------------------------------------------------------
