@@ -16,7 +16,7 @@ constexpr int NFACE = 576;     // faces per block per direction (9 x 8 x 8)
 constexpr int NGHOST = 768;    // face-slab ghost cells (6 x 2 x 64)
 constexpr int NTILE = 1280;    // interior + face-slab ghosts
 constexpr int MAXLEV = 14;
-constexpr int STAGE_THREADS = 576;
+constexpr int STAGE_THREADS = 384;  // two threads per grid line, three directions
 
 enum FaceType : int32_t { FACE_SAME = 0, FACE_COARSER = 1, FACE_FINER = 2, FACE_OUTFLOW = 3, FACE_INFLOW = 4 };
 enum B0Mode : int32_t { B0_NONE = 0, B0_UNIFORM = 1, B0_DIPOLE = 2, B0_LINEAR = 3 };

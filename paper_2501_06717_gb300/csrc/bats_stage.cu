@@ -285,6 +285,24 @@ __device__ __forceinline__ void phys_flux(const R W[8], const R B0[3], R gamma, 
     cf = fast_speed_n<R>(gamma, rho, p, B_0, B_1, B_2);
 }
 
+// minmod of two doubles by integer tests on the bit patterns: 0 unless both
+// are nonzero with the same sign, else the one of smaller magnitude (the
+// second on a tie).  The same selection as the floating-point definition,
+// without the FP64 comparison unit.
+__device__ __forceinline__ double minmod_d(double a, double b) {
+  long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+  unsigned long long ma = static_cast<unsigned long long>(ia) & 0x7fffffffffffffffull;
+  unsigned long long mb = static_cast<unsigned long long>(ib) & 0x7fffffffffffffffull;
+  bool same = ((ia ^ ib) >= 0) && ma != 0 && mb != 0;
+  long long r = ma < mb ? ia : ib;
+  return same ? __longlong_as_double(r) : 0.0;
+}
+// Validity tests on bit patterns: finite, and finite and > 0.
+__device__ __forceinline__ bool finite_d(double x) {
+  return (static_cast<unsigned>(__double2hiint(x)) & 0x7ff00000u) != 0x7ff00000u;
+}
+__device__ __forceinline__ bool positive_d(double x) { return __double_as_longlong(x) > 0 && finite_d(x); }
+
 // ---------------------------------------------------------------------------
 // Ghost fill by point location (copy / restriction / prolongation / boundary).
 
@@ -413,12 +431,94 @@ __device__ __noinline__ void ghost_value(const GhostCtx& cx, int lev, int g[3], 
     double sgn = (g[a] & 1) ? 0.25 : -0.25;
 #pragma unroll
     for (int v = 0; v < NV; v++) {
-      double s = minmod_(__dsub_rn(Vc[v], Vm[v]), __dsub_rn(Vp[v], Vc[v]));
+      double s = minmod_d(__dsub_rn(Vc[v], Vm[v]), __dsub_rn(Vp[v], Vc[v]));
       acc[v] = __dadd_rn(acc[v], sgn * s);
     }
   }
 #pragma unroll
   for (int v = 0; v < NV; v++) out[v] = acc[v];
+}
+
+// One variable of the mean of the 8 children (level lev+1) of cell g.
+__device__ __forceinline__ double restrict_v(const GhostCtx& cx, int lev, const int g[3], int v) {
+  int f[3] = {2 * g[0], 2 * g[1], 2 * g[2]};
+  int ll;
+  int leaf = locate(*cx.G, cx.levmap, lev + 1, f, ll);
+  if (leaf < 0 || ll != lev + 1) {
+    atomicOr(cx.err, ERR_BOUNDS);
+    return 0.0;
+  }
+  const BlockDev& B = cx.blocks[leaf];
+  int li = f[0] - B.bi * NC, lj = f[1] - B.bj * NC, lk = f[2] - B.bk * NC;
+  const double* q = cx.U + static_cast<int64_t>(leaf) * (NV * NCELL) + v * NCELL + (lk * NC + lj) * NC + li;
+  double c0 = q[0], c1 = q[1], c2 = q[NC], c3 = q[NC + 1];
+  double c4 = q[NC * NC], c5 = q[NC * NC + 1], c6 = q[NC * NC + NC], c7 = q[NC * NC + NC + 1];
+  double sum = __dadd_rn(__dadd_rn(__dadd_rn(c0, c1), __dadd_rn(c2, c3)),
+                         __dadd_rn(__dadd_rn(c4, c5), __dadd_rn(c6, c7)));
+  return 0.125 * sum;
+}
+// One variable of the copy or restriction at level lc (coarse sample).
+__device__ __forceinline__ double coarse_value_v(const GhostCtx& cx, int lc, int g0, int g1, int g2, int v) {
+  const GridDev& G = *cx.G;
+  int gc[3] = {g0, g1, g2};
+  if (bc_map(G, lc, gc)) return G.Uinflow[v];
+  int ll;
+  int leaf = locate(G, cx.levmap, lc, gc, ll);
+  if (leaf >= 0 && ll == lc) {
+    const BlockDev& B = cx.blocks[leaf];
+    int li = gc[0] - B.bi * NC, lj = gc[1] - B.bj * NC, lk = gc[2] - B.bk * NC;
+    return cx.U[static_cast<int64_t>(leaf) * (NV * NCELL) + v * NCELL + (lk * NC + lj) * NC + li];
+  }
+  if (leaf < 0) return restrict_v(cx, lc, gc, v);
+  atomicOr(cx.err, ERR_BOUNDS);  // two levels coarser: excluded by 2:1 balance
+  return 0.0;
+}
+
+// Prolongation of one variable v for the 2x2x2 fine ghost cells of a face
+// slab of face s that share coarse cell cc (0..15 over the face): the seven
+// coarse samples and three minmod slopes are computed once, and the eight
+// children are Vc + (+-1/4) sx + (+-1/4) sy + (+-1/4) sz summed x, then y,
+// then z (the partial sums are shared between children).  Results go to
+// scr[(local fine index in the slab) * 8 + v].
+__device__ __noinline__ void prolong_item(const GhostCtx& cx, const BlockDev& B, int s, int cc, int v, double* scr) {
+  const int d = s >> 1, side = s & 1;
+  const int ca = cc & 3, cb = cc >> 2;
+  const int lev = B.level;
+  // fine base cell (even coordinates) of the 2x2x2 group, global at level lev
+  const int n0 = side ? NC : -2;
+  int b0 = B.bi * NC + (d == 0 ? n0 : 2 * ca);
+  int b1 = B.bj * NC + (d == 1 ? n0 : (d == 0 ? 2 * ca : 2 * cb));
+  int b2 = B.bk * NC + (d == 2 ? n0 : 2 * cb);
+  const int c0 = b0 >> 1, c1 = b1 >> 1, c2 = b2 >> 1;
+  const double Vc = coarse_value_v(cx, lev - 1, c0, c1, c2, v);
+  double qx, qy, qz;
+  {
+    double m = coarse_value_v(cx, lev - 1, c0 - 1, c1, c2, v), p = coarse_value_v(cx, lev - 1, c0 + 1, c1, c2, v);
+    qx = 0.25 * minmod_d(__dsub_rn(Vc, m), __dsub_rn(p, Vc));
+  }
+  {
+    double m = coarse_value_v(cx, lev - 1, c0, c1 - 1, c2, v), p = coarse_value_v(cx, lev - 1, c0, c1 + 1, c2, v);
+    qy = 0.25 * minmod_d(__dsub_rn(Vc, m), __dsub_rn(p, Vc));
+  }
+  {
+    double m = coarse_value_v(cx, lev - 1, c0, c1, c2 - 1, v), p = coarse_value_v(cx, lev - 1, c0, c1, c2 + 1, v);
+    qz = 0.25 * minmod_d(__dsub_rn(Vc, m), __dsub_rn(p, Vc));
+  }
+  // even fine index -> -1/4, odd -> +1/4 along each axis
+  const double tx0 = __dsub_rn(Vc, qx), tx1 = __dadd_rn(Vc, qx);
+  const double t00 = __dsub_rn(tx0, qy), t01 = __dadd_rn(tx0, qy), t10 = __dsub_rn(tx1, qy), t11 = __dadd_rn(tx1, qy);
+#pragma unroll
+  for (int o = 0; o < 8; o++) {
+    const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
+    const double txy = ox ? (oy ? t11 : t10) : (oy ? t01 : t00);
+    const double val = oz ? __dadd_rn(txy, qz) : __dsub_rn(txy, qz);
+    // local index in the face slab: layer (normal), then the two transverse axes
+    const int on = d == 0 ? ox : (d == 1 ? oy : oz);
+    const int oa = d == 0 ? oy : ox;
+    const int ob = d == 2 ? oy : oz;
+    const int local = on + 2 * ((2 * ca + oa) + NC * (2 * cb + ob));
+    scr[local * NV + v] = val;
+  }
 }
 
 // Tile index of cell c (-2..9) along direction d at transverse (a, b).
@@ -482,22 +582,100 @@ __device__ __forceinline__ void fill_ghost(const StageArgs& a, const GhostCtx& c
   for (int v = 0; v < NV; v++) sT[v * NTILE + t] = w[v];
 }
 
+// All face-slab ghosts of block blk.  Faces whose neighbour is coarser are
+// filled by prolongation work items (one per coarse cell and variable, up to
+// three such faces per block) through the FP64 scratch `scr` (3 x 128 x 8
+// doubles); every other ghost cell is filled directly.  Ends with the tile
+// complete for the calling CTA after a __syncthreads (the caller's, for
+// blocks without coarser faces).
+template <bool MIXED, class R>
+__device__ __forceinline__ void fill_ghosts_block(const StageArgs& a, const GhostCtx& cx, const BlockDev& B, int blk,
+                                                  R* sT, double* scr, int tid, int nthr) {
+  unsigned cmask = 0;
+#pragma unroll
+  for (int f = 0; f < 6; f++) cmask |= (B.ftype[f] == FACE_COARSER ? 1u : 0u) << f;
+  const int ncoarse = __popc(cmask);
+  const int nheavy = ncoarse * 128;
+  for (int q = tid; q < nheavy + NGHOST; q += nthr) {
+    if (q < nheavy) {
+      const int slot = q >> 7, rem = q & 127;
+      unsigned m = cmask;
+      for (int k = 0; k < slot; k++) m &= m - 1;
+      const int sface = __ffs(m) - 1;
+      prolong_item(cx, B, sface, rem >> 3, rem & 7, scr + slot * 128 * NV);
+    } else {
+      const int g = q - nheavy;
+      if (!((cmask >> (g >> 7)) & 1u)) fill_ghost<MIXED, R>(a, cx, B, blk, g, sT);
+    }
+  }
+  if (ncoarse) {
+    __syncthreads();
+    for (int q = tid; q < nheavy; q += nthr) {
+      const int slot = q >> 7, local = q & 127;
+      unsigned m = cmask;
+      for (int k = 0; k < slot; k++) m &= m - 1;
+      const int sface = __ffs(m) - 1;
+      const double* u = scr + (slot * 128 + local) * NV;
+      double uu[8];
+#pragma unroll
+      for (int v = 0; v < NV; v++) uu[v] = u[v];
+      R w[8];
+      if constexpr (MIXED) {
+        prim_mixed(uu, a.ph.gm1f, w);
+      } else {
+#pragma unroll
+        for (int v = 0; v < NV; v++) w[v] = uu[v];
+      }
+      const int t = NCELL + sface * 128 + local;
+#pragma unroll
+      for (int v = 0; v < NV; v++) sT[v * NTILE + t] = w[v];
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // The fused stage kernel.
 
 template <bool MIXED>
 struct StageCfg {
   using R = typename std::conditional<MIXED, float, double>::type;
-  static constexpr int NFCOMP = 12;  // 8 fluxes, face-averaged B1n, B0 (3)
-  static constexpr size_t SMEM = sizeof(R) * (NV * NTILE + NFCOMP * NFACE);
+  static constexpr int NFC = 9;  // per face: 8 fluxes and the face-averaged normal B1
+  static constexpr size_t SMEM = sizeof(R) * (NV * NTILE + 3 * NFC * NFACE);
 };
 
-template <bool MIXED>
+// Load the 8 primitives of tile cell `idx` in the face frame (normal, t1, t2):
+// offsets o[v] already select the rotated component's column.
+template <class R>
+__device__ __forceinline__ void load_rot(const R* sT, const int o[8], int idx, R w[8]) {
+#pragma unroll
+  for (int v = 0; v < NV; v++) w[v] = sT[o[v] + idx];
+}
+
+// B0 at the centre of the face on the low side of cell (i, j, k) (block-local)
+// normal to axis d, or at the cell centre when d < 0.
+template <class R>
+__device__ __forceinline__ void b0_face(const PhysDev& ph, int d, int i, int j, int k, int gb0, int gb1, int gb2,
+                                        R lo0, R lo1, R lo2, R dx0, R dx1, R dx2, R B0[3]) {
+  R x[3];
+  x[0] = lo0 + (R(gb0 + i) + (d == 0 ? R(0) : R(0.5))) * dx0;
+  x[1] = lo1 + (R(gb1 + j) + (d == 1 ? R(0) : R(0.5))) * dx1;
+  x[2] = lo2 + (R(gb2 + k) + (d == 2 ? R(0) : R(0.5))) * dx2;
+  b0_at<R>(ph, x, B0);
+}
+
+// The fused stage.  Per block: (1) interior by TMA, face-slab ghosts by
+// threads; (2) FP64 form: primitives in place; (3) faces of all three
+// directions at once, two threads per grid line (faces 0-4 and 5-8), each
+// sliding a window along its line so that every cell is loaded and every
+// limited slope computed once; (4) per cell: flux differences x, y, z, the
+// sources, the update and (last stage) the CFL bound.
+template <bool MIXED, int LIM, bool HAS_B0>
 __global__ void __launch_bounds__(STAGE_THREADS, MIXED ? 2 : 1) k_stage(const StageArgs a) {
   using R = typename StageCfg<MIXED>::R;
+  constexpr int NFC = StageCfg<MIXED>::NFC;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   R* sT = reinterpret_cast<R*>(smem_raw);       // [8][1280] tile
-  R* sF = sT + NV * NTILE;                       // [12][576] face values
+  R* sF = sT + NV * NTILE;                       // [3][9][576] face values
   __shared__ uint64_t bar;
   __shared__ R sred[STAGE_THREADS / 32];
 
@@ -506,7 +684,27 @@ __global__ void __launch_bounds__(STAGE_THREADS, MIXED ? 2 : 1) k_stage(const St
   R gamma, inv_gm1;
   if constexpr (MIXED) { gamma = ph.gammaf; inv_gm1 = ph.inv_gm1f; }
   else { gamma = ph.gamma; inv_gm1 = ph.inv_gm1; }
-  const bool has_b0 = ph.b0 != B0_NONE;
+  constexpr bool has_b0 = HAS_B0;
+
+  // this thread's line in the face phase
+  const int fd = tid >> 7;                      // direction 0..2
+  const int fline = (tid & 127) >> 1, fhalf = tid & 1;
+  const int fta = fline & 7, ftb = fline >> 3;  // transverse coordinates (increasing axis order)
+  const int fd1 = fd == 2 ? 0 : fd + 1, fd2 = fd == 0 ? 2 : fd - 1;
+  const int fstride = fd == 0 ? 1 : (fd == 1 ? NC : NC * NC);
+  const int fibase = fd == 0 ? (ftb * NC + fta) * NC : (fd == 1 ? ftb * NC * NC + fta : ftb * NC + fta);
+  const int flo = NCELL + 2 * fd * 128 + 2 * (fta + NC * ftb), fhi = flo + 128;
+  int rot[8];
+  rot[0] = 0;
+  rot[1] = (1 + fd) * NTILE;
+  rot[2] = (1 + fd1) * NTILE;
+  rot[3] = (1 + fd2) * NTILE;
+  rot[4] = (4 + fd) * NTILE;
+  rot[5] = (4 + fd1) * NTILE;
+  rot[6] = (4 + fd2) * NTILE;
+  rot[7] = 7 * NTILE;
+  // flux store columns (un-rotated)
+  R* const fcol = sF + fd * NFC * NFACE;
 
   if (tid == 0) mbar_init(&bar, 1);
   __syncthreads();
@@ -529,12 +727,12 @@ __global__ void __launch_bounds__(STAGE_THREADS, MIXED ? 2 : 1) k_stage(const St
 #pragma unroll
         for (int v = 0; v < NV; v++) bulk_g2s(sT + v * NTILE, src + v * NCELL, NCELL * sizeof(R), &bar);
       }
-      for (int q = tid; q < NGHOST; q += STAGE_THREADS) fill_ghost<MIXED, R>(a, cx, B, blk, q, sT);
+      fill_ghosts_block<MIXED, R>(a, cx, B, blk, sT, reinterpret_cast<double*>(sF), tid, STAGE_THREADS);
       if (!mbar_wait_bounded(&bar, parity, a.err)) mbar_wait_bounded(&bar, parity, a.err);
       parity ^= 1u;
       __syncthreads();
 
-      // 2. FP64 path: primitives in place over the whole tile
+      // 2. FP64 form: primitives in place over the whole tile
       if constexpr (!MIXED) {
         for (int c = tid; c < NTILE; c += STAGE_THREADS) {
           double U[8], W[8];
@@ -562,108 +760,85 @@ __global__ void __launch_bounds__(STAGE_THREADS, MIXED ? 2 : 1) k_stage(const St
       }
       const int gb0 = B.bi * NC, gb1 = B.bj * NC, gb2 = B.bk * NC;
 
-      // per-cell accumulators (threads < 512 own cell tid)
-      const int ci = tid & 7, cj = (tid >> 3) & 7, ck = tid >> 6;
-      R res[8];
-      R divb = R(0), divb0 = R(0), curl0 = R(0), curl1 = R(0), curl2 = R(0);
-#pragma unroll
-      for (int v = 0; v < NV; v++) res[v] = R(0);
-
-#pragma unroll 1
-      for (int d = 0; d < 3; d++) {
-        // 3. faces of direction d: reconstruction + Rusanov flux in the frame
-        //    (normal, t1, t2) = (d, d+1, d+2 mod 3)
+      // 3. faces: reconstruction + Rusanov flux in the frame (d, d+1, d+2)
+      {
+        auto cidx = [&](int c) { return c < 0 ? flo + (c + 2) : (c >= NC ? fhi + (c - NC) : fibase + c * fstride); };
+        const int f0 = fhalf ? 5 : 0, nf = fhalf ? 4 : 5;
+        R Wm1[8], W0[8], sm1[8];
         {
-          const int t = tid;
-          int f, ta, tb;
-          if (d == 0) { f = t % 9; ta = (t / 9) & 7; tb = t / 72; }
-          else if (d == 1) { ta = t & 7; f = (t >> 3) % 9; tb = t / 72; }
-          else { ta = t & 7; tb = (t >> 3) & 7; f = t >> 6; }
-          const int d1 = d == 2 ? 0 : d + 1, d2 = d == 0 ? 2 : d - 1;
-          const int i0 = tile_index(d, f - 2, ta, tb), i1 = tile_index(d, f - 1, ta, tb);
-          const int i2 = tile_index(d, f, ta, tb), i3 = tile_index(d, f + 1, ta, tb);
-          // source variable of rotated component v
-          R WL[8], WR[8];
+          R Wm2[8];
+          load_rot<R>(sT, rot, cidx(f0 - 2), Wm2);
+          load_rot<R>(sT, rot, cidx(f0 - 1), Wm1);
+          load_rot<R>(sT, rot, cidx(f0), W0);
+#pragma unroll
+          for (int v = 0; v < NV; v++) sm1[v] = limit_<R>(LIM, Wm1[v] - Wm2[v], W0[v] - Wm1[v]);
+        }
+#pragma unroll 1
+        for (int k = 0; k < nf; k++) {
+          const int f = f0 + k;
+          R Wp[8], WL[8], WR[8];
+          load_rot<R>(sT, rot, cidx(f + 1), Wp);
 #pragma unroll
           for (int v = 0; v < NV; v++) {
-            int sv = v;
-            if (v >= 1 && v <= 3) sv = 1 + (v == 1 ? d : v == 2 ? d1 : d2);
-            if (v >= 4 && v <= 6) sv = 4 + (v == 4 ? d : v == 5 ? d1 : d2);
-            const R* col = sT + sv * NTILE;
-            R w0 = col[i0], w1 = col[i1], w2 = col[i2], w3 = col[i3];
-            R sl = limit_<R>(ph.limiter, w1 - w0, w2 - w1);
-            R sr = limit_<R>(ph.limiter, w2 - w1, w3 - w2);
-            WL[v] = w1 + R(0.5) * sl;
-            WR[v] = w2 - R(0.5) * sr;
+            R s0 = limit_<R>(LIM, W0[v] - Wm1[v], Wp[v] - W0[v]);
+            WL[v] = Wm1[v] + R(0.5) * sm1[v];
+            WR[v] = W0[v] - R(0.5) * s0;
+            sm1[v] = s0;
+            Wm1[v] = W0[v];
+            W0[v] = Wp[v];
           }
           R B0f[3] = {R(0), R(0), R(0)}, B0r[3];
-          if (has_b0) {
-            // face centre: index f along d, (ta, tb) on the other two axes in
-            // increasing order
-            const int cc0 = d == 0 ? f : ta, cc1 = d == 1 ? f : (d == 0 ? ta : tb), cc2 = d == 2 ? f : tb;
-            R xf[3];
-            xf[0] = lor0 + (R(gb0 + cc0) + (d == 0 ? R(0) : R(0.5))) * dxr0;
-            xf[1] = lor1 + (R(gb1 + cc1) + (d == 1 ? R(0) : R(0.5))) * dxr1;
-            xf[2] = lor2 + (R(gb2 + cc2) + (d == 2 ? R(0) : R(0.5))) * dxr2;
-            b0_at<R>(ph, xf, B0f);
+          if constexpr (HAS_B0) {
+            const int ci_ = fd == 0 ? f : fta, cj_ = fd == 1 ? f : (fd == 0 ? fta : ftb), ck_ = fd == 2 ? f : ftb;
+            b0_face<R>(ph, fd, ci_, cj_, ck_, gb0, gb1, gb2, lor0, lor1, lor2, dxr0, dxr1, dxr2, B0f);
           }
-          B0r[0] = d == 0 ? B0f[0] : (d == 1 ? B0f[1] : B0f[2]);
-          B0r[1] = d1 == 0 ? B0f[0] : (d1 == 1 ? B0f[1] : B0f[2]);
-          B0r[2] = d2 == 0 ? B0f[0] : (d2 == 1 ? B0f[1] : B0f[2]);
+          B0r[0] = fd == 0 ? B0f[0] : (fd == 1 ? B0f[1] : B0f[2]);
+          B0r[1] = fd1 == 0 ? B0f[0] : (fd1 == 1 ? B0f[1] : B0f[2]);
+          B0r[2] = fd2 == 0 ? B0f[0] : (fd2 == 1 ? B0f[1] : B0f[2]);
           R FL[8], UL[8], FR[8], UR[8], unL, unR, cfL, cfR;
           phys_flux<R>(WL, B0r, gamma, inv_gm1, FL, UL, unL, cfL);
           phys_flux<R>(WR, B0r, gamma, inv_gm1, FR, UR, unR, cfR);
           R aL = Ops<R>::abs_(unL) + cfL, aR = Ops<R>::abs_(unR) + cfR;
           R cmax = aL > aR ? aL : aR;
+          const int fi = fline * 9 + f;
           R Fr[8];
 #pragma unroll
           for (int v = 0; v < NV; v++) Fr[v] = R(0.5) * (FL[v] + FR[v]) - R(0.5) * cmax * (UR[v] - UL[v]);
-          // store un-rotated
-          sF[0 * NFACE + t] = Fr[0];
-          sF[(1 + d) * NFACE + t] = Fr[1];
-          sF[(1 + d1) * NFACE + t] = Fr[2];
-          sF[(1 + d2) * NFACE + t] = Fr[3];
-          sF[(4 + d) * NFACE + t] = Fr[4];
-          sF[(4 + d1) * NFACE + t] = Fr[5];
-          sF[(4 + d2) * NFACE + t] = Fr[6];
-          sF[7 * NFACE + t] = Fr[7];
-          sF[8 * NFACE + t] = R(0.5) * (WL[4] + WR[4]);
-          if (has_b0) {
-            sF[9 * NFACE + t] = B0f[0];
-            sF[10 * NFACE + t] = B0f[1];
-            sF[11 * NFACE + t] = B0f[2];
-          }
+          fcol[0 * NFACE + fi] = Fr[0];
+          fcol[(1 + fd) * NFACE + fi] = Fr[1];
+          fcol[(1 + fd1) * NFACE + fi] = Fr[2];
+          fcol[(1 + fd2) * NFACE + fi] = Fr[3];
+          fcol[(4 + fd) * NFACE + fi] = Fr[4];
+          fcol[(4 + fd1) * NFACE + fi] = Fr[5];
+          fcol[(4 + fd2) * NFACE + fi] = Fr[6];
+          fcol[7 * NFACE + fi] = Fr[7];
+          fcol[8 * NFACE + fi] = R(0.5) * (WL[4] + WR[4]);
         }
-        __syncthreads();
-        // 4. flux differences into the cells
-        if (tid < NCELL) {
-          int tl, th;
-          if (d == 0) { tl = (ck * 8 + cj) * 9 + ci; th = tl + 1; }
-          else if (d == 1) { tl = (ck * 9 + cj) * 8 + ci; th = tl + 8; }
-          else { tl = (ck * 8 + cj) * 8 + ci; th = tl + 64; }
-          const R id = d == 0 ? idx0 : (d == 1 ? idx1 : idx2);
-#pragma unroll
-          for (int v = 0; v < NV; v++) {
-            R df = (sF[v * NFACE + th] - sF[v * NFACE + tl]) * id;
-            res[v] = d == 0 ? -df : res[v] - df;
-          }
-          divb = divb + (sF[8 * NFACE + th] - sF[8 * NFACE + tl]) * id;
-          if (has_b0) {
-            R dbx = (sF[9 * NFACE + th] - sF[9 * NFACE + tl]) * id;
-            R dby = (sF[10 * NFACE + th] - sF[10 * NFACE + tl]) * id;
-            R dbz = (sF[11 * NFACE + th] - sF[11 * NFACE + tl]) * id;
-            if (d == 0) { divb0 = dbx; curl2 = dby; curl1 = -dbz; }
-            else if (d == 1) { divb0 = divb0 + dby; curl0 = dbz; curl2 = curl2 - dbx; }
-            else { divb0 = divb0 + dbz; curl1 = curl1 + dbx; curl0 = curl0 - dby; }
-          }
-        }
-        __syncthreads();
       }
+      __syncthreads();
 
-      // 5. sources and update of the owned cell
+      // 4. per cell: flux differences, sources, update, CFL bound
       R smax_loc = R(0);
-      if (tid < NCELL) {
-        const int c = tid;
+      for (int c = tid; c < NCELL; c += STAGE_THREADS) {
+        const int ci = c & 7, cj = (c >> 3) & 7, ck = c >> 6;
+        // face indices (line * 9 + position) of the low faces in x, y, z
+        const int tx = (ck * NC + cj) * 9 + ci;
+        const int ty = (ck * NC + ci) * 9 + cj;
+        const int tz = (cj * NC + ci) * 9 + ck;
+        const R* Fx = sF;
+        const R* Fy = sF + NFC * NFACE;
+        const R* Fz = sF + 2 * NFC * NFACE;
+        R res[8];
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+          R r = -((Fx[v * NFACE + tx + 1] - Fx[v * NFACE + tx]) * idx0);
+          r = r - (Fy[v * NFACE + ty + 1] - Fy[v * NFACE + ty]) * idx1;
+          r = r - (Fz[v * NFACE + tz + 1] - Fz[v * NFACE + tz]) * idx2;
+          res[v] = r;
+        }
+        const R divb = ((Fx[8 * NFACE + tx + 1] - Fx[8 * NFACE + tx]) * idx0 +
+                        (Fy[8 * NFACE + ty + 1] - Fy[8 * NFACE + ty]) * idx1) +
+                       (Fz[8 * NFACE + tz + 1] - Fz[8 * NFACE + tz]) * idx2;
         bool in_body = false;
         if (B.body) {  // FP64, the same centre formula as the host and the oracle
           double x = G.lo[0] + ((static_cast<double>(gb0) + ci) + 0.5) * G.dx[lev][0];
@@ -675,12 +850,8 @@ __global__ void __launch_bounds__(STAGE_THREADS, MIXED ? 2 : 1) k_stage(const St
 #pragma unroll
         for (int v = 0; v < NV; v++) Wc[v] = sT[v * NTILE + c];
         R B0c[3] = {R(0), R(0), R(0)};
-        if (has_b0) {
-          R xr[3] = {lor0 + (R(gb0 + ci) + R(0.5)) * dxr0, lor1 + (R(gb1 + cj) + R(0.5)) * dxr1,
-                     lor2 + (R(gb2 + ck) + R(0.5)) * dxr2};
-          b0_at<R>(ph, xr, B0c);
-        }
         R S[8] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+        if constexpr (HAS_B0) b0_face<R>(ph, -1, ci, cj, ck, gb0, gb1, gb2, lor0, lor1, lor2, dxr0, dxr1, dxr2, B0c);
         if (ph.powell) {
           R ub1 = Wc[1] * Wc[4] + Wc[2] * Wc[5] + Wc[3] * Wc[6];
 #pragma unroll
@@ -690,11 +861,24 @@ __global__ void __launch_bounds__(STAGE_THREADS, MIXED ? 2 : 1) k_stage(const St
           }
           S[7] = -divb * ub1;
         }
-        if (has_b0) {
+        if constexpr (HAS_B0) {
+          // split-field correction from the face-centre B0 of the six faces:
+          // S_m += -B1 (div B0)_h + B1 x (curl B0)_h
+          R xm[3], xp[3], ym[3], yp[3], zm[3], zp[3];
+          b0_face<R>(ph, 0, ci, cj, ck, gb0, gb1, gb2, lor0, lor1, lor2, dxr0, dxr1, dxr2, xm);
+          b0_face<R>(ph, 0, ci + 1, cj, ck, gb0, gb1, gb2, lor0, lor1, lor2, dxr0, dxr1, dxr2, xp);
+          b0_face<R>(ph, 1, ci, cj, ck, gb0, gb1, gb2, lor0, lor1, lor2, dxr0, dxr1, dxr2, ym);
+          b0_face<R>(ph, 1, ci, cj + 1, ck, gb0, gb1, gb2, lor0, lor1, lor2, dxr0, dxr1, dxr2, yp);
+          b0_face<R>(ph, 2, ci, cj, ck, gb0, gb1, gb2, lor0, lor1, lor2, dxr0, dxr1, dxr2, zm);
+          b0_face<R>(ph, 2, ci, cj, ck + 1, gb0, gb1, gb2, lor0, lor1, lor2, dxr0, dxr1, dxr2, zp);
+          R divb0 = ((xp[0] - xm[0]) * idx0 + (yp[1] - ym[1]) * idx1) + (zp[2] - zm[2]) * idx2;
+          R cu0 = (yp[2] - ym[2]) * idx1 - (zp[1] - zm[1]) * idx2;
+          R cu1 = (zp[0] - zm[0]) * idx2 - (xp[2] - xm[2]) * idx0;
+          R cu2 = (xp[1] - xm[1]) * idx0 - (yp[0] - ym[0]) * idx1;
           R b1x = Wc[4], b1y = Wc[5], b1z = Wc[6];
-          S[1] = (S[1] - b1x * divb0) + (b1y * curl2 - b1z * curl1);
-          S[2] = (S[2] - b1y * divb0) + (b1z * curl0 - b1x * curl2);
-          S[3] = (S[3] - b1z * divb0) + (b1x * curl1 - b1y * curl0);
+          S[1] = (S[1] - b1x * divb0) + (b1y * cu2 - b1z * cu1);
+          S[2] = (S[2] - b1y * divb0) + (b1z * cu0 - b1x * cu2);
+          S[3] = (S[3] - b1z * divb0) + (b1x * cu1 - b1y * cu0);
         }
         const double cdt = a.beta * a.dt[B.grid];
         const int64_t base = static_cast<int64_t>(blk) * (NV * NCELL) + c;
@@ -713,26 +897,25 @@ __global__ void __launch_bounds__(STAGE_THREADS, MIXED ? 2 : 1) k_stage(const St
           if (a.kind == 2) o = rd;  // residual only (debug view)
           o = in_body ? (a.kind == 2 ? 0.0 : G.Ubody[v]) : o;
           Uo[v] = o;
-          bad |= !(o == o) || isinf(o);
+          bad |= !finite_d(o);
         }
-        if (a.kind != 2) bad |= !(Uo[0] > 0.0);
+        if (a.kind != 2) bad |= !positive_d(Uo[0]);
         R Wn[8];
-        bool need_w = MIXED || a.last;
+        const bool need_w = MIXED || a.last;
         if (need_w && a.kind != 2) {
           if constexpr (MIXED) {
             double p64;
             prim_mixed(Uo, ph.gm1f, Wn, &p64);
-            bad |= !(p64 > 0.0);
+            bad |= !positive_d(p64);
           } else {
             prim64(Uo, ph.gm1, Wn);
-            bad |= !(Wn[7] > 0.0);
+            bad |= !positive_d(Wn[7]);
           }
         }
         if (bad && !in_body && a.kind != 2) {
           atomicOr(&a.err[0], ERR_NONPHYSICAL);
           atomicMin(&a.err[1], blk);
         }
-        // outputs
         const bool write_u = !MIXED || a.last || a.write_u_all || B.need_u;
         if (write_u || a.kind == 2) {
 #pragma unroll
@@ -747,20 +930,20 @@ __global__ void __launch_bounds__(STAGE_THREADS, MIXED ? 2 : 1) k_stage(const St
         // CFL bound of the new state: sum_d (|u_d| + c_f,d) / dx_d
         if (a.last && !in_body && a.kind != 2) {
           R Bt[3] = {B0c[0] + Wn[4], B0c[1] + Wn[5], B0c[2] + Wn[6]};
-          R s = R(0);
+          R sacc = R(0);
 #pragma unroll
           for (int e = 0; e < 3; e++) {
             R bn = Bt[e], bt1 = Bt[(e + 1) % 3], bt2 = Bt[(e + 2) % 3];
             R cf;
             if constexpr (MIXED) {
               cf = fast_speed_n<R>(gamma, Wn[0], Wn[7], bn, bt1, bt2);
-              s = s + (Ops<R>::abs_(Wn[1 + e]) + cf) * (e == 0 ? idx0 : (e == 1 ? idx1 : idx2));
+              sacc = sacc + (Ops<R>::abs_(Wn[1 + e]) + cf) * (e == 0 ? idx0 : (e == 1 ? idx1 : idx2));
             } else {
               cf = fast_speed_exact(ph.gamma, Wn[0], Wn[7], bn, bt1, bt2);
-              s = s + (Ops<R>::abs_(Wn[1 + e]) + cf) / (e == 0 ? dxr0 : (e == 1 ? dxr1 : dxr2));
+              sacc = sacc + (Ops<R>::abs_(Wn[1 + e]) + cf) / (e == 0 ? dxr0 : (e == 1 ? dxr1 : dxr2));
             }
           }
-          smax_loc = s;
+          smax_loc = sacc > smax_loc ? sacc : smax_loc;
         }
       }
       if (a.last && a.kind != 2) {
@@ -785,7 +968,6 @@ __global__ void __launch_bounds__(STAGE_THREADS, MIXED ? 2 : 1) k_stage(const St
     }
   }
 }
-
 
 // ---------------------------------------------------------------------------
 // Small kernels.
@@ -921,7 +1103,7 @@ __global__ void k_debug_fill(const StageArgs a, int b0, int nb, double* T) {
   GhostCtx cx{&a.grids[B.grid], a.blocks, a.levmap, a.Uin, a.err};
   for (int e = threadIdx.x; e < NV * NCELL; e += blockDim.x)
     sT[(e / NCELL) * NTILE + (e % NCELL)] = a.Uin[static_cast<int64_t>(blk) * NV * NCELL + e];
-  for (int q = threadIdx.x; q < NGHOST; q += blockDim.x) fill_ghost<false, double>(a, cx, B, blk, q, sT);
+  fill_ghosts_block<false, double>(a, cx, B, blk, sT, sT + NV * NTILE, threadIdx.x, blockDim.x);
   __syncthreads();
   const int tile = 12 * 12 * 12;
   for (int e = threadIdx.x; e < tile; e += blockDim.x) {
@@ -955,25 +1137,39 @@ size_t stage_smem_bytes(bool mixed) {
   return mixed ? StageCfg<true>::SMEM : StageCfg<false>::SMEM;
 }
 
+using StageFn = void (*)(const StageArgs);
+template <bool MIXED>
+StageFn stage_fn(int lim, bool b0) {
+  if (lim == 1) return b0 ? k_stage<MIXED, 1, true> : k_stage<MIXED, 1, false>;
+  return b0 ? k_stage<MIXED, 0, true> : k_stage<MIXED, 0, false>;
+}
+
 cudaError_t stage_setup(int occ[2]) {
-  cudaError_t e = cudaFuncSetAttribute(k_stage<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(StageCfg<false>::SMEM));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_stage<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(StageCfg<true>::SMEM));
+  cudaError_t e = cudaSuccess;
+  for (int lim = 0; lim < 2 && e == cudaSuccess; lim++)
+    for (int b0 = 0; b0 < 2 && e == cudaSuccess; b0++) {
+      e = cudaFuncSetAttribute(stage_fn<false>(lim, b0), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               static_cast<int>(StageCfg<false>::SMEM));
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(stage_fn<true>(lim, b0), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(StageCfg<true>::SMEM));
+    }
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_debug_fill, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(sizeof(double) * NV * NTILE));
+                             static_cast<int>(sizeof(double) * (NV * NTILE + 3 * 128 * NV)));
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], k_stage<false>, STAGE_THREADS, StageCfg<false>::SMEM);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], stage_fn<false>(0, false), STAGE_THREADS,
+                                                      StageCfg<false>::SMEM);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], k_stage<true>, STAGE_THREADS, StageCfg<true>::SMEM);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], stage_fn<true>(0, false), STAGE_THREADS,
+                                                      StageCfg<true>::SMEM);
   return e;
 }
 
 cudaError_t launch_stage_kernel(bool mixed, int grid, cudaStream_t st, const StageArgs& a) {
-  if (mixed) k_stage<true><<<grid, STAGE_THREADS, StageCfg<true>::SMEM, st>>>(a);
-  else k_stage<false><<<grid, STAGE_THREADS, StageCfg<false>::SMEM, st>>>(a);
+  const bool b0 = a.ph.b0 != B0_NONE;
+  if (mixed) stage_fn<true>(a.ph.limiter, b0)<<<grid, STAGE_THREADS, StageCfg<true>::SMEM, st>>>(a);
+  else stage_fn<false>(a.ph.limiter, b0)<<<grid, STAGE_THREADS, StageCfg<false>::SMEM, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -1007,7 +1203,7 @@ cudaError_t launch_dt(int ngrids, int mode, double cfl, double fixed_dt, double*
   return cudaGetLastError();
 }
 cudaError_t launch_debug_fill(const StageArgs& a, int b0, int nb, double* T, cudaStream_t st) {
-  k_debug_fill<<<nb, 256, sizeof(double) * NV * NTILE, st>>>(a, b0, nb, T);
+  k_debug_fill<<<nb, 256, sizeof(double) * (NV * NTILE + 3 * 128 * NV), st>>>(a, b0, nb, T);
   return cudaGetLastError();
 }
 cudaError_t launch_check_conversions(const float* f, const double* d, int n, double* f2d_out, float* d2f_out) {
