@@ -496,6 +496,89 @@ void or_mlp_forward(const double* P, const double x[MLP_IN], double h1[MLP_H], d
   }
 }
 
+/* Derivative of the tanh-form GELU. */
+static double gelu_tanh_grad(double x) {
+  const double k = 0.7978845608028654;
+  double u = k * (x + 0.044715 * x * x * x);
+  double t = tanh(u);
+  double du = k * (1.0 + 3.0 * 0.044715 * x * x);
+  return 0.5 * (1.0 + t) + 0.5 * x * (1.0 - t * t) * du;
+}
+
+double or_gelu(double x) { return gelu_tanh(x); }
+
+/* Mean-squared-error loss over n samples and its gradient by backpropagation
+ * (chain rule through the three layers):
+ *   L = (1/(8n)) sum_s sum_o (y_o(x_s) - t_so)^2.
+ * X is n x 40, T is n x 8; grad has MLP_NPARAM entries in the parameter
+ * layout (W1, b1, W2, b2, W3, b3).  Returns L. */
+double or_mlp_loss_grad(const double* P, const double* X, const double* T, long n, double* grad) {
+  const double* W1 = P;
+  const double* b1 = W1 + MLP_H * MLP_IN;
+  const double* W2 = b1 + MLP_H;
+  const double* b2 = W2 + MLP_H * MLP_H;
+  const double* W3 = b2 + MLP_H;
+  const double* b3 = W3 + MLP_OUT * MLP_H;
+  double* gW1 = grad;
+  double* gb1 = gW1 + MLP_H * MLP_IN;
+  double* gW2 = gb1 + MLP_H;
+  double* gb2 = gW2 + MLP_H * MLP_H;
+  double* gW3 = gb2 + MLP_H;
+  double* gb3 = gW3 + MLP_OUT * MLP_H;
+  memset(grad, 0, sizeof(double) * MLP_NPARAM);
+  double loss = 0.0;
+  for (long s = 0; s < n; s++) {
+    const double* x = X + s * MLP_IN;
+    const double* t = T + s * MLP_OUT;
+    double z1[MLP_H], h1[MLP_H], z2[MLP_H], h2[MLP_H], y[MLP_OUT];
+    for (int o = 0; o < MLP_H; o++) {
+      double a = 0.0;
+      for (int i = 0; i < MLP_IN; i++) a += W1[o * MLP_IN + i] * x[i];
+      z1[o] = a + b1[o];
+      h1[o] = gelu_tanh(z1[o]);
+    }
+    for (int o = 0; o < MLP_H; o++) {
+      double a = 0.0;
+      for (int i = 0; i < MLP_H; i++) a += W2[o * MLP_H + i] * h1[i];
+      z2[o] = a + b2[o];
+      h2[o] = gelu_tanh(z2[o]);
+    }
+    double dy[MLP_OUT];
+    for (int o = 0; o < MLP_OUT; o++) {
+      double a = 0.0;
+      for (int i = 0; i < MLP_H; i++) a += W3[o * MLP_H + i] * h2[i];
+      y[o] = a + b3[o];
+      double e = y[o] - t[o];
+      loss += e * e;
+      dy[o] = 2.0 * e / (8.0 * (double)n);
+    }
+    double dh2[MLP_H], dz2[MLP_H], dh1[MLP_H], dz1[MLP_H];
+    for (int i = 0; i < MLP_H; i++) dh2[i] = 0.0;
+    for (int o = 0; o < MLP_OUT; o++) {
+      gb3[o] += dy[o];
+      for (int i = 0; i < MLP_H; i++) {
+        gW3[o * MLP_H + i] += dy[o] * h2[i];
+        dh2[i] += dy[o] * W3[o * MLP_H + i];
+      }
+    }
+    for (int o = 0; o < MLP_H; o++) dz2[o] = dh2[o] * gelu_tanh_grad(z2[o]);
+    for (int i = 0; i < MLP_H; i++) dh1[i] = 0.0;
+    for (int o = 0; o < MLP_H; o++) {
+      gb2[o] += dz2[o];
+      for (int i = 0; i < MLP_H; i++) {
+        gW2[o * MLP_H + i] += dz2[o] * h1[i];
+        dh1[i] += dz2[o] * W2[o * MLP_H + i];
+      }
+    }
+    for (int o = 0; o < MLP_H; o++) dz1[o] = dh1[o] * gelu_tanh_grad(z1[o]);
+    for (int o = 0; o < MLP_H; o++) {
+      gb1[o] += dz1[o];
+      for (int i = 0; i < MLP_IN; i++) gW1[o * MLP_IN + i] += dz1[o] * x[i];
+    }
+  }
+  return loss / (8.0 * (double)n);
+}
+
 /* Output scale per rotated flux component (flux units of each variable):
  * mass rho c, momentum rho c^2, B sqrt(rho) c^2, energy rho c^3. */
 void or_mlp_out_scale(double rho_ref, double c_ref, double sc[MLP_OUT]) {

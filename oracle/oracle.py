@@ -94,6 +94,10 @@ def lib():
         _lib.or_set_threads.argtypes = [ctypes.c_int]
         _lib.or_mlp_forward.argtypes = [dp, dp, dp, dp, dp]
         _lib.or_mlp_features.argtypes = [ctypes.c_int, dp, dp, dp, ctypes.c_double, dp]
+        _lib.or_mlp_loss_grad.argtypes = [dp, dp, dp, ctypes.c_long, dp]
+        _lib.or_mlp_loss_grad.restype = ctypes.c_double
+        _lib.or_gelu.argtypes = [ctypes.c_double]
+        _lib.or_gelu.restype = ctypes.c_double
     return _lib
 
 
@@ -267,3 +271,27 @@ def mlp_forward(params, x):
     y = np.zeros(MLP_OUT)
     lib().or_mlp_forward(_dp(P), _dp(x), _dp(h1), _dp(h2), _dp(y))
     return h1, h2, y
+
+
+def mlp_loss_grad(params, X, T):
+    """MSE loss (1/(8n)) sum (y - t)^2 and its gradient (FP64 backprop)."""
+    P = np.ascontiguousarray(params, dtype=np.float64).reshape(MLP_NPARAM)
+    X = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, MLP_IN)
+    T = np.ascontiguousarray(T, dtype=np.float64).reshape(-1, MLP_OUT)
+    g = np.zeros(MLP_NPARAM)
+    loss = lib().or_mlp_loss_grad(_dp(P), _dp(X), _dp(T), X.shape[0], _dp(g))
+    return loss, g
+
+
+def gelu(x):
+    return lib().or_gelu(float(x))
+
+
+def mlp_features(direction, Wstencil, WL, WR, cmax):
+    """The 40 normalised inputs of one face (see oracle.c)."""
+    Ws = np.ascontiguousarray(Wstencil, dtype=np.float64).reshape(32)
+    WL = np.ascontiguousarray(WL, dtype=np.float64).reshape(8)
+    WR = np.ascontiguousarray(WR, dtype=np.float64).reshape(8)
+    x = np.zeros(MLP_IN)
+    lib().or_mlp_features(int(direction), _dp(Ws), _dp(WL), _dp(WR), float(cmax), _dp(x))
+    return x

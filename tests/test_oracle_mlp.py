@@ -1,0 +1,132 @@
+"""Pins of the oracle's learned flux correction (MLP 40 -> 64 -> 64 -> 8).
+
+Backprop against central finite differences, GELU identities, the exact
+reduction to plain Rusanov with zero weights, and the invariance of the
+normalised inputs (and the matching scaling of the correction) under the
+similarity scaling of ideal MHD.  CPU only.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2501_06717_gb300 import workloads as W
+
+
+def _params(seed, scale=0.3):
+    rng = np.random.default_rng(seed)
+    return rng.normal(0, scale, size=O.MLP_NPARAM)
+
+
+def test_gelu_identities():
+    """tanh-form GELU (Hendrycks & Gimpel): gelu(0) = 0, gelu(x) - gelu(-x) = x,
+    gelu(1) = 0.84119199..., gelu(x) -> x for large x."""
+    assert O.gelu(0.0) == 0.0
+    assert O.gelu(1.0) == pytest.approx(0.8411919906082768, rel=1e-14)
+    for x in (0.3, 1.7, -2.2, 5.0):
+        assert O.gelu(x) - O.gelu(-x) == pytest.approx(x, rel=1e-14, abs=1e-15)
+    assert O.gelu(12.0) == pytest.approx(12.0, rel=1e-15)
+
+
+def test_backprop_matches_central_differences():
+    rng = np.random.default_rng(4)
+    P = _params(1)
+    X = rng.normal(size=(37, O.MLP_IN))
+    T = rng.normal(size=(37, O.MLP_OUT))
+    loss, g = O.mlp_loss_grad(P, X, T)
+    assert loss > 0
+    idx = rng.choice(O.MLP_NPARAM, size=60, replace=False)
+    # include every parameter group: W1, b1, W2, b2, W3, b3
+    starts = np.cumsum([0, 64 * 40, 64, 64 * 64, 64, 8 * 64])
+    idx = np.concatenate([idx, starts + 3])
+    h = 1e-5  # central differences: truncation O(h^2) and round-off O(eps L / h) both below 1e-8 here
+    for i in idx:
+        Pp = P.copy()
+        Pm = P.copy()
+        Pp[i] += h
+        Pm[i] -= h
+        fd = (O.mlp_loss_grad(Pp, X, T)[0] - O.mlp_loss_grad(Pm, X, T)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * abs(g[i]) + 2e-9, (i, fd, g[i])
+
+
+def test_forward_matches_loss_definition():
+    """mlp_forward and the loss use the same network: L = mean (y - t)^2."""
+    rng = np.random.default_rng(2)
+    P = _params(3)
+    X = rng.normal(size=(5, O.MLP_IN))
+    T = rng.normal(size=(5, O.MLP_OUT))
+    ys = np.array([O.mlp_forward(P, x)[2] for x in X])
+    loss, _ = O.mlp_loss_grad(P, X, T)
+    assert loss == pytest.approx(np.mean((ys - T) ** 2), rel=1e-13)
+    # zero weights: output is the last bias
+    Z = np.zeros(O.MLP_NPARAM)
+    Z[-8:] = np.arange(8)
+    assert np.array_equal(O.mlp_forward(Z, X[0])[2], np.arange(8.0))
+
+
+def test_zero_network_is_plain_rusanov_bitwise():
+    q = W.blast(nsteps=2)
+    U0, _, _ = O.run(q, q.U0, 2, cfl=0.8)
+    ql = W.Problem(**{**q.__dict__, "learned": 1, "mlp": np.zeros(O.MLP_NPARAM)})
+    U1, _, _ = O.run(ql, q.U0, 2, cfl=0.8)
+    assert np.array_equal(U0, U1)
+
+
+def _stencil(rng):
+    Ws = np.zeros((4, 8))
+    Ws[:, 0] = rng.uniform(0.5, 2, 4)
+    Ws[:, 1:7] = rng.normal(0, 0.5, (4, 6))
+    Ws[:, 7] = rng.uniform(0.5, 2, 4)
+    WL = Ws[1] + rng.normal(0, 0.01, 8)
+    WR = Ws[2] + rng.normal(0, 0.01, 8)
+    return Ws, WL, WR
+
+
+def _scale_prim(Wv, a, b):
+    out = Wv.copy()
+    out[..., 0] *= a
+    out[..., 1:4] *= b
+    out[..., 4:7] *= math.sqrt(a) * b
+    out[..., 7] *= a * b * b
+    return out
+
+
+def test_features_are_similarity_invariant_and_rotate_with_the_face():
+    rng = np.random.default_rng(7)
+    Ws, WL, WR = _stencil(rng)
+    cmax = 1.3
+    x = O.mlp_features(0, Ws, WL, WR, cmax)
+    a, b = 3.7, 0.21
+    xs = O.mlp_features(0, _scale_prim(Ws, a, b), _scale_prim(WL, a, b), _scale_prim(WR, a, b), cmax * b)
+    assert np.allclose(xs, x, rtol=1e-13, atol=1e-14)
+    # a y-face of the state whose (y, z, x) components are the x-face's (x, y, z)
+    perm = [0, 3, 1, 2, 6, 4, 5, 7]   # new[v] = old[perm[v]]: u_x' = u_z, u_y' = u_x, u_z' = u_y
+    xy = O.mlp_features(1, Ws[:, perm], WL[perm], WR[perm], cmax)
+    assert np.array_equal(xy, x)
+
+
+def test_learned_residual_scales_like_the_flux():
+    """Under rho -> a rho, u -> b u, B -> sqrt(a) b B, p -> a b^2 p the features are
+    unchanged and the corrections are rescaled by the flux units, so the whole
+    learned residual scales like the plain one: (a b, a b^2, sqrt(a) b^2, a b^3)."""
+    q = W.blast(nsteps=1)
+    q.learned = 1
+    q.mlp = _params(11, scale=0.2)
+    # smooth nontrivial state
+    X = W.cell_centres(q.lo, q.hi, q.root, q.leaves)
+    Wp = [1 + 0.3 * np.sin(2 * X[0]), 0.2 * np.cos(3 * X[1]), 0.1 * np.sin(X[2]), 0.05 + 0 * X[0],
+          0.5 + 0.1 * X[1], 0.3 * np.cos(X[0]), 0.1 + 0 * X[0], 1 + 0.2 * np.cos(X[0] + X[2])]
+    q = W.with_state(q, Wp)
+    R = O.residual(q, q.U0)
+    q0 = W.Problem(**{**q.__dict__, "learned": 0})
+    R0 = O.residual(q0, q.U0)
+    assert np.abs(R - R0).max() > 1e-6 * np.abs(R0).max()   # the network changes the residual
+    a, b = 2.5, 0.4
+    Wsc = [Wp[0] * a] + [w * b for w in Wp[1:4]] + [w * math.sqrt(a) * b for w in Wp[4:7]] + [Wp[7] * a * b * b]
+    qs = W.with_state(W.Problem(**{**q.__dict__}), Wsc)
+    Rs = O.residual(qs, qs.U0)
+    f = np.array([a * b] + [a * b * b] * 3 + [math.sqrt(a) * b * b] * 3 + [a * b ** 3])
+    scale = np.abs(R).reshape(8, -1).max(1)
+    err = np.abs(Rs - f[:, None, None, None, None] * R).reshape(8, -1).max(1) / (f * scale)
+    assert err.max() < 1e-11, err
