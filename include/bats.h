@@ -182,6 +182,58 @@ int bats_get_launch_count(bats_t* h, long long* n);
  * the compiler's conversions.  Allocates and frees its own device buffers. */
 int bats_debug_check_conversions(const float* f, const double* d, int n, double* f2d_out, float* d2f_out);
 
+/* ---- learned flux correction (a small MLP on tensor cores) -------------
+ * Network: 40 inputs -> 64 -> 64 -> 8 outputs, tanh-form GELU after the two
+ * hidden layers, BF16 weights and activations with FP32 accumulation.
+ * Parameters (BATS_MLP_NPARAM floats, row-major [out][in]): W1 [64][40],
+ * b1 [64], W2 [64][64], b2 [64], W3 [8][64], b3 [8].
+ * Inputs of a face (in the face frame: normal component first, then the next
+ * two axes cyclically): the primitives (rho, u, B1, p) of the four cells
+ * around the face and the mean of the two reconstructed face states, scaled
+ * by rho_ref (mean stencil density) and c_ref (the Rusanov speed cmax):
+ * rho/rho_ref, u/c_ref, B1/(sqrt(rho_ref) c_ref), p/(rho_ref c_ref^2).
+ * Outputs: the flux correction in the face frame in units of
+ * (rho_ref c_ref, rho_ref c_ref^2, sqrt(rho_ref) c_ref^2, rho_ref c_ref^3);
+ * each component is clipped to the Rusanov dissipation |cmax (UR - UL)/2| of
+ * that face and added to the Rusanov flux.  With all-zero weights the method
+ * is the plain Rusanov scheme. */
+#define BATS_MLP_NPARAM 7304
+
+/* Install network weights in a solver (host or device pointer, copied) and
+ * turn the learned form on for its next steps; params == NULL turns it off.
+ * Each stage then runs three launches: face inputs, the network, the fused
+ * stage with the correction. */
+int bats_set_mlp(bats_t* h, const float* params);
+
+/* Training-data view of grid `grid`: for every face of every block (index
+ * ((block * 3 + d) * 576 + line * 9 + f), line = a + 8 b over the two
+ * transverse cell indices in increasing axis order, f = 0..8 the face on the
+ * low side of cell f along d) the 40 network inputs X (float, host or device,
+ * n_faces x 40) and the plain Rusanov flux F (double, n_faces x 8, x/y/z
+ * components), of the current state (stage_input 0) or of the midpoint
+ * stage-2 input U* = U + (dt/2) R(U) (stage_input 1, dt > 0).  The state is
+ * not changed.  n_faces = 1728 * n_blocks of the grid. */
+int bats_debug_face_data(bats_t* h, int grid, int stage_input, double dt, float* X, double* F, size_t n_faces);
+
+/* Trainer: FP32 master weights, Adam state, GPU forward and backward. */
+typedef struct bats_mlp bats_mlp_t;
+/* params NULL: seeded initialisation (hidden layers N(0, 1/fan_in), biases and
+ * the output layer zero, so the initial network is the plain scheme). */
+int bats_mlp_create(const float* params, uint64_t seed, void* cuda_stream, bats_mlp_t** out);
+void bats_mlp_destroy(bats_mlp_t* m);
+int bats_mlp_set_params(bats_mlp_t* m, const float* params);
+int bats_mlp_get_params(bats_mlp_t* m, float* params);
+/* Y (n x 8) = network(X (n x 40)); host or device pointers. */
+int bats_mlp_forward(bats_mlp_t* m, const float* X, int64_t n, float* Y);
+/* Loss L = (1/(8n)) sum (y - t)^2 over n samples (X n x 40, T n x 8) and its
+ * gradient (grad nullable, BATS_MLP_NPARAM floats); inputs are rounded to
+ * BF16 as in inference.  Weight gradients accumulate with atomics, so their
+ * last bits can vary between runs. */
+int bats_mlp_loss_grad(bats_mlp_t* m, const float* X, const float* T, int64_t n, float* grad, double* loss);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with learning rate lr on
+ * the batch; *loss (nullable) receives the loss before the step. */
+int bats_mlp_train_step(bats_mlp_t* m, const float* X, const float* T, int64_t n, float lr, double* loss);
+
 /* ---- stepping without device allocation --------------------------------
  * No counterpart in the paper: an addition for callers that cannot allocate
  * device memory when they step -- code whose device memory is owned by an

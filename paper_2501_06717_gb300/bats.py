@@ -99,6 +99,16 @@ def lib():
     L.bats_set_launch.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     L.bats_get_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     L.bats_debug_check_conversions.argtypes = [vp, vp, ctypes.c_int, vp, vp]
+    L.bats_set_mlp.argtypes = [vp, vp]
+    L.bats_debug_face_data.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, vp, vp, ctypes.c_size_t]
+    L.bats_mlp_create.argtypes = [vp, ctypes.c_uint64, vp, ctypes.POINTER(vp)]
+    L.bats_mlp_destroy.argtypes = [vp]
+    L.bats_mlp_destroy.restype = None
+    L.bats_mlp_set_params.argtypes = [vp, vp]
+    L.bats_mlp_get_params.argtypes = [vp, vp]
+    L.bats_mlp_forward.argtypes = [vp, vp, ctypes.c_int64, vp]
+    L.bats_mlp_loss_grad.argtypes = [vp, vp, vp, ctypes.c_int64, vp, ctypes.POINTER(ctypes.c_double)]
+    L.bats_mlp_train_step.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.c_float, ctypes.POINTER(ctypes.c_double)]
     L.bats_step_noalloc.argtypes = [ctypes.POINTER(bats_grid_desc), ctypes.POINTER(bats_physics), dp,
                                     ctypes.c_size_t, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                     ctypes.POINTER(ctypes.c_double), vp, ctypes.c_char_p, ctypes.c_size_t]
@@ -267,6 +277,102 @@ def bats_debug_check_conversions(f, d):
     return o1, o2
 
 
+BATS_MLP_NPARAM = 7304
+
+
+def bats_set_mlp(h, params):
+    """Install network weights (float32, BATS_MLP_NPARAM) and turn the learned
+    form on; None turns it off."""
+    if params is None:
+        _check(h, lib().bats_set_mlp(h, None))
+        return
+    if not hasattr(params, "data_ptr"):
+        params = np.ascontiguousarray(params, dtype=np.float32)
+    p, n = _ptr_and_size(params)
+    if n != BATS_MLP_NPARAM:
+        raise ValueError("expected %d parameters" % BATS_MLP_NPARAM)
+    _check(h, lib().bats_set_mlp(h, p))
+
+
+def bats_debug_face_data(h, grid, nblocks, stage_input=0, dt=0.0, X=None, F=None):
+    """Network inputs (n_faces x 40 float32) and plain Rusanov fluxes
+    (n_faces x 8 float64) of every face of grid `grid`."""
+    nf = nblocks * 3 * 576
+    if X is None:
+        X = np.zeros((nf, 40), np.float32)
+    if F is None:
+        F = np.zeros((nf, 8), np.float64)
+    px, nx = _ptr_and_size(X)
+    pf, _ = _ptr_and_size(F)
+    _check(h, lib().bats_debug_face_data(h, int(grid), int(stage_input), float(dt), px, pf, nf))
+    return X, F
+
+
+class Mlp:
+    """The trainer: FP32 master weights + Adam state on the device."""
+
+    def __init__(self, params=None, seed=0, stream=None):
+        self.h = ctypes.c_void_p()
+        s = None
+        if stream is not None:
+            s = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        buf = None
+        if params is not None:
+            buf = np.ascontiguousarray(params, dtype=np.float32)
+        rc = lib().bats_mlp_create(buf.ctypes.data if buf is not None else None, int(seed), s, ctypes.byref(self.h))
+        if rc != BATS_OK:
+            raise BatsError(rc, "bats_mlp_create failed")
+
+    def close(self):
+        if self.h:
+            lib().bats_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _rc(self, rc, what):
+        if rc != BATS_OK:
+            raise BatsError(rc, what)
+
+    def set_params(self, params):
+        buf = np.ascontiguousarray(params, dtype=np.float32)
+        self._rc(lib().bats_mlp_set_params(self.h, buf.ctypes.data), "set_params")
+
+    def get_params(self):
+        out = np.zeros(BATS_MLP_NPARAM, np.float32)
+        self._rc(lib().bats_mlp_get_params(self.h, out.ctypes.data), "get_params")
+        return out
+
+    def forward(self, X):
+        X = X if hasattr(X, "data_ptr") else np.ascontiguousarray(X, dtype=np.float32)
+        px, n = _ptr_and_size(X)
+        n //= 40
+        Y = np.zeros((n, 8), np.float32)
+        self._rc(lib().bats_mlp_forward(self.h, px, n, Y.ctypes.data), "forward")
+        return Y
+
+    def loss_grad(self, X, T):
+        X = X if hasattr(X, "data_ptr") else np.ascontiguousarray(X, dtype=np.float32)
+        T = T if hasattr(T, "data_ptr") else np.ascontiguousarray(T, dtype=np.float32)
+        px, n = _ptr_and_size(X)
+        pt, _ = _ptr_and_size(T)
+        g = np.zeros(BATS_MLP_NPARAM, np.float32)
+        loss = ctypes.c_double(0.0)
+        self._rc(lib().bats_mlp_loss_grad(self.h, px, pt, n // 40, g.ctypes.data, ctypes.byref(loss)), "loss_grad")
+        return loss.value, g
+
+    def train_step(self, X, T, lr):
+        px, n = _ptr_and_size(X)
+        pt, _ = _ptr_and_size(T)
+        loss = ctypes.c_double(0.0)
+        self._rc(lib().bats_mlp_train_step(self.h, px, pt, n // 40, float(lr), ctypes.byref(loss)), "train_step")
+        return loss.value
+
+
 BATS_NOALLOC_MAX_BLOCKS = 128
 BATS_NOALLOC_MAX_MAP_ENTRIES = 16384
 
@@ -357,6 +463,12 @@ class Solver:
         p = self.problems[grid]
         out = np.zeros((8, p.nb, 8, 8, 8))
         return bats_debug_residual(self.h, grid, out)
+
+    def set_mlp(self, params):
+        bats_set_mlp(self.h, params)
+
+    def face_data(self, grid=0, stage_input=0, dt=0.0):
+        return bats_debug_face_data(self.h, grid, self.problems[grid].nb, stage_input, dt)
 
     def set_launch(self, persistent=0, blocks_per_cta=1, ctas_per_sm=0, use_graph=0):
         bats_set_launch(self.h, persistent, blocks_per_cta, ctas_per_sm, use_graph)

@@ -33,6 +33,10 @@ cudaError_t launch_dt(int ngrids, int mode, double cfl, double fixed_dt, double*
                       unsigned long long* smax, unsigned long long* smax_next, cudaStream_t st);
 cudaError_t launch_debug_fill(const StageArgs& a, int b0, int nb, double* T, cudaStream_t st);
 cudaError_t launch_check_conversions(const float* f, const double* d, int n, double* f2d_out, float* d2f_out);
+cudaError_t mlp_alloc(MlpDev* w);
+void mlp_free(MlpDev* w);
+cudaError_t launch_mlp_pack(const float* P, const MlpDev& m, cudaStream_t st);
+cudaError_t launch_mlp_infer(const uint32_t* X, float* Y, int64_t n, const MlpDev& m, int nsm, cudaStream_t st);
 
 }  // namespace batsk
 
@@ -67,6 +71,12 @@ struct bats {
   cudaGraphExec_t graph = nullptr;
   int graph_n = -1;
   double graph_cfl = 0, graph_dt = 0;
+  // learned form
+  bool learned_requested = false, learned = false;
+  MlpDev mlp{};
+  float* mlp_params = nullptr;
+  uint32_t* Xb = nullptr;   // BF16 network inputs of every face
+  float* Yb = nullptr;      // network outputs of every face
 };
 
 static std::string g_create_error;
@@ -315,6 +325,10 @@ void free_all(bats_t* h) {
   cudaFree(h->smax_next);
   cudaFree(h->errw);
   cudaFree(h->staging);
+  mlp_free(&h->mlp);
+  cudaFree(h->mlp_params);
+  cudaFree(h->Xb);
+  cudaFree(h->Yb);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
   for (cudaEvent_t e : h->stage_ev) cudaEventDestroy(e);
@@ -343,7 +357,7 @@ StageArgs base_args(bats_t* h) {
   return a;
 }
 
-int launch_stage(bats_t* h, const StageArgs& a) {
+int launch_stage_one(bats_t* h, const StageArgs& a) {
   bool mixed = h->ph.precision == BATS_MIXED;
   int nitems = (a.nblocks + a.blocks_per_item - 1) / a.blocks_per_item;
   int grid = nitems;
@@ -355,6 +369,24 @@ int launch_stage(bats_t* h, const StageArgs& a) {
   h->launches++;
   CK(h, launch_stage_kernel(mixed, grid, h->stream, a));
   return BATS_OK;
+}
+
+// One stage; with the learned form, three launches: the network inputs of
+// every face, the network, and the stage with the correction.
+int launch_stage(bats_t* h, const StageArgs& a) {
+  if (!h->learned || a.kind >= 3) return launch_stage_one(h, a);
+  StageArgs f = a;
+  f.kind = 3;
+  f.learned = 0;
+  f.Xb = h->Xb;
+  int rc = launch_stage_one(h, f);
+  if (rc) return rc;
+  h->launches++;
+  CK(h, launch_mlp_infer(h->Xb, h->Yb, static_cast<int64_t>(h->nbt) * 3 * NFACE, h->mlp, h->num_sms, h->stream));
+  StageArgs u = a;
+  u.learned = 1;
+  u.Y = h->Yb;
+  return launch_stage_one(h, u);
 }
 
 int launch_cfl(bats_t* h, int g) {
@@ -428,6 +460,8 @@ int enqueue_steps(bats_t* h, int n, double cfl, double fixed_dt, bool timed) {
 
 int run_steps(bats_t* h, int n, double cfl, double fixed_dt, double* t_out) {
   if (n < 0) return fail(h, BATS_ERR_INVALID_ARG, "negative step count");
+  if (h->learned_requested && !h->learned)
+    return fail(h, BATS_ERR_NOT_TRAINED, "learned form requested but no weights set (bats_set_mlp)");
   h->launches = 0;
   CK(h, cudaGetLastError());  // report (and clear) anything left from an earlier call
   int32_t init[2] = {0, INT_MAX};
@@ -452,7 +486,7 @@ int run_steps(bats_t* h, int n, double cfl, double fixed_dt, double* t_out) {
       h->launches = l0;
     }
     CK(h, cudaGraphLaunch(h->graph, h->stream));
-    h->launches = static_cast<long long>(n) * 4;
+    h->launches = static_cast<long long>(n) * (h->learned ? 8 : 4);
     h->timed_steps = 0;
   } else {
     int rc = enqueue_steps(h, n, cfl, fixed_dt, true);
@@ -500,8 +534,8 @@ int bats_create(const bats_grid_desc* grids, int n_grids, const bats_physics* ph
   if (phys->limiter < 0 || phys->limiter > 1 || phys->rk < 0 || phys->rk > 1 || phys->precision < 0 ||
       phys->precision > 1 || phys->b0 < 0 || phys->b0 > 3)
     return fail(nullptr, BATS_ERR_INVALID_ARG, "bad physics enumeration");
-  if (phys->learned) return fail(nullptr, BATS_ERR_NOT_TRAINED, "learned form needs bats_set_mlp (not set)");
   bats_t* h = new bats_t();
+  h->learned_requested = phys->learned != 0;
   h->stream = static_cast<cudaStream_t>(cuda_stream);
   h->ngrids = n_grids;
   h->grids_h.resize(n_grids);
@@ -739,6 +773,99 @@ int bats_set_launch(bats_t* h, int persistent, int blocks_per_cta, int ctas_per_
     cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
   }
+  return BATS_OK;
+}
+
+int bats_set_mlp(bats_t* h, const float* params) {
+  if (!h) return BATS_ERR_INVALID_ARG;
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  if (!params) {
+    h->learned = false;
+    h->learned_requested = false;
+    return BATS_OK;
+  }
+  if (!h->mlp_params) {
+    int rc;
+    const size_t nf = static_cast<size_t>(h->nbt) * 3 * NFACE;
+    if ((rc = dev_alloc(h, &h->mlp_params, MLP_NPARAM)) || (rc = dev_alloc(h, &h->Xb, nf * 24)) ||
+        (rc = dev_alloc(h, &h->Yb, nf * 8)))
+      return rc;
+    CK(h, mlp_alloc(&h->mlp));
+  }
+  CK(h, cudaMemcpyAsync(h->mlp_params, params, sizeof(float) * MLP_NPARAM,
+                        is_device_ptr(params) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+  CK(h, launch_mlp_pack(h->mlp_params, h->mlp, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  h->learned = true;
+  return BATS_OK;
+}
+
+int bats_debug_face_data(bats_t* h, int grid, int stage_input, double dt, float* X, double* F, size_t n_faces) {
+  int rc = grid_check(h, grid);
+  if (rc) return rc;
+  const GridDev& G = h->grids_h[grid];
+  const size_t nf = static_cast<size_t>(G.nb) * 3 * NFACE;
+  if (!X || !F || n_faces != nf) return fail(h, BATS_ERR_INVALID_ARG, "face buffer size mismatch");
+  if (stage_input && !(dt > 0.0)) return fail(h, BATS_ERR_INVALID_ARG, "stage_input needs dt > 0");
+  const size_t all = static_cast<size_t>(h->nbt) * 3 * NFACE;
+  float* Xf = nullptr;
+  double* Fd = nullptr;
+  if ((rc = dev_alloc(h, &Xf, all * 40)) || (rc = dev_alloc(h, &Fd, all * 8))) {
+    cudaFree(Xf);
+    return rc;
+  }
+  StageArgs a = base_args(h);
+  int32_t init[2] = {0, INT_MAX};
+  cudaError_t e = cudaMemcpyAsync(h->errw, init, sizeof(init), cudaMemcpyHostToDevice, h->stream);
+  const double* Uin = h->U;
+  const float* Win = h->W;
+  if (e == cudaSuccess && stage_input) {
+    e = launch_dt(h->ngrids, 0, -1.0, dt, h->dt, h->t, h->smax, h->smax_next, h->stream);
+    StageArgs s1 = a;
+    s1.Uin = h->U;
+    s1.Ubase = h->U;
+    s1.Uout = h->U1;
+    s1.Win = h->W;
+    s1.Wout = h->W1;
+    s1.kind = 0;
+    s1.last = 0;
+    s1.beta = 0.5;
+    s1.write_u_all = 1;
+    if (e == cudaSuccess) {
+      rc = launch_stage(h, s1);
+      if (rc) {
+        cudaFree(Xf);
+        cudaFree(Fd);
+        return rc;
+      }
+    }
+    Uin = h->U1;
+    Win = h->W1;
+  }
+  if (e == cudaSuccess) {
+    a.Uin = Uin;
+    a.Win = Win;
+    a.kind = 4;
+    a.learned = 0;
+    a.Xf = Xf;
+    a.Fd = Fd;
+    rc = launch_stage_one(h, a);
+  }
+  const size_t off = static_cast<size_t>(G.block0) * 3 * NFACE;
+  if (e == cudaSuccess && !rc)
+    e = cudaMemcpyAsync(X, Xf + off * 40, nf * 40 * sizeof(float),
+                        is_device_ptr(X) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess && !rc)
+    e = cudaMemcpyAsync(F, Fd + off * 8, nf * 8 * sizeof(double),
+                        is_device_ptr(F) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cudaFree(Xf);
+  cudaFree(Fd);
+  if (rc) return rc;
+  if (e != cudaSuccess) return cuda_fail(h, e, "bats_debug_face_data");
   return BATS_OK;
 }
 

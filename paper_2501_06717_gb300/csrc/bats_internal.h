@@ -58,6 +58,15 @@ struct PhysDev {
   double b0p[12];
 };
 
+// Learned flux correction: network sizes and the device weight set (BF16
+// pairs in the layouts the tensor-core kernels read, FP32 biases).
+constexpr int MLP_IN = 40, MLP_H = 64, MLP_OUT = 8;
+constexpr int MLP_NPARAM = MLP_H * MLP_IN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_OUT * MLP_H + MLP_OUT;
+struct MlpDev {
+  uint32_t *w1, *w2, *w3, *w2t, *w3t;  // [64][24], [64][32], [8][32], [64][32], [64][8]
+  float *b1, *b2, *b3;
+};
+
 // Arguments of one stage launch.
 struct StageArgs {
   const double* Uin;      // stage input, block-major FP64
@@ -73,11 +82,19 @@ struct StageArgs {
   int32_t* err;           // [0] error bits, [1] first bad block
   int32_t nblocks;
   int32_t blocks_per_item;
-  int32_t kind;           // 0: Uout = Ubase + c R;  1: Uout = 0.5 Ubase + 0.5 (Uin + c R)
+  int32_t kind;           // 0: Uout = Ubase + c R;  1: Uout = 0.5 Ubase + 0.5 (Uin + c R);
+                          // 2: Uout = R (debug);  3: face features only (Xb);
+                          // 4: features and plain fluxes only (Xf, Fd)
   int32_t last;           // 1: reduce the CFL bound of Uout into smax_next
   int32_t write_u_all;    // mixed: 1 = write Uout for every block, 0 = only need_u blocks
   double beta;            // c = beta * dt[grid]
   PhysDev ph;
+  // learned form; face index ((blk * 3 + d) * 576 + line * 9 + f)
+  int32_t learned;        // kinds 0-2: add the clipped, rescaled correction Y
+  uint32_t* Xb;           // kind 3: BF16 features, 24 words (48 columns) per face
+  float* Xf;              // kind 4: FP32 features, 40 per face
+  double* Fd;             // kind 4: plain Rusanov flux, 8 per face (x, y, z components)
+  const float* Y;         // normalised correction in the face frame, 8 per face
 };
 
 }  // namespace batsk

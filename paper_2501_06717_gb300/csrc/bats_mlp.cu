@@ -1,0 +1,638 @@
+// bats_mlp.cu -- the learned flux correction's network on tensor cores:
+// a 40 -> 64 -> 64 -> 8 MLP with tanh-form GELU (Hendrycks & Gimpel), BF16
+// weights and activations, FP32 accumulation, on mma.sync m16n8k16 BF16.
+//
+//  * k_mlp_infer: Y = MLP(X) for face feature rows X (BF16, 48 columns: the
+//    40 features and 8 zeros); each warp carries 16-row tiles through the
+//    three layers with the accumulators of one layer re-packed in registers
+//    as the A operand of the next.
+//  * k_mlp_train: the mean-squared-error loss and its gradient for a batch;
+//    forward and the backward data products on tensor cores, the weight
+//    gradients (outer products over the tile's samples) on the CUDA cores,
+//    accumulated per CTA in shared memory and once per CTA in global memory.
+//  * k_mlp_adam, k_mlp_pack: the Adam update of the FP32 master weights and
+//    the BF16 copies in the layouts the kernels read.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <random>
+#include <vector>
+
+#include "bats.h"
+#include "bats_internal.h"
+
+namespace batsk {
+
+__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+__device__ __forceinline__ float bf16_lo(uint32_t u) { return __uint_as_float(u << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t u) { return __uint_as_float(u & 0xffff0000u); }
+__device__ __forceinline__ float tanh_approx(float x) {
+  float r;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+// GELU, tanh form, and its derivative.
+__device__ __forceinline__ float gelu_f(float x) {
+  const float k = 0.7978845608028654f;
+  return 0.5f * x * (1.0f + tanh_approx(k * (x + 0.044715f * x * x * x)));
+}
+__device__ __forceinline__ float gelu_grad_f(float x) {
+  const float k = 0.7978845608028654f;
+  float t = tanh_approx(k * (x + 0.044715f * x * x * x));
+  return 0.5f * (1.0f + t) + 0.5f * x * (1.0f - t * t) * k * (1.0f + 3.0f * 0.044715f * x * x);
+}
+
+// Shared-memory weight layout (32-bit words = BF16 pairs), rows padded so the
+// B-fragment loads of a warp fall in distinct banks.
+constexpr int W1S = 28;  // W1 [64 out][48 in] -> 24 words + 4 pad
+constexpr int W2S = 36;  // W2, W2T [64][64] -> 32 words + 4 pad
+constexpr int W3S = 36;  // W3 [8][64]
+constexpr int W3TS = 12; // W3T [64 in][16 out (8 + zeros)] -> 8 words + 4 pad
+struct MlpSmem {
+  uint32_t w1[64 * W1S];
+  uint32_t w2[64 * W2S];
+  uint32_t w3[8 * W3S];
+  uint32_t w2t[64 * W2S];
+  uint32_t w3t[64 * W3TS];
+  float b1[64], b2[64], b3[8];
+};
+
+// Copy the packed device weights (MlpDev, unpadded rows) into shared memory.
+__device__ void load_mlp_smem(const MlpDev& m, MlpSmem& s) {
+  for (int e = threadIdx.x; e < 64 * 24; e += blockDim.x) s.w1[(e / 24) * W1S + e % 24] = m.w1[e];
+  for (int e = threadIdx.x; e < 64 * 32; e += blockDim.x) {
+    s.w2[(e / 32) * W2S + e % 32] = m.w2[e];
+    s.w2t[(e / 32) * W2S + e % 32] = m.w2t[e];
+  }
+  for (int e = threadIdx.x; e < 8 * 32; e += blockDim.x) s.w3[(e / 32) * W3S + e % 32] = m.w3[e];
+  for (int e = threadIdx.x; e < 64 * 8; e += blockDim.x) s.w3t[(e / 8) * W3TS + e % 8] = m.w3t[e];
+  for (int e = threadIdx.x; e < 64; e += blockDim.x) {
+    s.b1[e] = m.b1[e];
+    s.b2[e] = m.b2[e];
+  }
+  for (int e = threadIdx.x; e < 8; e += blockDim.x) s.b3[e] = m.b3[e];
+}
+
+// Forward of one 16-row tile.  a1: A fragments of the inputs (3 k-tiles).
+// Outputs: z1, z2 (pre-activations, C layout, 8 n-tiles x 4), a2, a3 (BF16
+// A fragments of H1, H2, 4 k-tiles x 4), y (C layout of the 8 outputs).
+template <bool KEEP>
+__device__ __forceinline__ void mlp_tile_forward(const MlpSmem& s, const uint32_t a1[3][4], float z1[8][4],
+                                                 float z2[8][4], uint32_t a2[4][4], uint32_t a3[4][4],
+                                                 float y[4]) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  float acc[8][4];
+#pragma unroll
+  for (int nt = 0; nt < 8; nt++) {
+    const float bl = s.b1[nt * 8 + 2 * t], bh = s.b1[nt * 8 + 2 * t + 1];
+    acc[nt][0] = bl; acc[nt][1] = bh; acc[nt][2] = bl; acc[nt][3] = bh;
+#pragma unroll
+    for (int kt = 0; kt < 3; kt++)
+      mma_bf16(acc[nt], a1[kt], s.w1[(nt * 8 + g) * W1S + kt * 8 + t], s.w1[(nt * 8 + g) * W1S + kt * 8 + 4 + t]);
+  }
+#pragma unroll
+  for (int nt = 0; nt < 8; nt++) {
+    if (KEEP) {
+#pragma unroll
+      for (int r = 0; r < 4; r++) z1[nt][r] = acc[nt][r];
+    }
+    const int kt = nt >> 1, hi = nt & 1;
+    a2[kt][hi * 2 + 0] = pack_bf16(gelu_f(acc[nt][0]), gelu_f(acc[nt][1]));
+    a2[kt][hi * 2 + 1] = pack_bf16(gelu_f(acc[nt][2]), gelu_f(acc[nt][3]));
+  }
+#pragma unroll
+  for (int nt = 0; nt < 8; nt++) {
+    const float bl = s.b2[nt * 8 + 2 * t], bh = s.b2[nt * 8 + 2 * t + 1];
+    acc[nt][0] = bl; acc[nt][1] = bh; acc[nt][2] = bl; acc[nt][3] = bh;
+#pragma unroll
+    for (int kt = 0; kt < 4; kt++)
+      mma_bf16(acc[nt], a2[kt], s.w2[(nt * 8 + g) * W2S + kt * 8 + t], s.w2[(nt * 8 + g) * W2S + kt * 8 + 4 + t]);
+  }
+#pragma unroll
+  for (int nt = 0; nt < 8; nt++) {
+    if (KEEP) {
+#pragma unroll
+      for (int r = 0; r < 4; r++) z2[nt][r] = acc[nt][r];
+    }
+    const int kt = nt >> 1, hi = nt & 1;
+    a3[kt][hi * 2 + 0] = pack_bf16(gelu_f(acc[nt][0]), gelu_f(acc[nt][1]));
+    a3[kt][hi * 2 + 1] = pack_bf16(gelu_f(acc[nt][2]), gelu_f(acc[nt][3]));
+  }
+  const float bl = s.b3[2 * t], bh = s.b3[2 * t + 1];
+  y[0] = bl; y[1] = bh; y[2] = bl; y[3] = bh;
+#pragma unroll
+  for (int kt = 0; kt < 4; kt++) mma_bf16(y, a3[kt], s.w3[g * W3S + kt * 8 + t], s.w3[g * W3S + kt * 8 + 4 + t]);
+}
+
+// Y[n][8] = MLP(X[n][48] BF16).
+__global__ void __launch_bounds__(128) k_mlp_infer(const uint32_t* __restrict__ X, float* __restrict__ Y,
+                                                   int64_t n, MlpDev m) {
+  __shared__ MlpSmem s;
+  load_mlp_smem(m, s);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int64_t warp = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t r0 = warp * 16; r0 < n; r0 += nwarps * 16) {
+    const int64_t ra = r0 + g, rb = r0 + g + 8;
+    uint32_t a1[3][4];
+#pragma unroll
+    for (int kt = 0; kt < 3; kt++) {
+      a1[kt][0] = ra < n ? X[ra * 24 + kt * 8 + t] : 0u;
+      a1[kt][1] = rb < n ? X[rb * 24 + kt * 8 + t] : 0u;
+      a1[kt][2] = ra < n ? X[ra * 24 + kt * 8 + 4 + t] : 0u;
+      a1[kt][3] = rb < n ? X[rb * 24 + kt * 8 + 4 + t] : 0u;
+    }
+    float z1[8][4], z2[8][4], y[4];
+    uint32_t a2[4][4], a3[4][4];
+    mlp_tile_forward<false>(s, a1, z1, z2, a2, a3, y);
+    if (ra < n) *reinterpret_cast<float2*>(Y + ra * 8 + 2 * t) = make_float2(y[0], y[1]);
+    if (rb < n) *reinterpret_cast<float2*>(Y + rb * 8 + 2 * t) = make_float2(y[2], y[3]);
+  }
+}
+
+// Loss sum and gradient of L = (1/(8 n_total)) sum (y - t)^2 over rows
+// [0, n) of X (FP32 [n][40], rounded to BF16 on load) and T (FP32 [n][8]).
+// grad (FP32 [NPARAM], zeroed by the caller) and loss_sum accumulate.
+constexpr int TRAIN_WARPS = 4;
+struct TrainTile {           // per-warp staging of one 16-sample tile, FP32
+  float x[16][40];
+  float h1[16][64];
+  float h2[16][64];
+  float dz1[16][64];
+  float dz2[16][64];
+  float dy[16][8];
+};
+
+__global__ void __launch_bounds__(TRAIN_WARPS * 32) k_mlp_train(const float* __restrict__ X,
+                                                                const float* __restrict__ T, int64_t n,
+                                                                double inv_count, MlpDev m,
+                                                                float* __restrict__ grad,
+                                                                double* __restrict__ loss_sum) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  MlpSmem& s = *reinterpret_cast<MlpSmem*>(smem_raw);
+  TrainTile* tiles = reinterpret_cast<TrainTile*>(smem_raw + sizeof(MlpSmem));
+  float* sgrad = reinterpret_cast<float*>(smem_raw + sizeof(MlpSmem) + TRAIN_WARPS * sizeof(TrainTile));
+  load_mlp_smem(m, s);
+  for (int e = threadIdx.x; e < MLP_NPARAM; e += blockDim.x) sgrad[e] = 0.f;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3, w = threadIdx.x >> 5;
+  TrainTile& tt = tiles[w];
+  const int64_t warp = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  const float scale = static_cast<float>(2.0 * inv_count);
+  double lsum = 0.0;
+  for (int64_t r0 = warp * 16; r0 < n; r0 += nwarps * 16) {
+    const int64_t ra = r0 + g, rb = r0 + g + 8;
+    // inputs as BF16 A fragments (and their FP32 values for the W1 gradient)
+    uint32_t a1[3][4];
+#pragma unroll
+    for (int kt = 0; kt < 3; kt++) {
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const int64_t r = (q & 1) ? rb : ra;
+        const int col = kt * 16 + (q >> 1) * 8 + 2 * t;
+        float v0 = 0.f, v1 = 0.f;
+        if (r < n && col < MLP_IN) {
+          v0 = X[r * MLP_IN + col];
+          v1 = X[r * MLP_IN + col + 1];
+        }
+        a1[kt][q] = pack_bf16(v0, v1);
+        if (col < MLP_IN) {
+          const int rr = (q & 1) ? g + 8 : g;
+          tt.x[rr][col] = bf16_lo(a1[kt][q]);
+          tt.x[rr][col + 1] = bf16_hi(a1[kt][q]);
+        }
+      }
+    }
+    float z1[8][4], z2[8][4], y[4];
+    uint32_t a2[4][4], a3[4][4];
+    mlp_tile_forward<true>(s, a1, z1, z2, a2, a3, y);
+    // dL/dy
+    float dy[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int64_t r = q < 2 ? ra : rb;
+      const int col = 2 * t + (q & 1);
+      float e = 0.f;
+      if (r < n) e = y[q] - T[r * 8 + col];
+      lsum += static_cast<double>(e) * e;
+      dy[q] = scale * e;
+      tt.dy[q < 2 ? g : g + 8][col] = dy[q];
+    }
+    // stage H1, H2 (the BF16 values the next layers saw)
+#pragma unroll
+    for (int kt = 0; kt < 4; kt++)
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const int rr = (q & 1) ? g + 8 : g;
+        const int col = kt * 16 + (q >> 1) * 8 + 2 * t;
+        tt.h1[rr][col] = bf16_lo(a2[kt][q]);
+        tt.h1[rr][col + 1] = bf16_hi(a2[kt][q]);
+        tt.h2[rr][col] = bf16_lo(a3[kt][q]);
+        tt.h2[rr][col + 1] = bf16_hi(a3[kt][q]);
+      }
+    // dH2 = dY W3 (K = 8 outputs, zero-padded to 16), dZ2 = dH2 * gelu'(Z2)
+    uint32_t ady[4] = {pack_bf16(dy[0], dy[1]), pack_bf16(dy[2], dy[3]), 0u, 0u};
+    uint32_t adz2[4][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; nt++) {
+      float c[4] = {0.f, 0.f, 0.f, 0.f};
+      mma_bf16(c, ady, s.w3t[(nt * 8 + g) * W3TS + t], s.w3t[(nt * 8 + g) * W3TS + 4 + t]);
+#pragma unroll
+      for (int q = 0; q < 4; q++) c[q] *= gelu_grad_f(z2[nt][q]);
+      const int kt = nt >> 1, hi = nt & 1;
+      adz2[kt][hi * 2 + 0] = pack_bf16(c[0], c[1]);
+      adz2[kt][hi * 2 + 1] = pack_bf16(c[2], c[3]);
+      const int col = nt * 8 + 2 * t;
+      tt.dz2[g][col] = c[0];
+      tt.dz2[g][col + 1] = c[1];
+      tt.dz2[g + 8][col] = c[2];
+      tt.dz2[g + 8][col + 1] = c[3];
+    }
+    // dH1 = dZ2 W2, dZ1 = dH1 * gelu'(Z1)
+#pragma unroll
+    for (int nt = 0; nt < 8; nt++) {
+      float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int kt = 0; kt < 4; kt++)
+        mma_bf16(c, adz2[kt], s.w2t[(nt * 8 + g) * W2S + kt * 8 + t], s.w2t[(nt * 8 + g) * W2S + kt * 8 + 4 + t]);
+      const int col = nt * 8 + 2 * t;
+      tt.dz1[g][col] = c[0] * gelu_grad_f(z1[nt][0]);
+      tt.dz1[g][col + 1] = c[1] * gelu_grad_f(z1[nt][1]);
+      tt.dz1[g + 8][col] = c[2] * gelu_grad_f(z1[nt][2]);
+      tt.dz1[g + 8][col + 1] = c[3] * gelu_grad_f(z1[nt][3]);
+    }
+    __syncwarp();
+    // weight and bias gradients: sums over the tile's 16 samples
+    for (int e = lane; e < MLP_NPARAM; e += 32) {
+      float acc = 0.f;
+      if (e < 2560) {
+        const int o = e / 40, i = e % 40;
+#pragma unroll 4
+        for (int r = 0; r < 16; r++) acc += tt.dz1[r][o] * tt.x[r][i];
+      } else if (e < 2624) {
+        const int o = e - 2560;
+        for (int r = 0; r < 16; r++) acc += tt.dz1[r][o];
+      } else if (e < 6720) {
+        const int o = (e - 2624) >> 6, i = (e - 2624) & 63;
+#pragma unroll 4
+        for (int r = 0; r < 16; r++) acc += tt.dz2[r][o] * tt.h1[r][i];
+      } else if (e < 6784) {
+        const int o = e - 6720;
+        for (int r = 0; r < 16; r++) acc += tt.dz2[r][o];
+      } else if (e < 7296) {
+        const int o = (e - 6784) >> 6, i = (e - 6784) & 63;
+#pragma unroll 4
+        for (int r = 0; r < 16; r++) acc += tt.dy[r][o] * tt.h2[r][i];
+      } else {
+        const int o = e - 7296;
+        for (int r = 0; r < 16; r++) acc += tt.dy[r][o];
+      }
+      atomicAdd(&sgrad[e], acc);
+    }
+    __syncwarp();
+  }
+  // loss: warp sum, then one atomic per warp
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+  if (lane == 0) atomicAdd(loss_sum, lsum);
+  __syncthreads();
+  for (int e = threadIdx.x; e < MLP_NPARAM; e += blockDim.x) atomicAdd(&grad[e], sgrad[e]);
+}
+
+// Adam (Kingma & Ba 2015) on the FP32 master weights, bias-corrected.
+__global__ void k_mlp_adam(float* __restrict__ p, const float* __restrict__ gr, float* __restrict__ m1,
+                           float* __restrict__ m2, float lr, float b1, float b2, float eps, float c1, float c2) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= MLP_NPARAM) return;
+  float gv = gr[e];
+  float a = b1 * m1[e] + (1.f - b1) * gv;
+  float b = b2 * m2[e] + (1.f - b2) * gv * gv;
+  m1[e] = a;
+  m2[e] = b;
+  p[e] -= lr * (a / c1) / (sqrtf(b / c2) + eps);
+}
+
+// FP32 master weights (W1 [64][40], b1, W2 [64][64], b2, W3 [8][64], b3) ->
+// BF16 pair layouts: w1 [64][24] (inputs 40..47 zero), w2 [64][32],
+// w3 [8][32], w2t [64][32] (transposed), w3t [64][8] (transposed, outputs
+// 8..15 zero), and the FP32 biases.
+__global__ void k_mlp_pack(const float* __restrict__ P, MlpDev m) {
+  const float* W1 = P;
+  const float* B1 = W1 + 64 * 40;
+  const float* W2 = B1 + 64;
+  const float* B2 = W2 + 64 * 64;
+  const float* W3 = B2 + 64;
+  const float* B3 = W3 + 8 * 64;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 64 * 32; e += gridDim.x * blockDim.x) {
+    const int r = e / 32, c = e % 32;
+    if (c < 24) {
+      float v0 = 2 * c < 40 ? W1[r * 40 + 2 * c] : 0.f, v1 = 2 * c + 1 < 40 ? W1[r * 40 + 2 * c + 1] : 0.f;
+      m.w1[r * 24 + c] = pack_bf16(v0, v1);
+    }
+    m.w2[r * 32 + c] = pack_bf16(W2[r * 64 + 2 * c], W2[r * 64 + 2 * c + 1]);
+    m.w2t[r * 32 + c] = pack_bf16(W2[(2 * c) * 64 + r], W2[(2 * c + 1) * 64 + r]);
+    if (r < 8) m.w3[r * 32 + c] = pack_bf16(W3[r * 64 + 2 * c], W3[r * 64 + 2 * c + 1]);
+    if (c < 8) {
+      float v0 = 2 * c < 8 ? W3[(2 * c) * 64 + r] : 0.f, v1 = 2 * c + 1 < 8 ? W3[(2 * c + 1) * 64 + r] : 0.f;
+      m.w3t[r * 8 + c] = pack_bf16(v0, v1);
+    }
+    if (e < 64) {
+      m.b1[e] = B1[e];
+      m.b2[e] = B2[e];
+    }
+    if (e < 8) m.b3[e] = B3[e];
+  }
+}
+
+// FP32 rows of 40 -> BF16 rows of 48 (24 words, the last 4 words zero).
+__global__ void k_rows_to_bf16(const float* __restrict__ X, uint32_t* __restrict__ Xb, int64_t n) {
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < n * 24;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = e / 24;
+    const int c = static_cast<int>(e % 24);
+    Xb[e] = c < 20 ? pack_bf16(X[r * 40 + 2 * c], X[r * 40 + 2 * c + 1]) : 0u;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers.
+
+size_t mlp_train_smem() { return sizeof(MlpSmem) + TRAIN_WARPS * sizeof(TrainTile) + MLP_NPARAM * sizeof(float); }
+
+cudaError_t mlp_setup() {
+  return cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(mlp_train_smem()));
+}
+cudaError_t launch_mlp_pack(const float* P, const MlpDev& m, cudaStream_t st) {
+  k_mlp_pack<<<8, 256, 0, st>>>(P, m);
+  return cudaGetLastError();
+}
+cudaError_t launch_mlp_infer(const uint32_t* X, float* Y, int64_t n, const MlpDev& m, int nsm, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int64_t tiles = (n + 15) / 16;
+  int grid = static_cast<int>(std::min<int64_t>((tiles + 3) / 4, static_cast<int64_t>(nsm) * 8));
+  k_mlp_infer<<<grid, 128, 0, st>>>(X, Y, n, m);
+  return cudaGetLastError();
+}
+cudaError_t launch_mlp_train(const float* X, const float* T, int64_t n, const MlpDev& m, float* grad, double* loss,
+                             int nsm, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int64_t tiles = (n + 15) / 16;
+  int grid = static_cast<int>(std::min<int64_t>((tiles + TRAIN_WARPS - 1) / TRAIN_WARPS, static_cast<int64_t>(nsm)));
+  k_mlp_train<<<grid, TRAIN_WARPS * 32, mlp_train_smem(), st>>>(X, T, n, 1.0 / (8.0 * static_cast<double>(n)), m,
+                                                                 grad, loss);
+  return cudaGetLastError();
+}
+cudaError_t launch_mlp_adam(float* p, const float* g, float* m1, float* m2, float lr, int step, cudaStream_t st) {
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  float c1 = 1.f - powf(b1, static_cast<float>(step)), c2 = 1.f - powf(b2, static_cast<float>(step));
+  k_mlp_adam<<<(MLP_NPARAM + 255) / 256, 256, 0, st>>>(p, g, m1, m2, lr, b1, b2, eps, c1, c2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rows_to_bf16(const float* X, uint32_t* Xb, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int grid = static_cast<int>(std::min<int64_t>((n * 24 + 255) / 256, 4096));
+  k_rows_to_bf16<<<grid, 256, 0, st>>>(X, Xb, n);
+  return cudaGetLastError();
+}
+
+// Device weight set: one allocation holding the BF16 layouts and biases.
+cudaError_t mlp_alloc(MlpDev* w) {
+  const size_t words = 64 * 24 + 64 * 32 + 8 * 32 + 64 * 32 + 64 * 8;
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, words * 4 + (64 + 64 + 8) * 4);
+  if (e != cudaSuccess) return e;
+  uint32_t* u = static_cast<uint32_t*>(p);
+  w->w1 = u;
+  w->w2 = w->w1 + 64 * 24;
+  w->w3 = w->w2 + 64 * 32;
+  w->w2t = w->w3 + 8 * 32;
+  w->w3t = w->w2t + 64 * 32;
+  float* f = reinterpret_cast<float*>(w->w3t + 64 * 8);
+  w->b1 = f;
+  w->b2 = f + 64;
+  w->b3 = f + 128;
+  return cudaMemsetAsync(p, 0, words * 4 + (64 + 64 + 8) * 4);
+}
+void mlp_free(MlpDev* w) {
+  if (w->w1) cudaFree(w->w1);
+  std::memset(w, 0, sizeof(*w));
+}
+
+// Seeded initialisation: hidden layers N(0, 1/fan_in), biases and the output
+// layer zero (the initial network adds nothing).
+void mlp_init_params(uint64_t seed, float* P) {
+  std::mt19937_64 rng(seed);
+  std::normal_distribution<double> nd(0.0, 1.0);
+  std::memset(P, 0, sizeof(float) * MLP_NPARAM);
+  for (int e = 0; e < 64 * 40; e++) P[e] = static_cast<float>(nd(rng) / std::sqrt(40.0));
+  float* W2 = P + 64 * 40 + 64;
+  for (int e = 0; e < 64 * 64; e++) W2[e] = static_cast<float>(nd(rng) / std::sqrt(64.0));
+}
+
+}  // namespace batsk
+
+using namespace batsk;
+
+struct bats_mlp {
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int nsm = 1;
+  float *P = nullptr, *M1 = nullptr, *M2 = nullptr, *G = nullptr;
+  double* loss = nullptr;
+  MlpDev w{};
+  int step = 0;
+  float *X = nullptr, *T = nullptr, *Y = nullptr;
+  uint32_t* Xb = nullptr;
+  int64_t cap = 0;
+};
+
+namespace {
+
+bool dev_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int mlp_reserve(bats_mlp_t* m, int64_t n) {
+  if (n <= m->cap) return BATS_OK;
+  cudaFree(m->X);
+  cudaFree(m->T);
+  cudaFree(m->Y);
+  cudaFree(m->Xb);
+  m->X = m->T = m->Y = nullptr;
+  m->Xb = nullptr;
+  m->cap = 0;
+  if (cudaMalloc(&m->X, n * 40 * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&m->T, n * 8 * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&m->Y, n * 8 * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&m->Xb, n * 24 * sizeof(uint32_t)) != cudaSuccess) {
+    cudaGetLastError();
+    return BATS_ERR_OUT_OF_MEMORY;
+  }
+  m->cap = n;
+  return BATS_OK;
+}
+
+int copy_in(bats_mlp_t* m, float* dst, const float* src, size_t count) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, count * sizeof(float),
+                                  dev_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, m->stream);
+  return e == cudaSuccess ? BATS_OK : BATS_ERR_CUDA;
+}
+
+int grad_pass(bats_mlp_t* m, const float* X, const float* T, int64_t n) {
+  if (!X || !T || n <= 0) return BATS_ERR_INVALID_ARG;
+  int rc = mlp_reserve(m, n);
+  if (rc) return rc;
+  if ((rc = copy_in(m, m->X, X, static_cast<size_t>(n) * 40)) || (rc = copy_in(m, m->T, T, static_cast<size_t>(n) * 8)))
+    return rc;
+  if (cudaMemsetAsync(m->G, 0, sizeof(float) * MLP_NPARAM, m->stream) != cudaSuccess ||
+      cudaMemsetAsync(m->loss, 0, sizeof(double), m->stream) != cudaSuccess ||
+      launch_mlp_train(m->X, m->T, n, m->w, m->G, m->loss, m->nsm, m->stream) != cudaSuccess)
+    return BATS_ERR_CUDA;
+  return BATS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bats_mlp_create(const float* params, uint64_t seed, void* cuda_stream, bats_mlp_t** out) {
+  if (!out) return BATS_ERR_INVALID_ARG;
+  *out = nullptr;
+  bats_mlp_t* m = new bats_mlp_t();
+  m->stream = static_cast<cudaStream_t>(cuda_stream);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&m->nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess && !m->stream) {
+    e = cudaStreamCreate(&m->stream);
+    m->own_stream = e == cudaSuccess;
+  }
+  if (e == cudaSuccess) e = mlp_setup();
+  if (e == cudaSuccess) e = cudaMalloc(&m->P, sizeof(float) * MLP_NPARAM * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&m->loss, sizeof(double));
+  if (e == cudaSuccess) e = mlp_alloc(&m->w);
+  if (e != cudaSuccess) {
+    bats_mlp_destroy(m);
+    return BATS_ERR_CUDA;
+  }
+  m->M1 = m->P + MLP_NPARAM;
+  m->M2 = m->P + 2 * MLP_NPARAM;
+  m->G = m->P + 3 * MLP_NPARAM;
+  int rc;
+  if (params) {
+    rc = bats_mlp_set_params(m, params);
+  } else {
+    std::vector<float> h(MLP_NPARAM);
+    mlp_init_params(seed, h.data());
+    rc = bats_mlp_set_params(m, h.data());
+  }
+  if (rc) {
+    bats_mlp_destroy(m);
+    return rc;
+  }
+  *out = m;
+  return BATS_OK;
+}
+
+void bats_mlp_destroy(bats_mlp_t* m) {
+  if (!m) return;
+  if (m->stream) cudaStreamSynchronize(m->stream);
+  cudaFree(m->P);
+  cudaFree(m->loss);
+  cudaFree(m->X);
+  cudaFree(m->T);
+  cudaFree(m->Y);
+  cudaFree(m->Xb);
+  mlp_free(&m->w);
+  if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
+  delete m;
+}
+
+int bats_mlp_set_params(bats_mlp_t* m, const float* params) {
+  if (!m || !params) return BATS_ERR_INVALID_ARG;
+  if (copy_in(m, m->P, params, MLP_NPARAM)) return BATS_ERR_CUDA;
+  if (cudaMemsetAsync(m->M1, 0, sizeof(float) * 2 * MLP_NPARAM, m->stream) != cudaSuccess) return BATS_ERR_CUDA;
+  m->step = 0;
+  if (launch_mlp_pack(m->P, m->w, m->stream) != cudaSuccess) return BATS_ERR_CUDA;
+  return cudaStreamSynchronize(m->stream) == cudaSuccess ? BATS_OK : BATS_ERR_CUDA;
+}
+
+int bats_mlp_get_params(bats_mlp_t* m, float* params) {
+  if (!m || !params) return BATS_ERR_INVALID_ARG;
+  cudaError_t e = cudaMemcpyAsync(params, m->P, sizeof(float) * MLP_NPARAM,
+                                  dev_ptr(params) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, m->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  return e == cudaSuccess ? BATS_OK : BATS_ERR_CUDA;
+}
+
+int bats_mlp_forward(bats_mlp_t* m, const float* X, int64_t n, float* Y) {
+  if (!m || !X || !Y || n <= 0) return BATS_ERR_INVALID_ARG;
+  int rc = mlp_reserve(m, n);
+  if (rc) return rc;
+  if ((rc = copy_in(m, m->X, X, static_cast<size_t>(n) * 40))) return rc;
+  cudaError_t e = launch_rows_to_bf16(m->X, m->Xb, n, m->stream);
+  if (e == cudaSuccess) e = launch_mlp_infer(m->Xb, m->Y, n, m->w, m->nsm, m->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(Y, m->Y, sizeof(float) * n * 8, dev_ptr(Y) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                        m->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  return e == cudaSuccess ? BATS_OK : BATS_ERR_CUDA;
+}
+
+int bats_mlp_loss_grad(bats_mlp_t* m, const float* X, const float* T, int64_t n, float* grad, double* loss) {
+  if (!m) return BATS_ERR_INVALID_ARG;
+  int rc = grad_pass(m, X, T, n);
+  if (rc) return rc;
+  double ls = 0.0;
+  cudaError_t e = cudaMemcpyAsync(&ls, m->loss, sizeof(double), cudaMemcpyDeviceToHost, m->stream);
+  if (e == cudaSuccess && grad)
+    e = cudaMemcpyAsync(grad, m->G, sizeof(float) * MLP_NPARAM,
+                        dev_ptr(grad) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, m->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  if (e != cudaSuccess) return BATS_ERR_CUDA;
+  if (loss) *loss = ls / (8.0 * static_cast<double>(n));
+  return BATS_OK;
+}
+
+int bats_mlp_train_step(bats_mlp_t* m, const float* X, const float* T, int64_t n, float lr, double* loss) {
+  if (!m || !(lr >= 0.f)) return BATS_ERR_INVALID_ARG;
+  int rc = grad_pass(m, X, T, n);
+  if (rc) return rc;
+  m->step++;
+  if (launch_mlp_adam(m->P, m->G, m->M1, m->M2, lr, m->step, m->stream) != cudaSuccess ||
+      launch_mlp_pack(m->P, m->w, m->stream) != cudaSuccess)
+    return BATS_ERR_CUDA;
+  if (loss) {
+    double ls = 0.0;
+    if (cudaMemcpyAsync(&ls, m->loss, sizeof(double), cudaMemcpyDeviceToHost, m->stream) != cudaSuccess ||
+        cudaStreamSynchronize(m->stream) != cudaSuccess)
+      return BATS_ERR_CUDA;
+    *loss = ls / (8.0 * static_cast<double>(n));
+  }
+  return BATS_OK;
+}
+
+}  // extern "C"

@@ -12,6 +12,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 #include <algorithm>
+#include <cuda_bf16.h>
 #include <type_traits>
 
 #include "bats_internal.h"
@@ -669,7 +670,7 @@ __device__ __forceinline__ void b0_face(const PhysDev& ph, int d, int i, int j, 
 // sliding a window along its line so that every cell is loaded and every
 // limited slope computed once; (4) per cell: flux differences x, y, z, the
 // sources, the update and (last stage) the CFL bound.
-template <bool MIXED, int LIM, bool HAS_B0>
+template <bool MIXED, int LIM, bool HAS_B0, bool LRN>
 __global__ void __launch_bounds__(STAGE_THREADS, MIXED ? 2 : 1) k_stage(const StageArgs a) {
   using R = typename StageCfg<MIXED>::R;
   constexpr int NFC = StageCfg<MIXED>::NFC;
@@ -765,27 +766,22 @@ __global__ void __launch_bounds__(STAGE_THREADS, MIXED ? 2 : 1) k_stage(const St
         auto cidx = [&](int c) { return c < 0 ? flo + (c + 2) : (c >= NC ? fhi + (c - NC) : fibase + c * fstride); };
         const int f0 = fhalf ? 5 : 0, nf = fhalf ? 4 : 5;
         R Wm1[8], W0[8], sm1[8];
-        {
-          R Wm2[8];
-          load_rot<R>(sT, rot, cidx(f0 - 2), Wm2);
-          load_rot<R>(sT, rot, cidx(f0 - 1), Wm1);
-          load_rot<R>(sT, rot, cidx(f0), W0);
+        R Wm2[8];  // kept along the line only for the network's inputs
+        load_rot<R>(sT, rot, cidx(f0 - 2), Wm2);
+        load_rot<R>(sT, rot, cidx(f0 - 1), Wm1);
+        load_rot<R>(sT, rot, cidx(f0), W0);
 #pragma unroll
-          for (int v = 0; v < NV; v++) sm1[v] = limit_<R>(LIM, Wm1[v] - Wm2[v], W0[v] - Wm1[v]);
-        }
+        for (int v = 0; v < NV; v++) sm1[v] = limit_<R>(LIM, Wm1[v] - Wm2[v], W0[v] - Wm1[v]);
 #pragma unroll 1
         for (int k = 0; k < nf; k++) {
           const int f = f0 + k;
-          R Wp[8], WL[8], WR[8];
+          R Wp[8], WL[8], WR[8], s0[8];
           load_rot<R>(sT, rot, cidx(f + 1), Wp);
 #pragma unroll
           for (int v = 0; v < NV; v++) {
-            R s0 = limit_<R>(LIM, W0[v] - Wm1[v], Wp[v] - W0[v]);
+            s0[v] = limit_<R>(LIM, W0[v] - Wm1[v], Wp[v] - W0[v]);
             WL[v] = Wm1[v] + R(0.5) * sm1[v];
-            WR[v] = W0[v] - R(0.5) * s0;
-            sm1[v] = s0;
-            Wm1[v] = W0[v];
-            W0[v] = Wp[v];
+            WR[v] = W0[v] - R(0.5) * s0[v];
           }
           R B0f[3] = {R(0), R(0), R(0)}, B0r[3];
           if constexpr (HAS_B0) {
@@ -804,6 +800,78 @@ __global__ void __launch_bounds__(STAGE_THREADS, MIXED ? 2 : 1) k_stage(const St
           R Fr[8];
 #pragma unroll
           for (int v = 0; v < NV; v++) Fr[v] = R(0.5) * (FL[v] + FR[v]) - R(0.5) * cmax * (UR[v] - UL[v]);
+          if constexpr (LRN) {
+            // network inputs: the 4 stencil cells f-2..f+1 and (WL + WR)/2 in
+            // the face frame, scaled by rho_ref = mean stencil density and
+            // c_ref = cmax (u / c_ref, B / (sqrt(rho_ref) c_ref), p / (rho_ref c_ref^2))
+            const int64_t gface = (static_cast<int64_t>(blk) * 3 + fd) * NFACE + fi;
+            const R rho_ref = R(0.25) * (((Wm2[0] + Wm1[0]) + W0[0]) + Wp[0]);
+            const R c_ref = cmax;
+            const R sq = Ops<R>::sqrt_(rho_ref);
+            if (a.kind >= 3) {
+              const R ir = Ops<R>::div_(R(1), rho_ref), ic = Ops<R>::div_(R(1), c_ref);
+              const R ib = Ops<R>::div_(R(1), sq * c_ref), ip = Ops<R>::div_(R(1), rho_ref * c_ref * c_ref);
+              float xin[40];
+#pragma unroll
+              for (int sidx = 0; sidx < 5; sidx++) {
+                const R* Wsrc = sidx == 0 ? Wm2 : (sidx == 1 ? Wm1 : (sidx == 2 ? W0 : Wp));
+                R wv[8];
+#pragma unroll
+                for (int v = 0; v < NV; v++) wv[v] = sidx < 4 ? Wsrc[v] : R(0.5) * (WL[v] + WR[v]);
+                xin[8 * sidx + 0] = static_cast<float>(wv[0] * ir);
+#pragma unroll
+                for (int c = 1; c < 4; c++) xin[8 * sidx + c] = static_cast<float>(wv[c] * ic);
+#pragma unroll
+                for (int c = 4; c < 7; c++) xin[8 * sidx + c] = static_cast<float>(wv[c] * ib);
+                xin[8 * sidx + 7] = static_cast<float>(wv[7] * ip);
+              }
+              if (a.kind == 3) {
+                uint32_t* dst = a.Xb + gface * 24;
+#pragma unroll
+                for (int q = 0; q < 20; q++) {
+                  __nv_bfloat162 v2 = __floats2bfloat162_rn(xin[2 * q], xin[2 * q + 1]);
+                  dst[q] = *reinterpret_cast<uint32_t*>(&v2);
+                }
+#pragma unroll
+                for (int q = 20; q < 24; q++) dst[q] = 0u;
+              } else {
+                float* dst = a.Xf + gface * 40;
+#pragma unroll
+                for (int q = 0; q < 40; q++) dst[q] = xin[q];
+                double* fo = a.Fd + gface * 8;
+                fo[0] = Fr[0];
+                fo[1 + fd] = Fr[1];
+                fo[1 + fd1] = Fr[2];
+                fo[1 + fd2] = Fr[3];
+                fo[4 + fd] = Fr[4];
+                fo[4 + fd1] = Fr[5];
+                fo[4 + fd2] = Fr[6];
+                fo[7] = Fr[7];
+              }
+            } else if (a.learned) {
+              // correction back in flux units, clipped to the Rusanov dissipation
+              const float* yv = a.Y + gface * 8;
+              const R sc0 = rho_ref * c_ref, sc1 = rho_ref * c_ref * c_ref, sc4 = sq * c_ref * c_ref;
+              const R sc7 = rho_ref * c_ref * c_ref * c_ref;
+#pragma unroll
+              for (int v = 0; v < NV; v++) {
+                const R sc = v == 0 ? sc0 : (v < 4 ? sc1 : (v < 7 ? sc4 : sc7));
+                R dF = R(yv[v]) * sc;
+                const R lim = Ops<R>::abs_(R(0.5) * cmax * (UR[v] - UL[v]));
+                dF = dF > lim ? lim : dF;
+                dF = dF < -lim ? -lim : dF;
+                Fr[v] = Fr[v] + dF;
+              }
+            }
+          }
+#pragma unroll
+          for (int v = 0; v < NV; v++) {
+            Wm2[v] = Wm1[v];
+            sm1[v] = s0[v];
+            Wm1[v] = W0[v];
+            W0[v] = Wp[v];
+          }
+          if (a.kind >= 3) continue;
           fcol[0 * NFACE + fi] = Fr[0];
           fcol[(1 + fd) * NFACE + fi] = Fr[1];
           fcol[(1 + fd1) * NFACE + fi] = Fr[2];
@@ -816,6 +884,7 @@ __global__ void __launch_bounds__(STAGE_THREADS, MIXED ? 2 : 1) k_stage(const St
         }
       }
       __syncthreads();
+      if (a.kind >= 3) continue;  // features / dumps only
 
       // 4. per cell: flux differences, sources, update, CFL bound
       R smax_loc = R(0);
@@ -1138,22 +1207,27 @@ size_t stage_smem_bytes(bool mixed) {
 }
 
 using StageFn = void (*)(const StageArgs);
+template <bool MIXED, bool LRN>
+StageFn stage_fn_l(int lim, bool b0) {
+  if (lim == 1) return b0 ? k_stage<MIXED, 1, true, LRN> : k_stage<MIXED, 1, false, LRN>;
+  return b0 ? k_stage<MIXED, 0, true, LRN> : k_stage<MIXED, 0, false, LRN>;
+}
 template <bool MIXED>
-StageFn stage_fn(int lim, bool b0) {
-  if (lim == 1) return b0 ? k_stage<MIXED, 1, true> : k_stage<MIXED, 1, false>;
-  return b0 ? k_stage<MIXED, 0, true> : k_stage<MIXED, 0, false>;
+StageFn stage_fn(int lim, bool b0, bool lrn = false) {
+  return lrn ? stage_fn_l<MIXED, true>(lim, b0) : stage_fn_l<MIXED, false>(lim, b0);
 }
 
 cudaError_t stage_setup(int occ[2]) {
   cudaError_t e = cudaSuccess;
   for (int lim = 0; lim < 2 && e == cudaSuccess; lim++)
-    for (int b0 = 0; b0 < 2 && e == cudaSuccess; b0++) {
-      e = cudaFuncSetAttribute(stage_fn<false>(lim, b0), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               static_cast<int>(StageCfg<false>::SMEM));
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(stage_fn<true>(lim, b0), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(StageCfg<true>::SMEM));
-    }
+    for (int b0 = 0; b0 < 2 && e == cudaSuccess; b0++)
+      for (int lrn = 0; lrn < 2 && e == cudaSuccess; lrn++) {
+        e = cudaFuncSetAttribute(stage_fn<false>(lim, b0, lrn), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(StageCfg<false>::SMEM));
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(stage_fn<true>(lim, b0, lrn), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   static_cast<int>(StageCfg<true>::SMEM));
+      }
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_debug_fill, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(sizeof(double) * (NV * NTILE + 3 * 128 * NV)));
@@ -1168,8 +1242,9 @@ cudaError_t stage_setup(int occ[2]) {
 
 cudaError_t launch_stage_kernel(bool mixed, int grid, cudaStream_t st, const StageArgs& a) {
   const bool b0 = a.ph.b0 != B0_NONE;
-  if (mixed) stage_fn<true>(a.ph.limiter, b0)<<<grid, STAGE_THREADS, StageCfg<true>::SMEM, st>>>(a);
-  else stage_fn<false>(a.ph.limiter, b0)<<<grid, STAGE_THREADS, StageCfg<false>::SMEM, st>>>(a);
+  const bool lrn = a.learned || a.kind >= 3;
+  if (mixed) stage_fn<true>(a.ph.limiter, b0, lrn)<<<grid, STAGE_THREADS, StageCfg<true>::SMEM, st>>>(a);
+  else stage_fn<false>(a.ph.limiter, b0, lrn)<<<grid, STAGE_THREADS, StageCfg<false>::SMEM, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,171 @@
+"""The learned flux correction on the GPU against the CPU oracle.
+
+Network forward and gradient: the GPU rounds inputs, weights and hidden
+activations to BF16 and accumulates in FP32; the oracle runs FP64 on the same
+BF16-representable weights and inputs.  With 8-bit mantissas per layer the
+expected relative difference is a few 2^-8, so the bound is 2e-2 (relative L2
+norm), as for any BF16 network against an FP64 evaluation.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2501_06717_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2501_06717_gb300 import bats
+    bats.lib()
+    return bats
+
+
+def bf16(a):
+    """Round float32 values to the nearest BF16 (ties to even), from the format:
+    keep the top 16 bits after adding half an ulp of the dropped part."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return r.view(np.float32)
+
+
+def _net(seed, scale=0.3):
+    rng = np.random.default_rng(seed)
+    P = rng.normal(0, scale, size=O.MLP_NPARAM).astype(np.float32)
+    return bf16(P)
+
+
+def _relnorm(a, b):
+    return float(np.linalg.norm(np.asarray(a, float) - b) / np.linalg.norm(b))
+
+
+def test_bf16_rounding_helper():
+    x = np.array([1.0, 1.00390625, 1.005859375, -2.5], np.float32)  # 1 + 2^-8 is a tie -> even (1.0)
+    assert np.array_equal(bf16(x), np.array([1.0, 1.0, 1.0078125, -2.5], np.float32))
+
+
+def test_network_forward_matches_oracle(B):
+    P = _net(1)
+    rng = np.random.default_rng(2)
+    X = bf16(rng.normal(size=(2000, 40)))
+    with_mlp = B.Mlp(P)
+    Y = with_mlp.forward(X)
+    Yo = np.array([O.mlp_forward(P.astype(np.float64), x.astype(np.float64))[2] for x in X])
+    assert _relnorm(Y, Yo) <= 2e-2
+
+
+def test_network_gradient_matches_oracle(B):
+    P = _net(3)
+    rng = np.random.default_rng(4)
+    X = bf16(rng.normal(size=(3000, 40)))
+    T = rng.normal(size=(3000, 8)).astype(np.float32)
+    m = B.Mlp(P)
+    loss, g = m.loss_grad(X, T)
+    lo, go = O.mlp_loss_grad(P.astype(np.float64), X.astype(np.float64), T.astype(np.float64))
+    assert loss == pytest.approx(lo, rel=1e-2)
+    assert _relnorm(g, go) <= 2e-2
+    # every parameter group
+    starts = np.cumsum([0, 64 * 40, 64, 64 * 64, 64, 8 * 64, 8])
+    for a, b in zip(starts[:-1], starts[1:]):
+        assert _relnorm(g[a:b], go[a:b]) <= 3e-2, (a, b)
+
+
+def test_training_fits_a_teacher_network(B):
+    teacher = _net(5, scale=0.2)
+    rng = np.random.default_rng(6)
+    X = bf16(rng.normal(size=(8192, 40)))
+    T = np.array([O.mlp_forward(teacher.astype(np.float64), x.astype(np.float64))[2] for x in X[:8192]],
+                 dtype=np.float32)
+    m = B.Mlp(seed=7)
+    l0, _ = m.loss_grad(X, T)
+    for it in range(400):
+        sl = slice((it * 1024) % 8192, (it * 1024) % 8192 + 1024)
+        m.train_step(np.ascontiguousarray(X[sl]), np.ascontiguousarray(T[sl]), 3e-3)
+    l1, _ = m.loss_grad(X, T)
+    assert l1 < 0.2 * l0, (l0, l1)
+
+
+def test_zero_network_stage_equals_plain_bitwise(B):
+    q = W.blast()
+    with B.Solver(q) as s:
+        s.set_state(0, q.U0)
+        s.step(3, 0.8)
+        ref = s.get_state(0)
+    with B.Solver(q) as s:
+        s.set_mlp(np.zeros(B.BATS_MLP_NPARAM, np.float32))
+        s.set_state(0, q.U0)
+        s.step(3, 0.8)
+        assert np.array_equal(s.get_state(0), ref)
+        assert s.launch_count() == 3 * (2 + 2 * 3)
+
+
+def test_learned_stage_matches_oracle(B):
+    q = W.blast()
+    P = _net(8, scale=0.15)
+    with B.Solver(q) as s:
+        s.set_mlp(P)
+        s.set_state(0, q.U0)
+        s.step_dt(2, 2e-3)
+        Ug = s.get_state(0)
+    ql = W.Problem(**{**q.__dict__, "learned": 1, "mlp": P.astype(np.float64)})
+    Uo, _, _ = O.run(ql, q.U0, 2, dt=2e-3)
+    U0, _, _ = O.run(q, q.U0, 2, dt=2e-3)
+    scale = np.abs(Uo).reshape(8, -1).max(1)
+    err = (np.abs(Ug - Uo).reshape(8, -1).max(1) / scale).max()
+    effect = (np.abs(Uo - U0).reshape(8, -1).max(1) / scale).max()
+    print("learned stage: max scaled error", err, "effect of the network", effect)
+    assert effect > 1e-4          # the network does change the solution
+    assert err <= 3e-2 * effect   # and the GPU reproduces that change to BF16 accuracy
+
+
+def test_face_data_fluxes_reproduce_the_residual(B):
+    """The dumped plain fluxes, differenced on the host, give the oracle's
+    residual (no sources: Powell off, no B0)."""
+    q = W.orszag_tang()
+    with B.Solver(q) as s:
+        s.set_state(0, q.U0)
+        X, F = s.face_data(0)
+    nb = q.nb
+    F = F.reshape(nb, 3, 64, 9, 8)   # block, direction, line (a + 8 b), f, variable
+    dx = 1.0 / 16
+    R = np.zeros((8, nb, 8, 8, 8))   # v, block, k, j, i
+    for d in range(3):
+        dF = (F[:, d, :, 1:, :] - F[:, d, :, :-1, :]) / dx     # block, line, cell along d, v
+        dF = dF.reshape(nb, 8, 8, 8, 8)                         # block, b, a, c, v
+        if d == 0:
+            R -= dF.transpose(4, 0, 1, 2, 3)                    # (b=k, a=j, c=i)
+        elif d == 1:
+            R -= dF.transpose(4, 0, 1, 3, 2)                    # (b=k, a=i, c=j)
+        else:
+            R -= dF.transpose(4, 0, 3, 1, 2)                    # (b=j, a=i, c=k)
+    Ro = O.residual(q, q.U0)
+    scale = np.abs(Ro).reshape(8, -1).max(1)
+    scale = np.where(scale > 0, scale, 1.0)  # u_z, B_z: identically zero in this z-invariant state
+    assert (np.abs(R - Ro).reshape(8, -1).max(1) / scale).max() <= 1e-12
+    # inputs of a uniform state in closed form
+    qu = W.Problem("u", (0, 0, 0), (1, 1, 1), (1, 1, 1), W.as_leaf_array([(0, 0, 0, 0)]), (W.BC_PERIODIC,) * 6)
+    rho, u, Bv, p = 2.0, np.array([0.3, -0.1, 0.2]), np.array([0.5, 0.2, -0.4]), 1.5
+    W.uniform_state(qu, [rho, *u, *Bv, p])
+    with B.Solver(qu) as s:
+        s.set_state(0, qu.U0)
+        Xu, _ = s.face_data(0)
+    cf = O.fast_speed(qu.gamma, np.r_[rho, u, Bv, p], Bv, 0)
+    c = abs(u[0]) + cf
+    face = Xu.reshape(1, 3, 576, 40)[0, 0, 0]
+    expect = np.r_[1.0, u / c, Bv / (np.sqrt(rho) * c), p / (rho * c * c)]
+    assert np.allclose(face.reshape(5, 8), expect[None, :], rtol=1e-6)
+
+
+def test_learned_graph_replay_equals_eager(B):
+    q = W.blast()
+    P = _net(9, scale=0.1)
+    outs = []
+    for graph in (0, 1):
+        with B.Solver(q, precision=B.BATS_MIXED, persistent=1, use_graph=graph) as s:
+            s.set_mlp(P)
+            s.set_state(0, q.U0)
+            s.step(2, 0.8)
+            s.step(2, 0.8)
+            outs.append(s.get_state(0))
+    assert np.array_equal(outs[0], outs[1])
