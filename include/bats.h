@@ -209,8 +209,9 @@ int bats_set_mlp(bats_t* h, const float* params);
  * ((block * 3 + d) * 576 + line * 9 + f), line = a + 8 b over the two
  * transverse cell indices in increasing axis order, f = 0..8 the face on the
  * low side of cell f along d) the 40 network inputs X (float, host or device,
- * n_faces x 40) and the plain Rusanov flux F (double, n_faces x 8, x/y/z
- * components), of the current state (stage_input 0) or of the midpoint
+ * n_faces x 40; nullable) and F (double, n_faces x 10): the plain Rusanov flux
+ * (8, x/y/z components) and the face's rho_ref and c_ref, of the current
+ * state (stage_input 0) or of the midpoint
  * stage-2 input U* = U + (dt/2) R(U) (stage_input 1, dt > 0).  The state is
  * not changed.  n_faces = 1728 * n_blocks of the grid. */
 int bats_debug_face_data(bats_t* h, int grid, int stage_input, double dt, float* X, double* F, size_t n_faces);

@@ -294,15 +294,16 @@ def bats_set_mlp(h, params):
     _check(h, lib().bats_set_mlp(h, p))
 
 
-def bats_debug_face_data(h, grid, nblocks, stage_input=0, dt=0.0, X=None, F=None):
-    """Network inputs (n_faces x 40 float32) and plain Rusanov fluxes
-    (n_faces x 8 float64) of every face of grid `grid`."""
+def bats_debug_face_data(h, grid, nblocks, stage_input=0, dt=0.0, X=None, F=None, with_inputs=True):
+    """Network inputs (n_faces x 40 float32, or None) and F (n_faces x 10
+    float64: the plain Rusanov flux, rho_ref, c_ref) of every face of grid
+    `grid`."""
     nf = nblocks * 3 * 576
-    if X is None:
+    if X is None and with_inputs:
         X = np.zeros((nf, 40), np.float32)
     if F is None:
-        F = np.zeros((nf, 8), np.float64)
-    px, nx = _ptr_and_size(X)
+        F = np.zeros((nf, 10), np.float64)
+    px = _ptr_and_size(X)[0] if X is not None else None
     pf, _ = _ptr_and_size(F)
     _check(h, lib().bats_debug_face_data(h, int(grid), int(stage_input), float(dt), px, pf, nf))
     return X, F
@@ -467,8 +468,8 @@ class Solver:
     def set_mlp(self, params):
         bats_set_mlp(self.h, params)
 
-    def face_data(self, grid=0, stage_input=0, dt=0.0):
-        return bats_debug_face_data(self.h, grid, self.problems[grid].nb, stage_input, dt)
+    def face_data(self, grid=0, stage_input=0, dt=0.0, with_inputs=True):
+        return bats_debug_face_data(self.h, grid, self.problems[grid].nb, stage_input, dt, with_inputs=with_inputs)
 
     def set_launch(self, persistent=0, blocks_per_cta=1, ctas_per_sm=0, use_graph=0):
         bats_set_launch(self.h, persistent, blocks_per_cta, ctas_per_sm, use_graph)

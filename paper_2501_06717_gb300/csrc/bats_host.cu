@@ -808,12 +808,12 @@ int bats_debug_face_data(bats_t* h, int grid, int stage_input, double dt, float*
   if (rc) return rc;
   const GridDev& G = h->grids_h[grid];
   const size_t nf = static_cast<size_t>(G.nb) * 3 * NFACE;
-  if (!X || !F || n_faces != nf) return fail(h, BATS_ERR_INVALID_ARG, "face buffer size mismatch");
+  if (!F || n_faces != nf) return fail(h, BATS_ERR_INVALID_ARG, "face buffer size mismatch");
   if (stage_input && !(dt > 0.0)) return fail(h, BATS_ERR_INVALID_ARG, "stage_input needs dt > 0");
   const size_t all = static_cast<size_t>(h->nbt) * 3 * NFACE;
   float* Xf = nullptr;
   double* Fd = nullptr;
-  if ((rc = dev_alloc(h, &Xf, all * 40)) || (rc = dev_alloc(h, &Fd, all * 8))) {
+  if ((X && (rc = dev_alloc(h, &Xf, all * 40))) || (rc = dev_alloc(h, &Fd, all * 10))) {
     cudaFree(Xf);
     return rc;
   }
@@ -855,11 +855,11 @@ int bats_debug_face_data(bats_t* h, int grid, int stage_input, double dt, float*
     rc = launch_stage_one(h, a);
   }
   const size_t off = static_cast<size_t>(G.block0) * 3 * NFACE;
-  if (e == cudaSuccess && !rc)
+  if (e == cudaSuccess && !rc && X)
     e = cudaMemcpyAsync(X, Xf + off * 40, nf * 40 * sizeof(float),
                         is_device_ptr(X) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess && !rc)
-    e = cudaMemcpyAsync(F, Fd + off * 8, nf * 8 * sizeof(double),
+    e = cudaMemcpyAsync(F, Fd + off * 10, nf * 10 * sizeof(double),
                         is_device_ptr(F) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   cudaFree(Xf);

@@ -93,7 +93,7 @@ struct StageArgs {
   int32_t learned;        // kinds 0-2: add the clipped, rescaled correction Y
   uint32_t* Xb;           // kind 3: BF16 features, 24 words (48 columns) per face
   float* Xf;              // kind 4: FP32 features, 40 per face
-  double* Fd;             // kind 4: plain Rusanov flux, 8 per face (x, y, z components)
+  double* Fd;             // kind 4: plain Rusanov flux (8, x/y/z components), rho_ref, c_ref per face
   const float* Y;         // normalised correction in the face frame, 8 per face
 };
 

@@ -835,10 +835,14 @@ __global__ void __launch_bounds__(STAGE_THREADS, MIXED ? 2 : 1) k_stage(const St
 #pragma unroll
                 for (int q = 20; q < 24; q++) dst[q] = 0u;
               } else {
-                float* dst = a.Xf + gface * 40;
+                if (a.Xf) {
+                  float* dst = a.Xf + gface * 40;
 #pragma unroll
-                for (int q = 0; q < 40; q++) dst[q] = xin[q];
-                double* fo = a.Fd + gface * 8;
+                  for (int q = 0; q < 40; q++) dst[q] = xin[q];
+                }
+                double* fo = a.Fd + gface * 10;
+                fo[8] = rho_ref;
+                fo[9] = c_ref;
                 fo[0] = Fr[0];
                 fo[1 + fd] = Fr[1];
                 fo[1 + fd1] = Fr[2];
