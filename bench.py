@@ -145,6 +145,53 @@ def run_reference(args, rank, world):
 
 
 # --------------------------------------------------------------------------
+# Learned form: train on solver-made pairs, then time and score it
+
+
+def learned_form_summary(stream, steps=32):
+    """Blast at 1x (120 blocks) with the trained network against the plain
+    scheme at 1x and 2x (960 blocks), FP64 state, fixed dt; times from CUDA
+    events around graph replays of `steps` coarse steps (2 * steps fine)."""
+    import torch
+    from paper_2501_06717_gb300 import bats, learn
+    t0 = time.perf_counter()
+    X, Y = learn.make_pairs(variants=[101, 102, 103, 104, 105, 106], snapshots=(4, 12), keep=0.3)
+    P, hist = learn.train(X, Y, epochs=6, lr=1e-3)
+    t_train = time.perf_counter() - t0
+    e_plain, e_learn = learn.evaluate(P, nsteps=16)
+    coarse, fine = W.blast(), W.blast(resolution=2)
+
+    def timed(prob, params, nsteps, dt):
+        with bats.Solver(prob, stream=stream, persistent=1, use_graph=1) as s:
+            if params is not None:
+                s.set_mlp(params)
+            s.set_state(0, prob.U0)
+            s.step_dt(nsteps, dt)   # capture
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.step_dt(nsteps, dt)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1)
+
+    with bats.Solver(coarse) as s:
+        s.set_state(0, coarse.U0)
+        dtc = 0.5 * s.dt(0, 0.8)
+    ms_learn = timed(coarse, P, steps, dtc)
+    ms_plain1 = timed(coarse, None, steps, dtc)
+    ms_plain2 = timed(fine, None, 2 * steps, 0.5 * dtc)
+    return {"workload": "spherical blast: 120 blocks (1x) with the trained network vs plain 1x and plain 2x "
+                        "(960 blocks), FP64 state, fixed dt, CUDA graph",
+            "pairs": int(X.shape[0]), "train_s": t_train, "loss_first_last_epoch": [hist[0], hist[-1]],
+            "error_vs_restricted_2x": {"plain_1x": e_plain, "learned_1x": e_learn},
+            "ms_per_coarse_step": {"learned_1x": ms_learn / steps, "plain_1x": ms_plain1 / steps,
+                                   "plain_2x_two_fine_steps": ms_plain2 / steps},
+            "cell_updates_per_s_learned_1x": coarse.ncells * steps / (ms_learn * 1e-3)}
+
+
+# --------------------------------------------------------------------------
 # Clocks during the timed region
 
 
@@ -202,6 +249,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--grids", type=int, default=64, help="first N grids of the batched workload")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-form summary")
+    ap.add_argument("--learned-only", action="store_true", help="only the learned-form summary (profiling)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -213,6 +262,11 @@ def main():
         return run_reference(args, rank, world)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
+    if args.learned_only:
+        import torch
+        torch.cuda.set_device(local)
+        print(json.dumps({"learned_form": learned_form_summary(torch.cuda.Stream())}), flush=True)
+        return 0
 
     # inputs and the CPU baseline before any CUDA call (spawned pool only)
     problems, desc = make_workload(args.workload, rank, processes=min(16, os.cpu_count() or 1), grids=args.grids)
@@ -325,6 +379,10 @@ def main():
         fp64 = cells * args.fp64_steps / (e0.elapsed_time(e1) * 1e-3)
         s64.close()
 
+    learned = None
+    if rank == 0 and world == 1 and not args.no_learned and args.workload == "batched":
+        learned = learned_form_summary(stream)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -348,6 +406,7 @@ def main():
             "gpu_launches": launches,
             "clocks": clk,
             "fp64_value": fp64,
+            "learned_form": learned,
             "stage_share": stage_ms / stage_total_ms if stage_total_ms > 0 else None,
         }
         if tune:

@@ -182,28 +182,44 @@ __device__ __forceinline__ void prim64(const double U[8], double gm1, double W[8
   W[7] = gm1 * ((U[7] - ke) - me);
 }
 
-// Mixed form: FP32 primitives of an FP64 state, with the pressure recovered in
-// FP64 (the cancellation e1 - rho u^2/2 - B1^2/2 is done in FP64; 1/rho by an
-// FP32 estimate plus one FP64 Newton-Raphson step).
+// Mixed form: FP32 primitives of an FP64 state.  The pressure comes from the
+// difference p/(gamma-1) = e1 - S, S = m.m/(2 rho) + B1.B1/2.  Where S <= e1/2
+// the difference is at least half of e1 and FP32 operands give p to about
+// 2e-7; where S > e1/2 (low beta, high Mach: the subtraction cancels) it is
+// recomputed in FP64, 1/rho by an FP32 estimate plus one FP64 Newton-Raphson
+// step.  *p64 (optional) receives e1 - S as a double (sign and finiteness
+// checks).
 __device__ __forceinline__ void prim_mixed(const double U[8], float gm1f, float W[8], double* p64 = nullptr) {
-  float rho32 = d2f_int(U[0]);
-  float rinv32 = rcp_approx(rho32);
-  double r0 = f2d_int(rinv32);
-  double e = fma(-U[0], r0, 1.0);
-  double rinv = fma(r0, e, r0);
-  double mm = U[1] * U[1] + U[2] * U[2] + U[3] * U[3];
-  double bb = U[4] * U[4] + U[5] * U[5] + U[6] * U[6];
-  double x = fma(-0.5, bb, U[7]);
-  x = fma(-0.5 * mm, rinv, x);
-  float rf = d2f_int(rinv);
+  const float rho32 = d2f_int(U[0]);
+  const float rinv32 = rcp_approx(rho32);
+  const float m0 = d2f_int(U[1]), m1 = d2f_int(U[2]), m2 = d2f_int(U[3]);
+  const float b0 = d2f_int(U[4]), b1 = d2f_int(U[5]), b2 = d2f_int(U[6]);
+  const float e32 = d2f_int(U[7]);
+  const float ke = 0.5f * (m0 * m0 + m1 * m1 + m2 * m2) * rinv32;
+  const float me = 0.5f * (b0 * b0 + b1 * b1 + b2 * b2);
+  const float sum = ke + me;
+  float x32 = e32 - sum;
+  double x;
+  if (sum > 0.5f * e32) {
+    double r0 = f2d_int(rinv32);
+    double e = fma(-U[0], r0, 1.0);
+    double rinv = fma(r0, e, r0);
+    double mm = U[1] * U[1] + U[2] * U[2] + U[3] * U[3];
+    double bb = U[4] * U[4] + U[5] * U[5] + U[6] * U[6];
+    x = fma(-0.5, bb, U[7]);
+    x = fma(-0.5 * mm, rinv, x);
+    x32 = d2f_int(x);
+  } else {
+    x = f2d_int(x32);
+  }
   W[0] = rho32;
-  W[1] = d2f_int(U[1]) * rf;
-  W[2] = d2f_int(U[2]) * rf;
-  W[3] = d2f_int(U[3]) * rf;
-  W[4] = d2f_int(U[4]);
-  W[5] = d2f_int(U[5]);
-  W[6] = d2f_int(U[6]);
-  W[7] = d2f_int(x) * gm1f;
+  W[1] = m0 * rinv32;
+  W[2] = m1 * rinv32;
+  W[3] = m2 * rinv32;
+  W[4] = b0;
+  W[5] = b1;
+  W[6] = b2;
+  W[7] = x32 * gm1f;
   if (p64) *p64 = x;
 }
 
