@@ -62,7 +62,7 @@ def _kernel_sha():
 
 def make_workload(name, rank=0, processes=None, grids=64):
     if name == "batched":
-        probs = W.batched_grids(seed=20250112 + rank, processes=processes)[:grids]
+        probs = W.batched_grids(seed=20250112 + rank, processes=processes, first=grids)
         return probs, "%d independent periodic block-adaptive grids, 64-4096 blocks of 8^3 cells " \
             "(log-uniform, seed %d), smooth Fourier states" % (len(probs), 20250112 + rank)
     if name == "blast":
@@ -70,6 +70,18 @@ def make_workload(name, rank=0, processes=None, grids=64):
     if name == "magnetosphere":
         return [W.magnetosphere()], "magnetosphere-like grid, 5 levels, dipole B0, body r=2.5 (3872 blocks)"
     raise ValueError(name)
+
+
+def reduce_over_ranks(ms, cells, device):
+    """Max of the timed-region durations and sum of the cells over all ranks
+    (each rank advances its own batch: weak scaling, no data-path collective)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(cells)], dtype=torch.float64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(c.item())
 
 
 # --------------------------------------------------------------------------
@@ -324,13 +336,7 @@ def main():
     stage_ms = solver.timings()[bats.BATS_PHASE_STAGE]
     stage_total_ms = solver.timings()[bats.BATS_PHASE_TOTAL]
     if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        c = torch.tensor([float(cells)], device="cuda")
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        total_cells = c.item()
+        ms, total_cells = reduce_over_ranks(ms, cells, "cuda")
     else:
         total_cells = cells
     value = total_cells * args.steps / (ms * 1e-3)

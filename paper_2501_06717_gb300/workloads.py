@@ -448,13 +448,16 @@ def _smooth_grid_job(args):
     return random_smooth_grid(*args)
 
 
-def batched_grids(n_grids=64, seed=20250112, lo_blocks=64, hi_blocks=4096, processes=None):
+def batched_grids(n_grids=64, seed=20250112, lo_blocks=64, hi_blocks=4096, processes=None, first=None):
     """n_grids independent grids with log-uniform leaf targets in
-    [lo_blocks, hi_blocks].  Each grid depends only on its own seed, so the
-    result does not depend on `processes` (a spawn-context pool when > 1)."""
+    [lo_blocks, hi_blocks] (only the first `first` of them are built when
+    given).  Each grid depends only on its own seed, so the result does not
+    depend on `processes` (a spawn-context pool when > 1)."""
     rng = np.random.default_rng(seed)
     targets = np.exp(rng.uniform(math.log(lo_blocks), math.log(hi_blocks), size=n_grids)).astype(int)
     jobs = [(int(t), seed * 1000 + i) for i, t in enumerate(targets)]
+    if first is not None:
+        jobs = jobs[:first]
     if processes and processes > 1:
         import multiprocessing as mp
         with mp.get_context("spawn").Pool(processes) as pool:
