@@ -77,7 +77,7 @@ typedef struct {
   int32_t limiter, rk, b0, powell;
   double b0_param[12];   /* UNIFORM: B0; DIPOLE: moment m; LINEAR: B0c(3) + G(3x3 row-major) */
   int32_t learned;       /* 1 = add the MLP flux correction */
-  int32_t pad_;
+  int32_t no_fallback;   /* test switch: 1 keeps a learned block update even where it is non-physical */
   const double* mlp;     /* MLP_NPARAM weights (W1,b1,W2,b2,W3,b3), row-major [out][in] */
 } or_desc;
 
@@ -866,41 +866,78 @@ int or_residual(const or_desc* d, const double* Uin, double* R) {
   return OR_OK;
 }
 
-/* One stage.  kind 0: Uout = Ubase + c R(Uin)   (midpoint stages, SSP-RK2 stage 1)
- *             kind 1: Uout = 0.5 Ubase + 0.5 (Uin + c R(Uin))   (SSP-RK2 stage 2)
- * Body cells (centre radius < body_r) are set to the body state. */
-int or_stage(const or_desc* d, const double* Uin, const double* Ubase, double* Uout, int kind, double c) {
+/* The stage output of block b from its residual Rb:
+ *   kind 0: Uout = Ubase + c R(Uin)   (midpoint stages, SSP-RK2 stage 1)
+ *   kind 1: Uout = 0.5 Ubase + 0.5 (Uin + c R(Uin))   (SSP-RK2 stage 2)
+ * Body cells (centre radius < body_r) are set to the body state.  Ob is
+ * [8][512].  Returns 1 when every non-body cell of the result is physical:
+ * all 8 values finite, rho > 0 and p > 0 (p from Eq. 5). */
+static int block_update(grid_t* G, int b, const double* Rb, const double* Uin, const double* Ubase, int kind,
+                        double c, double* Ob) {
+  const or_desc* d = G->d;
+  const int32_t* L = d->leaves + 4 * b;
+  int nb = G->nb, ok = 1;
+  for (int k = 0; k < NC; k++)
+    for (int j = 0; j < NC; j++)
+      for (int i = 0; i < NC; i++) {
+        int cidx = (k * NC + j) * NC + i;
+        double xc[3], Uc[NV], W[NV];
+        cell_centre(G, L[0], L, i, j, k, xc);
+        int body = in_body(d, xc);
+        for (int v = 0; v < NV; v++) {
+          long gidx = ((long)v * nb + b) * NCELL + cidx;
+          double r = Rb[v * NCELL + cidx];
+          double o;
+          if (body) o = G->Ubody[v];
+          else if (kind == 0) o = Ubase[gidx] + c * r;
+          else o = 0.5 * Ubase[gidx] + 0.5 * (Uin[gidx] + c * r);
+          Ob[v * NCELL + cidx] = o;
+          Uc[v] = o;
+        }
+        if (body) continue;
+        prim_from_cons(d->gamma, Uc, W);
+        for (int v = 0; v < NV; v++) ok &= isfinite(Uc[v]) != 0;
+        ok &= Uc[0] > 0.0;
+        ok &= W[7] > 0.0;
+      }
+  return ok;
+}
+
+/* One stage (kinds as in block_update).  With the learned correction, a block
+ * whose learned update leaves a non-physical cell is recomputed with the plain
+ * Rusanov flux (the fallback of the learned form); fb (nullable, one flag per
+ * block) records which blocks fell back. */
+int or_stage_ex(const or_desc* d, const double* Uin, const double* Ubase, double* Uout, int kind, double c,
+                int32_t* fb) {
   grid_t G;
   int rc = grid_init(&G, d, 0.0);
   if (rc) return rc;
   G.U = Uin;
   int nb = G.nb;
+  or_desc plain = *d;
+  plain.learned = 0;
 #pragma omp parallel for schedule(dynamic)
   for (int b = 0; b < nb; b++) {
     grid_t Gl = G;
-    double Rb[NV * NCELL];
+    double Rb[NV * NCELL], Ob[NV * NCELL];
     block_residual(&Gl, b, Rb);
-    const int32_t* L = d->leaves + 4 * b;
-    for (int k = 0; k < NC; k++)
-      for (int j = 0; j < NC; j++)
-        for (int i = 0; i < NC; i++) {
-          int cidx = (k * NC + j) * NC + i;
-          double xc[3];
-          cell_centre(&Gl, L[0], L, i, j, k, xc);
-          int body = in_body(d, xc);
-          for (int v = 0; v < NV; v++) {
-            long gidx = ((long)v * nb + b) * NCELL + cidx;
-            double r = Rb[v * NCELL + cidx];
-            double o;
-            if (body) o = Gl.Ubody[v];
-            else if (kind == 0) o = Ubase[gidx] + c * r;
-            else o = 0.5 * Ubase[gidx] + 0.5 * (Uin[gidx] + c * r);
-            Uout[gidx] = o;
-          }
-        }
+    int ok = block_update(&Gl, b, Rb, Uin, Ubase, kind, c, Ob);
+    int fell_back = 0;
+    if (!ok && d->learned && d->mlp && !d->no_fallback) {
+      Gl.d = &plain;
+      block_residual(&Gl, b, Rb);
+      block_update(&Gl, b, Rb, Uin, Ubase, kind, c, Ob);
+      fell_back = 1;
+    }
+    if (fb) fb[b] = fell_back;
+    for (int v = 0; v < NV; v++) memcpy(Uout + ((long)v * nb + b) * NCELL, Ob + v * NCELL, sizeof(double) * NCELL);
   }
   grid_free(&G);
   return OR_OK;
+}
+
+int or_stage(const or_desc* d, const double* Uin, const double* Ubase, double* Uout, int kind, double c) {
+  return or_stage_ex(d, Uin, Ubase, Uout, kind, c, NULL);
 }
 
 /* Largest sum_d (|u_d| + cf_d) / dx_d over non-body cells; dt = cfl / smax. */
@@ -934,17 +971,22 @@ int or_cfl_smax(const or_desc* d, const double* U, double* smax_out) {
 }
 
 /* n full steps of the two-stage scheme.  cfl > 0: dt = cfl / smax(U^n) each
- * step; cfl <= 0: dt = fixed_dt.  Returns the last dt and the elapsed time. */
-int or_run(const or_desc* d, double* U, int nsteps, double cfl, double fixed_dt, double* dt_last, double* t_total) {
+ * step; cfl <= 0: dt = fixed_dt.  Returns the last dt, the elapsed time and
+ * (nullable) the number of block-stages that fell back to the plain flux. */
+int or_run_ex(const or_desc* d, double* U, int nsteps, double cfl, double fixed_dt, double* dt_last,
+              double* t_total, long* n_fallback) {
   grid_t G;
   int rc = grid_init(&G, d, 0.0);
   if (rc) return rc;
-  size_t n = (size_t)NV * G.nb * NCELL;
+  int nb = G.nb;
+  size_t n = (size_t)NV * nb * NCELL;
   grid_free(&G);
   double* U1 = (double*)malloc(sizeof(double) * n);
   double* U2 = (double*)malloc(sizeof(double) * n);
-  if (!U1 || !U2) { free(U1); free(U2); return OR_ENOMEM; }
+  int32_t* fb = (int32_t*)malloc(sizeof(int32_t) * nb);
+  if (!U1 || !U2 || !fb) { free(U1); free(U2); free(fb); return OR_ENOMEM; }
   double t = 0.0, dt = fixed_dt;
+  long nfb = 0;
   for (int s = 0; s < nsteps; s++) {
     if (cfl > 0.0) {
       double smax;
@@ -952,12 +994,10 @@ int or_run(const or_desc* d, double* U, int nsteps, double cfl, double fixed_dt,
       if (rc) break;
       dt = cfl / smax;
     }
-    if (d->rk == RK_SSP2) {
-      rc = or_stage(d, U, U, U1, 0, dt);
-      if (!rc) rc = or_stage(d, U1, U, U2, 1, dt);
-    } else {
-      rc = or_stage(d, U, U, U1, 0, 0.5 * dt);
-      if (!rc) rc = or_stage(d, U1, U, U2, 0, dt);
+    for (int st = 0; st < 2 && !rc; st++) {
+      if (d->rk == RK_SSP2) rc = st == 0 ? or_stage_ex(d, U, U, U1, 0, dt, fb) : or_stage_ex(d, U1, U, U2, 1, dt, fb);
+      else rc = st == 0 ? or_stage_ex(d, U, U, U1, 0, 0.5 * dt, fb) : or_stage_ex(d, U1, U, U2, 0, dt, fb);
+      for (int b = 0; b < nb && !rc; b++) nfb += fb[b];
     }
     if (rc) break;
     memcpy(U, U2, sizeof(double) * n);
@@ -965,9 +1005,15 @@ int or_run(const or_desc* d, double* U, int nsteps, double cfl, double fixed_dt,
   }
   free(U1);
   free(U2);
+  free(fb);
   if (dt_last) *dt_last = dt;
   if (t_total) *t_total = t;
+  if (n_fallback) *n_fallback = nfb;
   return rc;
+}
+
+int or_run(const or_desc* d, double* U, int nsteps, double cfl, double fixed_dt, double* dt_last, double* t_total) {
+  return or_run_ex(d, U, nsteps, cfl, fixed_dt, dt_last, t_total, NULL);
 }
 
 /* Test hooks for single formulas. */

@@ -60,7 +60,7 @@ class _Desc(ctypes.Structure):
         ("powell", ctypes.c_int32),
         ("b0_param", ctypes.c_double * 12),
         ("learned", ctypes.c_int32),
-        ("pad_", ctypes.c_int32),
+        ("no_fallback", ctypes.c_int32),
         ("mlp", ctypes.POINTER(ctypes.c_double)),
     ]
 
@@ -81,8 +81,10 @@ def lib():
         _lib.or_ghost_info.argtypes = [D, ctypes.c_int, ip, ip]
         _lib.or_residual.argtypes = [D, dp, dp]
         _lib.or_stage.argtypes = [D, dp, dp, dp, ctypes.c_int, ctypes.c_double]
+        _lib.or_stage_ex.argtypes = [D, dp, dp, dp, ctypes.c_int, ctypes.c_double, ip]
         _lib.or_cfl_smax.argtypes = [D, dp, dp]
         _lib.or_run.argtypes = [D, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, dp]
+        _lib.or_run_ex.argtypes = [D, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, dp, lp]
         _lib.or_fast_speed.argtypes = [ctypes.c_double, dp, dp, ctypes.c_int]
         _lib.or_fast_speed.restype = ctypes.c_double
         _lib.or_prim_from_cons.argtypes = [ctypes.c_double, dp, dp, ctypes.c_long]
@@ -139,6 +141,7 @@ class _Bound:
             d.mlp = _dp(self.mlp)
         else:
             d.learned = 0
+        d.no_fallback = int(getattr(prob, "no_fallback", 0) or 0)
         self.desc = d
         self.nb = d.n_leaves
 
@@ -191,13 +194,17 @@ def residual(prob, U):
     return R.reshape(8, b.nb, 8, 8, 8)
 
 
-def stage(prob, Uin, Ubase, kind, c):
+def stage(prob, Uin, Ubase, kind, c, with_fallback_flags=False):
+    """One stage; with_fallback_flags also returns, per block, 1 where the
+    learned update was replaced by the plain one."""
     b = _Bound(prob)
     Uin = _state(prob, Uin, b.nb)
     Ubase = _state(prob, Ubase, b.nb)
     Uout = np.zeros_like(Uin)
-    _check(lib().or_stage(b.ref(), _dp(Uin), _dp(Ubase), _dp(Uout), int(kind), float(c)), "stage")
-    return Uout.reshape(8, b.nb, 8, 8, 8)
+    fb = np.zeros(b.nb, dtype=np.int32)
+    _check(lib().or_stage_ex(b.ref(), _dp(Uin), _dp(Ubase), _dp(Uout), int(kind), float(c), _ip(fb)), "stage")
+    Uout = Uout.reshape(8, b.nb, 8, 8, 8)
+    return (Uout, fb) if with_fallback_flags else Uout
 
 
 def cfl_smax(prob, U):
@@ -208,18 +215,22 @@ def cfl_smax(prob, U):
     return s.value
 
 
-def run(prob, U, nsteps, cfl=None, dt=None):
-    """Advance n steps; returns (U, last dt, elapsed time)."""
+def run(prob, U, nsteps, cfl=None, dt=None, with_fallbacks=False):
+    """Advance n steps; returns (U, last dt, elapsed time) and, with
+    with_fallbacks, the number of block-stages that fell back to the plain flux."""
     b = _Bound(prob)
     U = np.array(_state(prob, U, b.nb), copy=True)
     dtl = ctypes.c_double(0.0)
     tt = ctypes.c_double(0.0)
+    nfb = ctypes.c_long(0)
     c = float(cfl) if cfl is not None else -1.0
     fdt = float(dt) if dt is not None else 0.0
     if c <= 0.0 and not fdt > 0.0:
         raise ValueError("need cfl > 0 or a fixed dt > 0")
-    _check(lib().or_run(b.ref(), _dp(U), int(nsteps), c, fdt, ctypes.byref(dtl), ctypes.byref(tt)), "run")
-    return U.reshape(8, b.nb, 8, 8, 8), dtl.value, tt.value
+    _check(lib().or_run_ex(b.ref(), _dp(U), int(nsteps), c, fdt, ctypes.byref(dtl), ctypes.byref(tt),
+                           ctypes.byref(nfb)), "run")
+    out = (U.reshape(8, b.nb, 8, 8, 8), dtl.value, tt.value)
+    return out + (nfb.value,) if with_fallbacks else out
 
 
 def fast_speed(gamma, W, B, direction):

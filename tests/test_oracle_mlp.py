@@ -13,6 +13,8 @@ import pytest
 from oracle import oracle as O
 from paper_2501_06717_gb300 import workloads as W
 
+from learned_nets import double_dissipation_net, physical_per_block
+
 
 def _params(seed, scale=0.3):
     rng = np.random.default_rng(seed)
@@ -130,3 +132,46 @@ def test_learned_residual_scales_like_the_flux():
     scale = np.abs(R).reshape(8, -1).max(1)
     err = np.abs(Rs - f[:, None, None, None, None] * R).reshape(8, -1).max(1) / (f * scale)
     assert err.max() < 1e-11, err
+
+
+def test_learned_fallback_replaces_exactly_the_non_physical_blocks():
+    """The learned form's fallback: a block whose learned update has a cell with
+    rho <= 0 or p <= 0 is recomputed with the plain Rusanov flux; every other
+    block keeps its learned update."""
+    import copy
+    q = W.blast()
+    ql = W.Problem(**{**q.__dict__, "learned": 1, "mlp": double_dissipation_net()})
+    qn = copy.copy(ql)
+    qn.no_fallback = 1
+    # the first step: stage 1 stays physical, stage 2 fails next to the jump
+    U = q.U0
+    dt = 0.8 / O.cfl_smax(q, U)
+    Ustar = O.stage(ql, U, U, 0, 0.5 * dt)
+    found = False
+    for Uin, c in ((U, 0.5 * dt), (Ustar, dt)):
+        Uf, fb = O.stage(ql, Uin, U, 0, c, with_fallback_flags=True)
+        Un, fbn = O.stage(qn, Uin, U, 0, c, with_fallback_flags=True)
+        Up = O.stage(q, Uin, U, 0, c)
+        assert not fbn.any()
+        bad = ~physical_per_block(q.gamma, Un)
+        assert np.array_equal(fb.astype(bool), bad)
+        assert np.array_equal(Uf[:, fb == 1], Up[:, fb == 1])
+        assert np.array_equal(Uf[:, fb == 0], Un[:, fb == 0])
+        found |= bool(fb.any()) and not bool(fb.all())
+    assert found, "the test network never made a block non-physical"
+
+
+def test_learned_fallback_count_over_a_run():
+    """The run counts the block-stages that fell back: over one step it is the
+    sum of the two stages' flags; a zero network never falls back."""
+    q = W.blast()
+    ql = W.Problem(**{**q.__dict__, "learned": 1, "mlp": double_dissipation_net()})
+    dt = 0.8 / O.cfl_smax(q, q.U0)
+    Us, fb1 = O.stage(ql, q.U0, q.U0, 0, 0.5 * dt, with_fallback_flags=True)
+    U1, fb2 = O.stage(ql, Us, q.U0, 0, dt, with_fallback_flags=True)
+    Ur, _, _, nfb = O.run(ql, q.U0, 1, cfl=0.8, with_fallbacks=True)
+    assert nfb == fb1.sum() + fb2.sum() > 0
+    assert np.array_equal(Ur, U1)
+    qz = W.Problem(**{**q.__dict__, "learned": 1, "mlp": np.zeros(O.MLP_NPARAM)})
+    _, _, _, nz = O.run(qz, q.U0, 3, cfl=0.8, with_fallbacks=True)
+    assert nz == 0
