@@ -106,11 +106,19 @@ def oracle_sample(problems, seconds):
 
 
 def cpu_baseline(problems, seconds):
+    """The oracle with OpenMP over blocks on all host cores, and (a quarter of
+    the time) on one core."""
     from oracle import oracle as O
     cells, el, used = oracle_sample(problems, seconds)
-    return {"value": cells / el, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+    cores = O.num_threads()
+    O.set_threads(1)
+    c1, e1, u1 = oracle_sample(problems, seconds / 4)
+    O.set_threads(cores)
+    return {"value": cells / el, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "%d of %d grids (%d cells), 1 step each, FP64 C oracle with OpenMP over blocks, %.1f s"
-                      % (used, len(problems), cells, el)}
+                      % (used, len(problems), cells, el),
+            "single_core_value": c1 / e1,
+            "single_core_sample": "%d grids (%d cells), 1 step each, %.1f s" % (u1, c1, e1)}
 
 
 def run_reference(args, rank, world):
@@ -204,6 +212,39 @@ def learned_form_summary(stream, steps=32):
 
 
 # --------------------------------------------------------------------------
+# The other paper-shaped grids (one grid each)
+
+
+def other_workloads(stream, steps=20, fp64_steps=4):
+    """Mixed and FP64 throughput on the blast at 16^3 roots, the magnetosphere
+    stand-in and the Table 2 fast-wave grid at m = 12, each one grid in one
+    persistent launch per stage replayed from a CUDA graph."""
+    import torch
+    from paper_2501_06717_gb300 import bats
+    out = {}
+    for name, make in (("blast_16cube_roots", lambda: W.blast(roots_per_axis=16)),
+                       ("magnetosphere", W.magnetosphere),
+                       ("fast_wave_table2_m12", lambda: W.fast_wave(m=12))):
+        prob = make()
+        row = {"blocks": prob.nb, "cells": prob.ncells}
+        for pname, prec, n in (("mixed", bats.BATS_MIXED, steps), ("fp64", bats.BATS_FP64, fp64_steps)):
+            with bats.Solver(prob, precision=prec, stream=stream, persistent=1, use_graph=1) as s:
+                s.set_state(0, prob.U0)
+                s.step(n, prob.cfl)   # captures the n-step graph
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                s.step(n, prob.cfl)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                row[pname] = prob.ncells * n / (e0.elapsed_time(e1) * 1e-3)
+        del prob
+        out[name] = row
+    return out
+
+
+# --------------------------------------------------------------------------
 # Clocks during the timed region
 
 
@@ -263,6 +304,7 @@ def main():
     ap.add_argument("--grids", type=int, default=64, help="first N grids of the batched workload")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-form summary")
     ap.add_argument("--learned-only", action="store_true", help="only the learned-form summary (profiling)")
+    ap.add_argument("--no-others", action="store_true", help="skip the other paper-shaped grids")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -388,6 +430,9 @@ def main():
     learned = None
     if rank == 0 and world == 1 and not args.no_learned and args.workload == "batched":
         learned = learned_form_summary(stream)
+    others = None
+    if rank == 0 and world == 1 and not args.no_others and args.workload == "batched":
+        others = other_workloads(stream)
 
     if rank == 0:
         line = {
@@ -413,6 +458,7 @@ def main():
             "clocks": clk,
             "fp64_value": fp64,
             "learned_form": learned,
+            "other_workloads_cell_updates_per_s": others,
             "stage_share": stage_ms / stage_total_ms if stage_total_ms > 0 else None,
         }
         if tune:

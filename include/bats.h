@@ -174,6 +174,13 @@ int bats_set_launch(bats_t* h, int persistent, int blocks_per_cta, int ctas_per_
 /* Number of kernels launched by the last bats_step call. */
 int bats_get_launch_count(bats_t* h, long long* n);
 
+/* Learned form: number of block-stages, since bats_create, whose learned
+ * update left a non-physical cell (rho <= 0, p <= 0 or not finite) and were
+ * therefore recomputed with the plain Rusanov flux, the method's own flux
+ * (the network only corrects it).  0 for the plain forms.  The count is read
+ * back at the end of each bats_step/bats_step_dt call. */
+int bats_get_fallbacks(bats_t* h, long long* n);
+
 /* Self-check of the mixed form's integer-only number conversions (no paper
  * counterpart: on GB300 the FP32<->FP64 conversion instructions run on the
  * FP64 unit, so the kernels convert with integer operations instead).  For n

@@ -274,6 +274,10 @@ def set_threads(n):
     lib().or_set_threads(int(n))
 
 
+def set_threads(n):
+    lib().or_set_threads(int(n))
+
+
 def mlp_forward(params, x):
     P = np.ascontiguousarray(params, dtype=np.float64).reshape(MLP_NPARAM)
     x = np.ascontiguousarray(x, dtype=np.float64).reshape(MLP_IN)

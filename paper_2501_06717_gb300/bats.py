@@ -98,6 +98,7 @@ def lib():
     L.bats_debug_residual.argtypes = [vp, ctypes.c_int, dp, ctypes.c_size_t]
     L.bats_set_launch.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     L.bats_get_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+    L.bats_get_fallbacks.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     L.bats_debug_check_conversions.argtypes = [vp, vp, ctypes.c_int, vp, vp]
     L.bats_set_mlp.argtypes = [vp, vp]
     L.bats_debug_face_data.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, vp, vp, ctypes.c_size_t]
@@ -262,6 +263,12 @@ def bats_set_launch(h, persistent, blocks_per_cta, ctas_per_sm, use_graph):
 def bats_get_launch_count(h):
     n = ctypes.c_longlong(0)
     _check(h, lib().bats_get_launch_count(h, ctypes.byref(n)))
+    return n.value
+
+
+def bats_get_fallbacks(h):
+    n = ctypes.c_longlong(0)
+    _check(h, lib().bats_get_fallbacks(h, ctypes.byref(n)))
     return n.value
 
 
@@ -479,3 +486,6 @@ class Solver:
 
     def launch_count(self):
         return bats_get_launch_count(self.h)
+
+    def fallbacks(self):
+        return bats_get_fallbacks(self.h)

@@ -68,6 +68,7 @@ struct bats {
   int timed_steps = 0;
   double ms_last[BATS_NUM_PHASES] = {0, 0, 0};
   long long launches = 0;
+  long long fallbacks = 0;  // learned block-stages recomputed with the plain flux
   cudaGraphExec_t graph = nullptr;
   int graph_n = -1;
   double graph_cfl = 0, graph_dt = 0;
@@ -464,7 +465,7 @@ int run_steps(bats_t* h, int n, double cfl, double fixed_dt, double* t_out) {
     return fail(h, BATS_ERR_NOT_TRAINED, "learned form requested but no weights set (bats_set_mlp)");
   h->launches = 0;
   CK(h, cudaGetLastError());  // report (and clear) anything left from an earlier call
-  int32_t init[2] = {0, INT_MAX};
+  int32_t init[3] = {0, INT_MAX, 0};
   CK(h, cudaMemcpyAsync(h->errw, init, sizeof(init), cudaMemcpyHostToDevice, h->stream));
   CK(h, cudaEventRecord(h->ev0, h->stream));
   if (h->use_graph && n > 0) {
@@ -493,9 +494,10 @@ int run_steps(bats_t* h, int n, double cfl, double fixed_dt, double* t_out) {
     if (rc) return rc;
   }
   CK(h, cudaEventRecord(h->ev1, h->stream));
-  int32_t ew[2];
+  int32_t ew[3];
   CK(h, cudaMemcpyAsync(ew, h->errw, sizeof(ew), cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
+  h->fallbacks += ew[2];
   float ms = 0.f;
   CK(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
   double stage_ms = 0.0;
@@ -593,7 +595,7 @@ int bats_create(const bats_grid_desc* grids, int n_grids, const bats_physics* ph
       (rc = dev_alloc(h, &h->levmap_d, h->levmap_h.size())) || (rc = dev_alloc(h, &h->U, nstate)) ||
       (rc = dev_alloc(h, &h->U1, nstate)) || (rc = dev_alloc(h, &h->dt, h->ngrids)) ||
       (rc = dev_alloc(h, &h->t, h->ngrids)) || (rc = dev_alloc(h, &h->smax, h->ngrids)) ||
-      (rc = dev_alloc(h, &h->smax_next, h->ngrids)) || (rc = dev_alloc(h, &h->errw, 2)) ||
+      (rc = dev_alloc(h, &h->smax_next, h->ngrids)) || (rc = dev_alloc(h, &h->errw, 3)) ||
       (rc = dev_alloc(h, &h->staging, h->staging_n))) {
     free_all(h);
     g_create_error = h->err;
@@ -727,7 +729,7 @@ int bats_debug_fill_ghosts(bats_t* h, int grid, double* T, size_t n) {
   double* dst = dev ? T : h->staging;
   StageArgs a = base_args(h);
   a.Uin = h->U;
-  int32_t init[2] = {0, INT_MAX};
+  int32_t init[3] = {0, INT_MAX, 0};
   CK(h, cudaMemcpyAsync(h->errw, init, sizeof(init), cudaMemcpyHostToDevice, h->stream));
   CK(h, launch_debug_fill(a, G.block0, G.nb, dst, h->stream));
   if (!dev) CK(h, cudaMemcpyAsync(T, h->staging, need * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -751,7 +753,7 @@ int bats_debug_residual(bats_t* h, int grid, double* R, size_t n) {
   a.last = 0;
   a.beta = 1.0;
   a.write_u_all = 1;
-  int32_t init[2] = {0, INT_MAX};
+  int32_t init[3] = {0, INT_MAX, 0};
   CK(h, cudaMemcpyAsync(h->errw, init, sizeof(init), cudaMemcpyHostToDevice, h->stream));
   rc = launch_stage(h, a);
   if (rc) return rc;
@@ -818,7 +820,7 @@ int bats_debug_face_data(bats_t* h, int grid, int stage_input, double dt, float*
     return rc;
   }
   StageArgs a = base_args(h);
-  int32_t init[2] = {0, INT_MAX};
+  int32_t init[3] = {0, INT_MAX, 0};
   cudaError_t e = cudaMemcpyAsync(h->errw, init, sizeof(init), cudaMemcpyHostToDevice, h->stream);
   const double* Uin = h->U;
   const float* Win = h->W;
@@ -872,6 +874,12 @@ int bats_debug_face_data(bats_t* h, int grid, int stage_input, double dt, float*
 int bats_get_launch_count(bats_t* h, long long* n) {
   if (!h || !n) return BATS_ERR_INVALID_ARG;
   *n = h->launches;
+  return BATS_OK;
+}
+
+int bats_get_fallbacks(bats_t* h, long long* n) {
+  if (!h || !n) return BATS_ERR_INVALID_ARG;
+  *n = h->fallbacks;
   return BATS_OK;
 }
 

@@ -777,282 +777,307 @@ __global__ void __launch_bounds__(STAGE_THREADS, MIXED ? 2 : 1) k_stage(const St
       }
       const int gb0 = B.bi * NC, gb1 = B.bj * NC, gb2 = B.bk * NC;
 
-      // 3. faces: reconstruction + Rusanov flux in the frame (d, d+1, d+2)
-      {
-        auto cidx = [&](int c) { return c < 0 ? flo + (c + 2) : (c >= NC ? fhi + (c - NC) : fibase + c * fstride); };
-        const int f0 = fhalf ? 5 : 0, nf = fhalf ? 4 : 5;
-        R Wm1[8], W0[8], sm1[8];
-        R Wm2[8];  // kept along the line only for the network's inputs
-        load_rot<R>(sT, rot, cidx(f0 - 2), Wm2);
-        load_rot<R>(sT, rot, cidx(f0 - 1), Wm1);
-        load_rot<R>(sT, rot, cidx(f0), W0);
+      // 3. faces: reconstruction + Rusanov flux in the frame (d, d+1, d+2);
+      //    corr = add the network's correction (learned form)
+      auto faces = [&](const bool corr) {
+          auto cidx = [&](int c) { return c < 0 ? flo + (c + 2) : (c >= NC ? fhi + (c - NC) : fibase + c * fstride); };
+          const int f0 = fhalf ? 5 : 0, nf = fhalf ? 4 : 5;
+          R Wm1[8], W0[8], sm1[8];
+          R Wm2[8];  // kept along the line only for the network's inputs
+          load_rot<R>(sT, rot, cidx(f0 - 2), Wm2);
+          load_rot<R>(sT, rot, cidx(f0 - 1), Wm1);
+          load_rot<R>(sT, rot, cidx(f0), W0);
 #pragma unroll
-        for (int v = 0; v < NV; v++) sm1[v] = limit_<R>(LIM, Wm1[v] - Wm2[v], W0[v] - Wm1[v]);
-#pragma unroll 1
-        for (int k = 0; k < nf; k++) {
-          const int f = f0 + k;
-          R Wp[8], WL[8], WR[8], s0[8];
-          load_rot<R>(sT, rot, cidx(f + 1), Wp);
+          for (int v = 0; v < NV; v++) sm1[v] = limit_<R>(LIM, Wm1[v] - Wm2[v], W0[v] - Wm1[v]);
+  #pragma unroll 1
+          for (int k = 0; k < nf; k++) {
+            const int f = f0 + k;
+            R Wp[8], WL[8], WR[8], s0[8];
+            load_rot<R>(sT, rot, cidx(f + 1), Wp);
 #pragma unroll
-          for (int v = 0; v < NV; v++) {
-            s0[v] = limit_<R>(LIM, W0[v] - Wm1[v], Wp[v] - W0[v]);
-            WL[v] = Wm1[v] + R(0.5) * sm1[v];
-            WR[v] = W0[v] - R(0.5) * s0[v];
-          }
-          R B0f[3] = {R(0), R(0), R(0)}, B0r[3];
-          if constexpr (HAS_B0) {
-            const int ci_ = fd == 0 ? f : fta, cj_ = fd == 1 ? f : (fd == 0 ? fta : ftb), ck_ = fd == 2 ? f : ftb;
-            b0_face<R>(ph, fd, ci_, cj_, ck_, gb0, gb1, gb2, lor0, lor1, lor2, dxr0, dxr1, dxr2, B0f);
-          }
-          B0r[0] = fd == 0 ? B0f[0] : (fd == 1 ? B0f[1] : B0f[2]);
-          B0r[1] = fd1 == 0 ? B0f[0] : (fd1 == 1 ? B0f[1] : B0f[2]);
-          B0r[2] = fd2 == 0 ? B0f[0] : (fd2 == 1 ? B0f[1] : B0f[2]);
-          R FL[8], UL[8], FR[8], UR[8], unL, unR, cfL, cfR;
-          phys_flux<R>(WL, B0r, gamma, inv_gm1, FL, UL, unL, cfL);
-          phys_flux<R>(WR, B0r, gamma, inv_gm1, FR, UR, unR, cfR);
-          R aL = Ops<R>::abs_(unL) + cfL, aR = Ops<R>::abs_(unR) + cfR;
-          R cmax = aL > aR ? aL : aR;
-          const int fi = fline * 9 + f;
-          R Fr[8];
+            for (int v = 0; v < NV; v++) {
+              s0[v] = limit_<R>(LIM, W0[v] - Wm1[v], Wp[v] - W0[v]);
+              WL[v] = Wm1[v] + R(0.5) * sm1[v];
+              WR[v] = W0[v] - R(0.5) * s0[v];
+            }
+            R B0f[3] = {R(0), R(0), R(0)}, B0r[3];
+            if constexpr (HAS_B0) {
+              const int ci_ = fd == 0 ? f : fta, cj_ = fd == 1 ? f : (fd == 0 ? fta : ftb), ck_ = fd == 2 ? f : ftb;
+              b0_face<R>(ph, fd, ci_, cj_, ck_, gb0, gb1, gb2, lor0, lor1, lor2, dxr0, dxr1, dxr2, B0f);
+            }
+            B0r[0] = fd == 0 ? B0f[0] : (fd == 1 ? B0f[1] : B0f[2]);
+            B0r[1] = fd1 == 0 ? B0f[0] : (fd1 == 1 ? B0f[1] : B0f[2]);
+            B0r[2] = fd2 == 0 ? B0f[0] : (fd2 == 1 ? B0f[1] : B0f[2]);
+            R FL[8], UL[8], FR[8], UR[8], unL, unR, cfL, cfR;
+            phys_flux<R>(WL, B0r, gamma, inv_gm1, FL, UL, unL, cfL);
+            phys_flux<R>(WR, B0r, gamma, inv_gm1, FR, UR, unR, cfR);
+            R aL = Ops<R>::abs_(unL) + cfL, aR = Ops<R>::abs_(unR) + cfR;
+            R cmax = aL > aR ? aL : aR;
+            const int fi = fline * 9 + f;
+            R Fr[8];
 #pragma unroll
-          for (int v = 0; v < NV; v++) Fr[v] = R(0.5) * (FL[v] + FR[v]) - R(0.5) * cmax * (UR[v] - UL[v]);
-          if constexpr (LRN) {
-            // network inputs: the 4 stencil cells f-2..f+1 and (WL + WR)/2 in
-            // the face frame, scaled by rho_ref = mean stencil density and
-            // c_ref = cmax (u / c_ref, B / (sqrt(rho_ref) c_ref), p / (rho_ref c_ref^2))
-            const int64_t gface = (static_cast<int64_t>(blk) * 3 + fd) * NFACE + fi;
-            const R rho_ref = R(0.25) * (((Wm2[0] + Wm1[0]) + W0[0]) + Wp[0]);
-            const R c_ref = cmax;
-            const R sq = Ops<R>::sqrt_(rho_ref);
-            if (a.kind >= 3) {
-              const R ir = Ops<R>::div_(R(1), rho_ref), ic = Ops<R>::div_(R(1), c_ref);
-              const R ib = Ops<R>::div_(R(1), sq * c_ref), ip = Ops<R>::div_(R(1), rho_ref * c_ref * c_ref);
-              float xin[40];
+            for (int v = 0; v < NV; v++) Fr[v] = R(0.5) * (FL[v] + FR[v]) - R(0.5) * cmax * (UR[v] - UL[v]);
+            if constexpr (LRN) {
+              // network inputs: the 4 stencil cells f-2..f+1 and (WL + WR)/2 in
+              // the face frame, scaled by rho_ref = mean stencil density and
+              // c_ref = cmax (u / c_ref, B / (sqrt(rho_ref) c_ref), p / (rho_ref c_ref^2))
+              const int64_t gface = (static_cast<int64_t>(blk) * 3 + fd) * NFACE + fi;
+              const R rho_ref = R(0.25) * (((Wm2[0] + Wm1[0]) + W0[0]) + Wp[0]);
+              const R c_ref = cmax;
+              const R sq = Ops<R>::sqrt_(rho_ref);
+              if (a.kind >= 3) {
+                const R ir = Ops<R>::div_(R(1), rho_ref), ic = Ops<R>::div_(R(1), c_ref);
+                const R ib = Ops<R>::div_(R(1), sq * c_ref), ip = Ops<R>::div_(R(1), rho_ref * c_ref * c_ref);
+                float xin[40];
 #pragma unroll
-              for (int sidx = 0; sidx < 5; sidx++) {
-                const R* Wsrc = sidx == 0 ? Wm2 : (sidx == 1 ? Wm1 : (sidx == 2 ? W0 : Wp));
-                R wv[8];
+                for (int sidx = 0; sidx < 5; sidx++) {
+                  const R* Wsrc = sidx == 0 ? Wm2 : (sidx == 1 ? Wm1 : (sidx == 2 ? W0 : Wp));
+                  R wv[8];
 #pragma unroll
-                for (int v = 0; v < NV; v++) wv[v] = sidx < 4 ? Wsrc[v] : R(0.5) * (WL[v] + WR[v]);
-                xin[8 * sidx + 0] = static_cast<float>(wv[0] * ir);
+                  for (int v = 0; v < NV; v++) wv[v] = sidx < 4 ? Wsrc[v] : R(0.5) * (WL[v] + WR[v]);
+                  xin[8 * sidx + 0] = static_cast<float>(wv[0] * ir);
 #pragma unroll
-                for (int c = 1; c < 4; c++) xin[8 * sidx + c] = static_cast<float>(wv[c] * ic);
+                  for (int c = 1; c < 4; c++) xin[8 * sidx + c] = static_cast<float>(wv[c] * ic);
 #pragma unroll
-                for (int c = 4; c < 7; c++) xin[8 * sidx + c] = static_cast<float>(wv[c] * ib);
-                xin[8 * sidx + 7] = static_cast<float>(wv[7] * ip);
-              }
-              if (a.kind == 3) {
-                uint32_t* dst = a.Xb + gface * 24;
-#pragma unroll
-                for (int q = 0; q < 20; q++) {
-                  __nv_bfloat162 v2 = __floats2bfloat162_rn(xin[2 * q], xin[2 * q + 1]);
-                  dst[q] = *reinterpret_cast<uint32_t*>(&v2);
+                  for (int c = 4; c < 7; c++) xin[8 * sidx + c] = static_cast<float>(wv[c] * ib);
+                  xin[8 * sidx + 7] = static_cast<float>(wv[7] * ip);
                 }
+                if (a.kind == 3) {
+                  uint32_t* dst = a.Xb + gface * 24;
 #pragma unroll
-                for (int q = 20; q < 24; q++) dst[q] = 0u;
-              } else {
-                if (a.Xf) {
-                  float* dst = a.Xf + gface * 40;
+                  for (int q = 0; q < 20; q++) {
+                    __nv_bfloat162 v2 = __floats2bfloat162_rn(xin[2 * q], xin[2 * q + 1]);
+                    dst[q] = *reinterpret_cast<uint32_t*>(&v2);
+                  }
 #pragma unroll
-                  for (int q = 0; q < 40; q++) dst[q] = xin[q];
+                  for (int q = 20; q < 24; q++) dst[q] = 0u;
+                } else {
+                  if (a.Xf) {
+                    float* dst = a.Xf + gface * 40;
+#pragma unroll
+                    for (int q = 0; q < 40; q++) dst[q] = xin[q];
+                  }
+                  double* fo = a.Fd + gface * 10;
+                  fo[8] = rho_ref;
+                  fo[9] = c_ref;
+                  fo[0] = Fr[0];
+                  fo[1 + fd] = Fr[1];
+                  fo[1 + fd1] = Fr[2];
+                  fo[1 + fd2] = Fr[3];
+                  fo[4 + fd] = Fr[4];
+                  fo[4 + fd1] = Fr[5];
+                  fo[4 + fd2] = Fr[6];
+                  fo[7] = Fr[7];
                 }
-                double* fo = a.Fd + gface * 10;
-                fo[8] = rho_ref;
-                fo[9] = c_ref;
-                fo[0] = Fr[0];
-                fo[1 + fd] = Fr[1];
-                fo[1 + fd1] = Fr[2];
-                fo[1 + fd2] = Fr[3];
-                fo[4 + fd] = Fr[4];
-                fo[4 + fd1] = Fr[5];
-                fo[4 + fd2] = Fr[6];
-                fo[7] = Fr[7];
-              }
-            } else if (a.learned) {
-              // correction back in flux units, clipped to the Rusanov dissipation
-              const float* yv = a.Y + gface * 8;
-              const R sc0 = rho_ref * c_ref, sc1 = rho_ref * c_ref * c_ref, sc4 = sq * c_ref * c_ref;
-              const R sc7 = rho_ref * c_ref * c_ref * c_ref;
+              } else if (a.learned && corr) {
+                // correction back in flux units, clipped to the Rusanov dissipation
+                const float* yv = a.Y + gface * 8;
+                const R sc0 = rho_ref * c_ref, sc1 = rho_ref * c_ref * c_ref, sc4 = sq * c_ref * c_ref;
+                const R sc7 = rho_ref * c_ref * c_ref * c_ref;
 #pragma unroll
-              for (int v = 0; v < NV; v++) {
-                const R sc = v == 0 ? sc0 : (v < 4 ? sc1 : (v < 7 ? sc4 : sc7));
-                R dF = R(yv[v]) * sc;
-                const R lim = Ops<R>::abs_(R(0.5) * cmax * (UR[v] - UL[v]));
-                dF = dF > lim ? lim : dF;
-                dF = dF < -lim ? -lim : dF;
-                Fr[v] = Fr[v] + dF;
+                for (int v = 0; v < NV; v++) {
+                  const R sc = v == 0 ? sc0 : (v < 4 ? sc1 : (v < 7 ? sc4 : sc7));
+                  R dF = R(yv[v]) * sc;
+                  const R lim = Ops<R>::abs_(R(0.5) * cmax * (UR[v] - UL[v]));
+                  dF = dF > lim ? lim : dF;
+                  dF = dF < -lim ? -lim : dF;
+                  Fr[v] = Fr[v] + dF;
+                }
               }
             }
+#pragma unroll
+            for (int v = 0; v < NV; v++) {
+              Wm2[v] = Wm1[v];
+              sm1[v] = s0[v];
+              Wm1[v] = W0[v];
+              W0[v] = Wp[v];
+            }
+            if (a.kind >= 3) continue;
+            fcol[0 * NFACE + fi] = Fr[0];
+            fcol[(1 + fd) * NFACE + fi] = Fr[1];
+            fcol[(1 + fd1) * NFACE + fi] = Fr[2];
+            fcol[(1 + fd2) * NFACE + fi] = Fr[3];
+            fcol[(4 + fd) * NFACE + fi] = Fr[4];
+            fcol[(4 + fd1) * NFACE + fi] = Fr[5];
+            fcol[(4 + fd2) * NFACE + fi] = Fr[6];
+            fcol[7 * NFACE + fi] = Fr[7];
+            fcol[8 * NFACE + fi] = R(0.5) * (WL[4] + WR[4]);
           }
+      };
+      // 4. per cell: flux differences, sources, update, CFL bound.  commit =
+      //    false only checks the update (learned form): returns whether this
+      //    thread met a non-physical cell, writes nothing
+      auto cells = [&](const bool commit) -> bool {
+        bool any_bad = false;
+        R smax_loc = R(0);
+        for (int c = tid; c < NCELL; c += STAGE_THREADS) {
+          const int ci = c & 7, cj = (c >> 3) & 7, ck = c >> 6;
+          // face indices (line * 9 + position) of the low faces in x, y, z
+          const int tx = (ck * NC + cj) * 9 + ci;
+          const int ty = (ck * NC + ci) * 9 + cj;
+          const int tz = (cj * NC + ci) * 9 + ck;
+          const R* Fx = sF;
+          const R* Fy = sF + NFC * NFACE;
+          const R* Fz = sF + 2 * NFC * NFACE;
+          R res[8];
 #pragma unroll
           for (int v = 0; v < NV; v++) {
-            Wm2[v] = Wm1[v];
-            sm1[v] = s0[v];
-            Wm1[v] = W0[v];
-            W0[v] = Wp[v];
+            R r = -((Fx[v * NFACE + tx + 1] - Fx[v * NFACE + tx]) * idx0);
+            r = r - (Fy[v * NFACE + ty + 1] - Fy[v * NFACE + ty]) * idx1;
+            r = r - (Fz[v * NFACE + tz + 1] - Fz[v * NFACE + tz]) * idx2;
+            res[v] = r;
           }
-          if (a.kind >= 3) continue;
-          fcol[0 * NFACE + fi] = Fr[0];
-          fcol[(1 + fd) * NFACE + fi] = Fr[1];
-          fcol[(1 + fd1) * NFACE + fi] = Fr[2];
-          fcol[(1 + fd2) * NFACE + fi] = Fr[3];
-          fcol[(4 + fd) * NFACE + fi] = Fr[4];
-          fcol[(4 + fd1) * NFACE + fi] = Fr[5];
-          fcol[(4 + fd2) * NFACE + fi] = Fr[6];
-          fcol[7 * NFACE + fi] = Fr[7];
-          fcol[8 * NFACE + fi] = R(0.5) * (WL[4] + WR[4]);
+          const R divb = ((Fx[8 * NFACE + tx + 1] - Fx[8 * NFACE + tx]) * idx0 +
+                          (Fy[8 * NFACE + ty + 1] - Fy[8 * NFACE + ty]) * idx1) +
+                         (Fz[8 * NFACE + tz + 1] - Fz[8 * NFACE + tz]) * idx2;
+          bool in_body = false;
+          if (B.body) {  // FP64, the same centre formula as the host and the oracle
+            double x = G.lo[0] + ((static_cast<double>(gb0) + ci) + 0.5) * G.dx[lev][0];
+            double y = G.lo[1] + ((static_cast<double>(gb1) + cj) + 0.5) * G.dx[lev][1];
+            double z = G.lo[2] + ((static_cast<double>(gb2) + ck) + 0.5) * G.dx[lev][2];
+            in_body = (x * x + y * y + z * z) < G.body_r * G.body_r;
+          }
+          R Wc[8];
+#pragma unroll
+          for (int v = 0; v < NV; v++) Wc[v] = sT[v * NTILE + c];
+          R B0c[3] = {R(0), R(0), R(0)};
+          R S[8] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+          if constexpr (HAS_B0) b0_face<R>(ph, -1, ci, cj, ck, gb0, gb1, gb2, lor0, lor1, lor2, dxr0, dxr1, dxr2, B0c);
+          if (ph.powell) {
+            R ub1 = Wc[1] * Wc[4] + Wc[2] * Wc[5] + Wc[3] * Wc[6];
+#pragma unroll
+            for (int e = 0; e < 3; e++) {
+              S[1 + e] = -divb * (B0c[e] + Wc[4 + e]);
+              S[4 + e] = -divb * Wc[1 + e];
+            }
+            S[7] = -divb * ub1;
+          }
+          if constexpr (HAS_B0) {
+            // split-field correction from the face-centre B0 of the six faces:
+            // S_m += -B1 (div B0)_h + B1 x (curl B0)_h
+            R xm[3], xp[3], ym[3], yp[3], zm[3], zp[3];
+            b0_face<R>(ph, 0, ci, cj, ck, gb0, gb1, gb2, lor0, lor1, lor2, dxr0, dxr1, dxr2, xm);
+            b0_face<R>(ph, 0, ci + 1, cj, ck, gb0, gb1, gb2, lor0, lor1, lor2, dxr0, dxr1, dxr2, xp);
+            b0_face<R>(ph, 1, ci, cj, ck, gb0, gb1, gb2, lor0, lor1, lor2, dxr0, dxr1, dxr2, ym);
+            b0_face<R>(ph, 1, ci, cj + 1, ck, gb0, gb1, gb2, lor0, lor1, lor2, dxr0, dxr1, dxr2, yp);
+            b0_face<R>(ph, 2, ci, cj, ck, gb0, gb1, gb2, lor0, lor1, lor2, dxr0, dxr1, dxr2, zm);
+            b0_face<R>(ph, 2, ci, cj, ck + 1, gb0, gb1, gb2, lor0, lor1, lor2, dxr0, dxr1, dxr2, zp);
+            R divb0 = ((xp[0] - xm[0]) * idx0 + (yp[1] - ym[1]) * idx1) + (zp[2] - zm[2]) * idx2;
+            R cu0 = (yp[2] - ym[2]) * idx1 - (zp[1] - zm[1]) * idx2;
+            R cu1 = (zp[0] - zm[0]) * idx2 - (xp[2] - xm[2]) * idx0;
+            R cu2 = (xp[1] - xm[1]) * idx0 - (yp[0] - ym[0]) * idx1;
+            R b1x = Wc[4], b1y = Wc[5], b1z = Wc[6];
+            S[1] = (S[1] - b1x * divb0) + (b1y * cu2 - b1z * cu1);
+            S[2] = (S[2] - b1y * divb0) + (b1z * cu0 - b1x * cu2);
+            S[3] = (S[3] - b1z * divb0) + (b1x * cu1 - b1y * cu0);
+          }
+          const double cdt = a.beta * a.dt[B.grid];
+          const int64_t base = static_cast<int64_t>(blk) * (NV * NCELL) + c;
+          double Uo[8];
+          bool bad = false;
+#pragma unroll
+          for (int v = 0; v < NV; v++) {
+            R r = res[v] + S[v];
+            double rd;
+            if constexpr (MIXED) rd = f2d_int(r);
+            else rd = r;
+            double ub = a.Ubase[base + v * NCELL];
+            double o;
+            if (a.kind == 0) o = fma(cdt, rd, ub);
+            else o = 0.5 * ub + 0.5 * fma(cdt, rd, a.Uin[base + v * NCELL]);
+            if (a.kind == 2) o = rd;  // residual only (debug view)
+            o = in_body ? (a.kind == 2 ? 0.0 : G.Ubody[v]) : o;
+            Uo[v] = o;
+            bad |= !finite_d(o);
+          }
+          if (a.kind != 2) bad |= !positive_d(Uo[0]);
+          R Wn[8];
+          const bool need_w = MIXED || a.last || !commit;
+          if (need_w && a.kind != 2) {
+            if constexpr (MIXED) {
+              double p64;
+              prim_mixed(Uo, ph.gm1f, Wn, &p64);
+              bad |= !positive_d(p64);
+            } else {
+              prim64(Uo, ph.gm1, Wn);
+              bad |= !positive_d(Wn[7]);
+            }
+          }
+          if (bad && !in_body && a.kind != 2) {
+            any_bad = true;
+            if (commit) {
+              atomicOr(&a.err[0], ERR_NONPHYSICAL);
+              atomicMin(&a.err[1], blk);
+            }
+          }
+          if (!commit) continue;
+          const bool write_u = !MIXED || a.last || a.write_u_all || B.need_u;
+          if (write_u || a.kind == 2) {
+#pragma unroll
+            for (int v = 0; v < NV; v++) a.Uout[base + v * NCELL] = Uo[v];
+          }
+          if constexpr (MIXED) {
+            if (a.kind != 2) {
+#pragma unroll
+              for (int v = 0; v < NV; v++) a.Wout[base + v * NCELL] = Wn[v];
+            }
+          }
+          // CFL bound of the new state: sum_d (|u_d| + c_f,d) / dx_d
+          if (a.last && !in_body && a.kind != 2) {
+            R Bt[3] = {B0c[0] + Wn[4], B0c[1] + Wn[5], B0c[2] + Wn[6]};
+            R sacc = R(0);
+#pragma unroll
+            for (int e = 0; e < 3; e++) {
+              R bn = Bt[e], bt1 = Bt[(e + 1) % 3], bt2 = Bt[(e + 2) % 3];
+              R cf;
+              if constexpr (MIXED) {
+                cf = fast_speed_n<R>(gamma, Wn[0], Wn[7], bn, bt1, bt2);
+                sacc = sacc + (Ops<R>::abs_(Wn[1 + e]) + cf) * (e == 0 ? idx0 : (e == 1 ? idx1 : idx2));
+              } else {
+                cf = fast_speed_exact(ph.gamma, Wn[0], Wn[7], bn, bt1, bt2);
+                sacc = sacc + (Ops<R>::abs_(Wn[1 + e]) + cf) / (e == 0 ? dxr0 : (e == 1 ? dxr1 : dxr2));
+              }
+            }
+            smax_loc = sacc > smax_loc ? sacc : smax_loc;
+          }
         }
-      }
+        if (commit && a.last && a.kind != 2) {
+          R m = smax_loc;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            R q = __shfl_xor_sync(0xffffffffu, m, o);
+            m = q > m ? q : m;
+          }
+          if ((tid & 31) == 0) sred[tid >> 5] = m;
+          __syncthreads();
+          if (tid == 0) {
+            R mm = R(0);
+            for (int w = 0; w < STAGE_THREADS / 32; w++) mm = sred[w] > mm ? sred[w] : mm;
+            double md;
+            if constexpr (MIXED) md = f2d_int(mm);
+            else md = mm;
+            if (md > 0.0) atomicMax(&a.smax_next[B.grid], static_cast<unsigned long long>(__double_as_longlong(md)));
+          }
+        }
+        return any_bad;
+      };
+
+      faces(true);
       __syncthreads();
       if (a.kind >= 3) continue;  // features / dumps only
-
-      // 4. per cell: flux differences, sources, update, CFL bound
-      R smax_loc = R(0);
-      for (int c = tid; c < NCELL; c += STAGE_THREADS) {
-        const int ci = c & 7, cj = (c >> 3) & 7, ck = c >> 6;
-        // face indices (line * 9 + position) of the low faces in x, y, z
-        const int tx = (ck * NC + cj) * 9 + ci;
-        const int ty = (ck * NC + ci) * 9 + cj;
-        const int tz = (cj * NC + ci) * 9 + ck;
-        const R* Fx = sF;
-        const R* Fy = sF + NFC * NFACE;
-        const R* Fz = sF + 2 * NFC * NFACE;
-        R res[8];
-#pragma unroll
-        for (int v = 0; v < NV; v++) {
-          R r = -((Fx[v * NFACE + tx + 1] - Fx[v * NFACE + tx]) * idx0);
-          r = r - (Fy[v * NFACE + ty + 1] - Fy[v * NFACE + ty]) * idx1;
-          r = r - (Fz[v * NFACE + tz + 1] - Fz[v * NFACE + tz]) * idx2;
-          res[v] = r;
-        }
-        const R divb = ((Fx[8 * NFACE + tx + 1] - Fx[8 * NFACE + tx]) * idx0 +
-                        (Fy[8 * NFACE + ty + 1] - Fy[8 * NFACE + ty]) * idx1) +
-                       (Fz[8 * NFACE + tz + 1] - Fz[8 * NFACE + tz]) * idx2;
-        bool in_body = false;
-        if (B.body) {  // FP64, the same centre formula as the host and the oracle
-          double x = G.lo[0] + ((static_cast<double>(gb0) + ci) + 0.5) * G.dx[lev][0];
-          double y = G.lo[1] + ((static_cast<double>(gb1) + cj) + 0.5) * G.dx[lev][1];
-          double z = G.lo[2] + ((static_cast<double>(gb2) + ck) + 0.5) * G.dx[lev][2];
-          in_body = (x * x + y * y + z * z) < G.body_r * G.body_r;
-        }
-        R Wc[8];
-#pragma unroll
-        for (int v = 0; v < NV; v++) Wc[v] = sT[v * NTILE + c];
-        R B0c[3] = {R(0), R(0), R(0)};
-        R S[8] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
-        if constexpr (HAS_B0) b0_face<R>(ph, -1, ci, cj, ck, gb0, gb1, gb2, lor0, lor1, lor2, dxr0, dxr1, dxr2, B0c);
-        if (ph.powell) {
-          R ub1 = Wc[1] * Wc[4] + Wc[2] * Wc[5] + Wc[3] * Wc[6];
-#pragma unroll
-          for (int e = 0; e < 3; e++) {
-            S[1 + e] = -divb * (B0c[e] + Wc[4 + e]);
-            S[4 + e] = -divb * Wc[1 + e];
+      if constexpr (LRN) {
+        // fallback of the learned form: a block whose learned update leaves a
+        // non-physical cell (rho <= 0, p <= 0 or not finite) is recomputed
+        // with the plain Rusanov flux
+        if (a.learned && a.kind < 2) {
+          if (__syncthreads_or(cells(false))) {
+            faces(false);
+            __syncthreads();
+            if (tid == 0) atomicAdd(&a.err[2], 1);
           }
-          S[7] = -divb * ub1;
-        }
-        if constexpr (HAS_B0) {
-          // split-field correction from the face-centre B0 of the six faces:
-          // S_m += -B1 (div B0)_h + B1 x (curl B0)_h
-          R xm[3], xp[3], ym[3], yp[3], zm[3], zp[3];
-          b0_face<R>(ph, 0, ci, cj, ck, gb0, gb1, gb2, lor0, lor1, lor2, dxr0, dxr1, dxr2, xm);
-          b0_face<R>(ph, 0, ci + 1, cj, ck, gb0, gb1, gb2, lor0, lor1, lor2, dxr0, dxr1, dxr2, xp);
-          b0_face<R>(ph, 1, ci, cj, ck, gb0, gb1, gb2, lor0, lor1, lor2, dxr0, dxr1, dxr2, ym);
-          b0_face<R>(ph, 1, ci, cj + 1, ck, gb0, gb1, gb2, lor0, lor1, lor2, dxr0, dxr1, dxr2, yp);
-          b0_face<R>(ph, 2, ci, cj, ck, gb0, gb1, gb2, lor0, lor1, lor2, dxr0, dxr1, dxr2, zm);
-          b0_face<R>(ph, 2, ci, cj, ck + 1, gb0, gb1, gb2, lor0, lor1, lor2, dxr0, dxr1, dxr2, zp);
-          R divb0 = ((xp[0] - xm[0]) * idx0 + (yp[1] - ym[1]) * idx1) + (zp[2] - zm[2]) * idx2;
-          R cu0 = (yp[2] - ym[2]) * idx1 - (zp[1] - zm[1]) * idx2;
-          R cu1 = (zp[0] - zm[0]) * idx2 - (xp[2] - xm[2]) * idx0;
-          R cu2 = (xp[1] - xm[1]) * idx0 - (yp[0] - ym[0]) * idx1;
-          R b1x = Wc[4], b1y = Wc[5], b1z = Wc[6];
-          S[1] = (S[1] - b1x * divb0) + (b1y * cu2 - b1z * cu1);
-          S[2] = (S[2] - b1y * divb0) + (b1z * cu0 - b1x * cu2);
-          S[3] = (S[3] - b1z * divb0) + (b1x * cu1 - b1y * cu0);
-        }
-        const double cdt = a.beta * a.dt[B.grid];
-        const int64_t base = static_cast<int64_t>(blk) * (NV * NCELL) + c;
-        double Uo[8];
-        bool bad = false;
-#pragma unroll
-        for (int v = 0; v < NV; v++) {
-          R r = res[v] + S[v];
-          double rd;
-          if constexpr (MIXED) rd = f2d_int(r);
-          else rd = r;
-          double ub = a.Ubase[base + v * NCELL];
-          double o;
-          if (a.kind == 0) o = fma(cdt, rd, ub);
-          else o = 0.5 * ub + 0.5 * fma(cdt, rd, a.Uin[base + v * NCELL]);
-          if (a.kind == 2) o = rd;  // residual only (debug view)
-          o = in_body ? (a.kind == 2 ? 0.0 : G.Ubody[v]) : o;
-          Uo[v] = o;
-          bad |= !finite_d(o);
-        }
-        if (a.kind != 2) bad |= !positive_d(Uo[0]);
-        R Wn[8];
-        const bool need_w = MIXED || a.last;
-        if (need_w && a.kind != 2) {
-          if constexpr (MIXED) {
-            double p64;
-            prim_mixed(Uo, ph.gm1f, Wn, &p64);
-            bad |= !positive_d(p64);
-          } else {
-            prim64(Uo, ph.gm1, Wn);
-            bad |= !positive_d(Wn[7]);
-          }
-        }
-        if (bad && !in_body && a.kind != 2) {
-          atomicOr(&a.err[0], ERR_NONPHYSICAL);
-          atomicMin(&a.err[1], blk);
-        }
-        const bool write_u = !MIXED || a.last || a.write_u_all || B.need_u;
-        if (write_u || a.kind == 2) {
-#pragma unroll
-          for (int v = 0; v < NV; v++) a.Uout[base + v * NCELL] = Uo[v];
-        }
-        if constexpr (MIXED) {
-          if (a.kind != 2) {
-#pragma unroll
-            for (int v = 0; v < NV; v++) a.Wout[base + v * NCELL] = Wn[v];
-          }
-        }
-        // CFL bound of the new state: sum_d (|u_d| + c_f,d) / dx_d
-        if (a.last && !in_body && a.kind != 2) {
-          R Bt[3] = {B0c[0] + Wn[4], B0c[1] + Wn[5], B0c[2] + Wn[6]};
-          R sacc = R(0);
-#pragma unroll
-          for (int e = 0; e < 3; e++) {
-            R bn = Bt[e], bt1 = Bt[(e + 1) % 3], bt2 = Bt[(e + 2) % 3];
-            R cf;
-            if constexpr (MIXED) {
-              cf = fast_speed_n<R>(gamma, Wn[0], Wn[7], bn, bt1, bt2);
-              sacc = sacc + (Ops<R>::abs_(Wn[1 + e]) + cf) * (e == 0 ? idx0 : (e == 1 ? idx1 : idx2));
-            } else {
-              cf = fast_speed_exact(ph.gamma, Wn[0], Wn[7], bn, bt1, bt2);
-              sacc = sacc + (Ops<R>::abs_(Wn[1 + e]) + cf) / (e == 0 ? dxr0 : (e == 1 ? dxr1 : dxr2));
-            }
-          }
-          smax_loc = sacc > smax_loc ? sacc : smax_loc;
         }
       }
-      if (a.last && a.kind != 2) {
-        R m = smax_loc;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          R q = __shfl_xor_sync(0xffffffffu, m, o);
-          m = q > m ? q : m;
-        }
-        if ((tid & 31) == 0) sred[tid >> 5] = m;
-        __syncthreads();
-        if (tid == 0) {
-          R mm = R(0);
-          for (int w = 0; w < STAGE_THREADS / 32; w++) mm = sred[w] > mm ? sred[w] : mm;
-          double md;
-          if constexpr (MIXED) md = f2d_int(mm);
-          else md = mm;
-          if (md > 0.0) atomicMax(&a.smax_next[B.grid], static_cast<unsigned long long>(__double_as_longlong(md)));
-        }
-      }
+      cells(true);
       __syncthreads();
     }
   }

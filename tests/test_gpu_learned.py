@@ -12,6 +12,8 @@ import pytest
 from oracle import oracle as O
 from paper_2501_06717_gb300 import workloads as W
 
+from learned_nets import double_dissipation_net, physical_per_block
+
 pytestmark = pytest.mark.gpu
 
 
@@ -169,3 +171,34 @@ def test_learned_graph_replay_equals_eager(B):
             s.step(2, 0.8)
             outs.append(s.get_state(0))
     assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("precision,graph", [("fp64", 0), ("mixed", 0), ("mixed", 1)])
+def test_learned_fallback_matches_oracle(B, precision, graph):
+    """A network that doubles the dissipation of rho and e1 (weights 0, +-1,
+    +-1000: exact in BF16) drives p to about -0.053 in 8 blocks next to the
+    jump of a blast with p_in = 1.5 in the first step's second stage; the plain
+    recompute gives p >= 0.0166 there and every other block keeps p >= 0.1.
+    The decisions are far from the threshold, so the GPU must make the
+    oracle's (8 block-stages) and match its (physical) result."""
+    q = W.blast(pin=1.5)
+    P = double_dissipation_net()
+    ql = W.Problem(**{**q.__dict__, "learned": 1, "mlp": P})
+    dt = 0.8 / O.cfl_smax(q, q.U0)
+    Uo, _, _, nfb = O.run(ql, q.U0, 1, dt=dt, with_fallbacks=True)
+    Up, _, _ = O.run(q, q.U0, 1, dt=dt)
+    assert nfb == 8
+    prec = B.BATS_FP64 if precision == "fp64" else B.BATS_MIXED
+    with B.Solver(q, precision=prec, persistent=graph, use_graph=graph) as s:
+        s.set_mlp(P.astype(np.float32))
+        s.set_state(0, q.U0)
+        s.step_dt(1, dt)
+        Ug = s.get_state(0)
+        assert s.fallbacks() == nfb
+    assert physical_per_block(q.gamma, Ug).all()
+    scale = np.abs(Uo).reshape(8, -1).max(1)
+    err = (np.abs(Ug - Uo).reshape(8, -1).max(1) / scale).max()
+    effect = (np.abs(Uo - Up).reshape(8, -1).max(1) / scale).max()
+    print("fallback: max scaled error", err, "effect of the network", effect)
+    assert effect > 1e-3
+    assert err <= 3e-2 * effect

@@ -175,3 +175,19 @@ def test_learned_fallback_count_over_a_run():
     qz = W.Problem(**{**q.__dict__, "learned": 1, "mlp": np.zeros(O.MLP_NPARAM)})
     _, _, _, nz = O.run(qz, q.U0, 3, cfl=0.8, with_fallbacks=True)
     assert nz == 0
+
+
+def test_learned_fallback_rescues_a_stage_the_plain_flux_keeps_physical():
+    """Blast with p_in = 1.5 at CFL 0.8: the doubled dissipation makes 8 blocks
+    non-physical in the first step's second stage; their plain recompute is
+    physical, so the step ends physical, unlike the unguarded learned step."""
+    import copy
+    q = W.blast(pin=1.5)
+    ql = W.Problem(**{**q.__dict__, "learned": 1, "mlp": double_dissipation_net()})
+    U, _, _, nfb = O.run(ql, q.U0, 1, cfl=0.8, with_fallbacks=True)
+    assert nfb == 8
+    assert physical_per_block(q.gamma, U).all()
+    qn = copy.copy(ql)
+    qn.no_fallback = 1
+    Un, _, _ = O.run(qn, q.U0, 1, cfl=0.8)
+    assert (~physical_per_block(q.gamma, Un)).sum() == 8
