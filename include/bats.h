@@ -163,6 +163,13 @@ int bats_get_timings(bats_t* h, double* ms, int n);
  * set to 0. */
 int bats_debug_fill_ghosts(bats_t* h, int grid, double* T, size_t n);
 
+/* Mixed form (BATS_MIXED handles only, else BATS_ERR_INVALID_ARG): the same
+ * view of the FP32 ghost fill, as primitives (rho, u, B1, p) widened to
+ * double, same layout.  At resolution changes these are the restriction (the
+ * conservative mean of the 8 children) and the prolongation of Section 4.2
+ * written in primitive form from the FP32 primitive copies. */
+int bats_debug_fill_ghosts_w(bats_t* h, int grid, double* T, size_t n);
+
 /* Debug view of one stage: R = dU/dt of the current state of grid `grid`
  * (fluxes, sources; body cells 0), double [8][n_blocks][8][8][8]. */
 int bats_debug_residual(bats_t* h, int grid, double* R, size_t n);

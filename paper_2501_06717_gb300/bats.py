@@ -95,6 +95,7 @@ def lib():
     L.bats_get_time.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     L.bats_get_timings.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
     L.bats_debug_fill_ghosts.argtypes = [vp, ctypes.c_int, dp, ctypes.c_size_t]
+    L.bats_debug_fill_ghosts_w.argtypes = [vp, ctypes.c_int, dp, ctypes.c_size_t]
     L.bats_debug_residual.argtypes = [vp, ctypes.c_int, dp, ctypes.c_size_t]
     L.bats_set_launch.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     L.bats_get_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
@@ -247,6 +248,12 @@ def bats_get_timings(h):
 def bats_debug_fill_ghosts(h, grid, out):
     p, n = _ptr_and_size(out)
     _check(h, lib().bats_debug_fill_ghosts(h, int(grid), p, n))
+    return out
+
+
+def bats_debug_fill_ghosts_w(h, grid, out):
+    p, n = _ptr_and_size(out)
+    _check(h, lib().bats_debug_fill_ghosts_w(h, int(grid), p, n))
     return out
 
 
@@ -466,6 +473,11 @@ class Solver:
         p = self.problems[grid]
         out = np.zeros((8, p.nb, 12, 12, 12))
         return bats_debug_fill_ghosts(self.h, grid, out)
+
+    def fill_ghosts_w(self, grid=0):
+        p = self.problems[grid]
+        out = np.zeros((8, p.nb, 12, 12, 12))
+        return bats_debug_fill_ghosts_w(self.h, grid, out)
 
     def residual(self, grid=0):
         p = self.problems[grid]

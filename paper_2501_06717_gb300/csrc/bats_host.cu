@@ -32,6 +32,7 @@ cudaError_t launch_cfl(bool mixed, const double* U, const float* Wt, const GridD
 cudaError_t launch_dt(int ngrids, int mode, double cfl, double fixed_dt, double* dt, double* t,
                       unsigned long long* smax, unsigned long long* smax_next, cudaStream_t st);
 cudaError_t launch_debug_fill(const StageArgs& a, int b0, int nb, double* T, cudaStream_t st);
+cudaError_t launch_debug_fill_w(const StageArgs& a, int b0, int nb, double* T, cudaStream_t st);
 cudaError_t launch_check_conversions(const float* f, const double* d, int n, double* f2d_out, float* d2f_out);
 cudaError_t mlp_alloc(MlpDev* w);
 void mlp_free(MlpDev* w);
@@ -171,7 +172,6 @@ int build_grid(bats_t* h, const bats_grid_desc& d, int gidx, int block0, std::ve
     }
   }
   // neighbour relations through the 26 directions, 2:1 balance, face table
-  std::vector<std::vector<int>> touching(d.n_leaves);
   blocks.resize(block0 + d.n_leaves);
   for (int b = 0; b < d.n_leaves; b++) {
     const int32_t* L = d.leaves + 4 * b;
@@ -213,7 +213,6 @@ int build_grid(bats_t* h, const bats_grid_desc& d, int gidx, int block0, std::ve
           if (id >= 0) {
             if (lc < l - 1)
               return fail(h, BATS_ERR_UNBALANCED_TREE, "grid " + std::to_string(gidx) + ": neighbours differ by more than one level");
-            touching[b].push_back(id);
             if (face >= 0) {
               B.ftype[face] = lc == l ? FACE_SAME : FACE_COARSER;
               B.fnb[face] = block0 + id;
@@ -231,7 +230,6 @@ int build_grid(bats_t* h, const bats_grid_desc& d, int gidx, int block0, std::ve
               int32_t cid = H.at(l + 1, 2 * p[0] + oo[0], 2 * p[1] + oo[1], 2 * p[2] + oo[2]);
               if (cid < 0)
                 return fail(h, BATS_ERR_UNBALANCED_TREE, "grid " + std::to_string(gidx) + ": neighbours differ by more than one level");
-              touching[b].push_back(cid);
             }
             if (face >= 0) {
               B.ftype[face] = FACE_FINER;
@@ -242,11 +240,6 @@ int build_grid(bats_t* h, const bats_grid_desc& d, int gidx, int block0, std::ve
     for (int s = 0; s < 6; s++)
       if (B.ftype[s] == FACE_COARSER || B.ftype[s] == FACE_FINER) B.amr = 1;
     blocks[block0 + b] = B;
-  }
-  for (int b = 0; b < d.n_leaves; b++) {
-    if (!blocks[block0 + b].amr) continue;
-    blocks[block0 + b].need_u = 1;
-    for (int id : touching[b]) blocks[block0 + id].need_u = 1;
   }
   // grid record + level maps with global block indices
   std::memset(&gd, 0, sizeof(gd));
@@ -732,6 +725,26 @@ int bats_debug_fill_ghosts(bats_t* h, int grid, double* T, size_t n) {
   int32_t init[3] = {0, INT_MAX, 0};
   CK(h, cudaMemcpyAsync(h->errw, init, sizeof(init), cudaMemcpyHostToDevice, h->stream));
   CK(h, launch_debug_fill(a, G.block0, G.nb, dst, h->stream));
+  if (!dev) CK(h, cudaMemcpyAsync(T, h->staging, need * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return BATS_OK;
+}
+
+int bats_debug_fill_ghosts_w(bats_t* h, int grid, double* T, size_t n) {
+  int rc = grid_check(h, grid);
+  if (rc) return rc;
+  if (h->ph.precision != BATS_MIXED) return fail(h, BATS_ERR_INVALID_ARG, "mixed form only");
+  const GridDev& G = h->grids_h[grid];
+  size_t need = static_cast<size_t>(G.nb) * NV * 1728;
+  if (!T || n != need) return fail(h, BATS_ERR_INVALID_ARG, "tile size mismatch");
+  bool dev = is_device_ptr(T);
+  double* dst = dev ? T : h->staging;
+  StageArgs a = base_args(h);
+  a.Uin = h->U;
+  a.Win = h->W;
+  int32_t init[3] = {0, INT_MAX, 0};
+  CK(h, cudaMemcpyAsync(h->errw, init, sizeof(init), cudaMemcpyHostToDevice, h->stream));
+  CK(h, launch_debug_fill_w(a, G.block0, G.nb, dst, h->stream));
   if (!dev) CK(h, cudaMemcpyAsync(T, h->staging, need * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
   return BATS_OK;

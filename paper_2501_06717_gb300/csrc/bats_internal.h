@@ -44,11 +44,8 @@ struct BlockDev {
   int32_t ftype[6];              // FaceType per face (-x, +x, -y, +y, -z, +z)
   int32_t fnb[6];                // neighbour block (global index) for SAME / COARSER
   int32_t amr;                   // 1 if any face is COARSER or FINER
-  int32_t need_u;                // mixed form: FP64 stage output read by a neighbour's
-                                 // restriction/prolongation (this block or a block it
-                                 // touches has a COARSER/FINER face)
   int32_t body;                  // 1 if some cell centre lies inside the inner body
-  int32_t pad_;
+  int32_t pad_[2];
 };
 
 struct PhysDev {
@@ -86,7 +83,7 @@ struct StageArgs {
                           // 2: Uout = R (debug);  3: face features only (Xb);
                           // 4: features and plain fluxes only (Xf, Fd)
   int32_t last;           // 1: reduce the CFL bound of Uout into smax_next
-  int32_t write_u_all;    // mixed: 1 = write Uout for every block, 0 = only need_u blocks
+  int32_t write_u_all;    // mixed: 1 = write Uout (FP64) too, 0 = only the FP32 primitives Wout
   double beta;            // c = beta * dt[grid]
   PhysDev ph;
   // learned form; face index ((blk * 3 + d) * 576 + line * 9 + f)

@@ -211,7 +211,6 @@ int build_tables(const bats_grid_desc& d, Tables& T, char* err, size_t len) {
         }
     for (int s = 0; s < 6; s++)
       if (B.ftype[s] == FACE_COARSER || B.ftype[s] == FACE_FINER) B.amr = 1;
-    B.need_u = 1;
     T.blocks[b] = B;
   }
   for (int a = 0; a < 3; a++) {

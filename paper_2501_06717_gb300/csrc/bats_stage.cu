@@ -49,6 +49,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// Hint that [p, p + bytes) will be read soon: bring it into L2 (p 16-byte
+// aligned, bytes a multiple of 16).
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ uint64_t globaltimer() {
   uint64_t t;
@@ -538,6 +543,213 @@ __device__ __noinline__ void prolong_item(const GhostCtx& cx, const BlockDev& B,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Mixed form: ghost cells at resolution changes from the FP32 primitive
+// copies W alone; the FP64 state is never read by a ghost fill.  Every value
+// is the same quantity the FP64 path computes from the conservative state
+// (the conservative mean of the children; the coarse value plus limited
+// slopes of the conservative variables), rearranged so that the pressure is
+// never the small difference of two large numbers: the stored p of each cell
+// is FP64-accurate, and only differences and variances are formed in FP32.
+
+// Primitives of cell g (global, level of `leaf`) from W.
+__device__ __forceinline__ void load_w(const float* Wt, const BlockDev* blocks, int leaf, const int g[3], float w[8]) {
+  const BlockDev& B = blocks[leaf];
+  const int li = g[0] - B.bi * NC, lj = g[1] - B.bj * NC, lk = g[2] - B.bk * NC;
+  const float* p = Wt + static_cast<int64_t>(leaf) * (NV * NCELL) + (lk * NC + lj) * NC + li;
+#pragma unroll
+  for (int v = 0; v < NV; v++) w[v] = p[v * NCELL];
+}
+
+__device__ __forceinline__ float sum8(const float c[8]) {
+  return ((c[0] + c[1]) + (c[2] + c[3])) + ((c[4] + c[5]) + (c[6] + c[7]));
+}
+
+// Restriction in primitive form: the conservative mean of the 8 children
+// (level lev + 1) of cell g (level lev), as primitives.  With rho~ = mean rho_i,
+// u~ = sum rho_i u_i / sum rho_i and B~ = mean B_i, the pressure of the mean
+// state is p~ = mean p_i + (gamma - 1) [mean(rho_i |u_i - u~|^2) + mean(|B_i - B~|^2)] / 2
+// (the kinetic and magnetic energies of the mean fall short of the mean
+// energies by those two variances), a sum of non-negative terms.
+__device__ __noinline__ void restrict_w(const float* Wt, const GridDev& G, const BlockDev* blocks,
+                                        const int32_t* levmap, int lev, const int g[3], float gm1f, float w[8],
+                                        int32_t* err) {
+  const int f[3] = {2 * g[0], 2 * g[1], 2 * g[2]};
+  int ll;
+  const int leaf = locate(G, levmap, lev + 1, f, ll);
+  if (leaf < 0 || ll != lev + 1) {
+    atomicOr(err, ERR_BOUNDS);
+#pragma unroll
+    for (int v = 0; v < NV; v++) w[v] = 0.f;
+    return;
+  }
+  const BlockDev& B = blocks[leaf];
+  const int li = f[0] - B.bi * NC, lj = f[1] - B.bj * NC, lk = f[2] - B.bk * NC;
+  const float* p = Wt + static_cast<int64_t>(leaf) * (NV * NCELL) + (lk * NC + lj) * NC + li;
+  const int off[8] = {0, 1, NC, NC + 1, NC * NC, NC * NC + 1, NC * NC + NC, NC * NC + NC + 1};
+  float rho[8], c[8];
+#pragma unroll
+  for (int o = 0; o < 8; o++) rho[o] = p[off[o]];
+  const float srho = sum8(rho);
+  const float irs = rcp_approx(srho);
+  float ut[3], var = 0.f;
+#pragma unroll
+  for (int e = 0; e < 3; e++) {
+    float u[8];
+#pragma unroll
+    for (int o = 0; o < 8; o++) u[o] = p[(1 + e) * NCELL + off[o]];
+    const float ub = 0.125f * sum8(u);
+#pragma unroll
+    for (int o = 0; o < 8; o++) c[o] = rho[o] * (u[o] - ub);
+    ut[e] = ub + sum8(c) * irs;
+#pragma unroll
+    for (int o = 0; o < 8; o++) {
+      const float du = u[o] - ut[e];
+      c[o] = rho[o] * du * du;
+    }
+    var += sum8(c);
+  }
+  float bt[3];
+#pragma unroll
+  for (int e = 0; e < 3; e++) {
+    float b[8];
+#pragma unroll
+    for (int o = 0; o < 8; o++) b[o] = p[(4 + e) * NCELL + off[o]];
+    bt[e] = 0.125f * sum8(b);
+#pragma unroll
+    for (int o = 0; o < 8; o++) {
+      const float db = b[o] - bt[e];
+      c[o] = db * db;
+    }
+    var += sum8(c);
+  }
+#pragma unroll
+  for (int o = 0; o < 8; o++) c[o] = p[7 * NCELL + off[o]];
+  w[0] = 0.125f * srho;
+  w[1] = ut[0];
+  w[2] = ut[1];
+  w[3] = ut[2];
+  w[4] = bt[0];
+  w[5] = bt[1];
+  w[6] = bt[2];
+  w[7] = 0.125f * sum8(c) + gm1f * (0.0625f * var);
+}
+
+// Primitives of the cell g (global, level lev): boundary mapping, then copy
+// (leaf at lev) or restriction (finer region); a coarser leaf is excluded by
+// the 2:1 balance and flagged.
+__device__ __noinline__ void sample_w(const float* Wt, const GridDev& G, const BlockDev* blocks,
+                                      const int32_t* levmap, int lev, int g[3], float gm1f, float w[8],
+                                      int32_t* err) {
+  if (bc_map(G, lev, g)) {
+#pragma unroll
+    for (int v = 0; v < NV; v++) w[v] = G.Winflow32[v];
+    return;
+  }
+  int ll;
+  const int leaf = locate(G, levmap, lev, g, ll);
+  if (leaf >= 0 && ll == lev) {
+    load_w(Wt, blocks, leaf, g, w);
+  } else if (leaf < 0) {
+    restrict_w(Wt, G, blocks, levmap, lev, g, gm1f, w, err);
+  } else {
+    atomicOr(err, ERR_BOUNDS);
+#pragma unroll
+    for (int v = 0; v < NV; v++) w[v] = 0.f;
+  }
+}
+
+// Coarse samples of the prolongation of one COARSER face: the 6 x 6 box of
+// the coarse layer that holds the face's ghost cells (its 4 corners are not
+// used), the 4 x 4 cells one coarse layer inwards (inside this block) and
+// one outwards.  Per sample the table holds the conservative state (FP32),
+// p and u.
+constexpr int PSLOTS = 68;
+constexpr int PSTRIDE = 12;
+
+__device__ __forceinline__ bool psample(const BlockDev& B, int s, int k, int gc[3]) {
+  const int d = s >> 1, side = s & 1;
+  const int ta = d == 0 ? 1 : 0, tb = d == 2 ? 1 : 2;
+  const int co[3] = {B.bi * (NC / 2), B.bj * (NC / 2), B.bk * (NC / 2)};
+  int t1, t2, n;
+  if (k < 36) {
+    t1 = k % 6;
+    t2 = k / 6;
+    if ((t1 == 0 || t1 == 5) && (t2 == 0 || t2 == 5)) return false;
+    n = side ? co[d] + 4 : co[d] - 1;
+  } else {
+    const int j = k < 52 ? k - 36 : k - 52;
+    t1 = 1 + (j & 3);
+    t2 = 1 + (j >> 2);
+    n = k < 52 ? (side ? co[d] + 3 : co[d]) : (side ? co[d] + 5 : co[d] - 2);
+  }
+  gc[d] = n;
+  gc[ta] = co[ta] - 1 + t1;
+  gc[tb] = co[tb] - 1 + t2;
+  return true;
+}
+
+// Fine ghost cell `local` (0..127, as in the face slab) of COARSER face s
+// from the sample table: the coarse value plus (+-1/4) x minmod of the
+// undivided coarse differences of the conservative variables (x, then y,
+// then z), turned into primitives through the increments of the coarse
+// cell's own primitives.  With dU the increment: rho = rho_c + drho,
+// u = u_c + (dm - u_c drho) / rho, B = B_c + dB and
+// p = p_c + (gamma - 1) [de - dK - (B_c.dB + |dB|^2 / 2)],
+// dK = (2 rho_c u_c.dm - rho_c drho |u_c|^2 + |dm|^2) / (2 rho).
+__device__ __forceinline__ void prolong_child_w(const float* tab, int s, int local, float gm1f, float w[8]) {
+  const int d = s >> 1, side = s & 1;
+  const int ta = d == 0 ? 1 : 0;
+  const int on = local & 1, taf = (local >> 1) & 7, tbf = local >> 4;
+  const int ca = taf >> 1, oa = taf & 1, cb = tbf >> 1, ob = tbf & 1;
+  const int kc = (cb + 1) * 6 + (ca + 1);
+  const int kin = 36 + ca + 4 * cb, kfar = 52 + ca + 4 * cb;
+  const float* Uc = tab + kc * PSTRIDE;
+  float dl[8];
+#pragma unroll
+  for (int v = 0; v < NV; v++) dl[v] = 0.f;
+#pragma unroll
+  for (int ax = 0; ax < 3; ax++) {
+    int km, kp, odd;
+    if (ax == d) {
+      km = side ? kin : kfar;
+      kp = side ? kfar : kin;
+      odd = on;
+    } else if (ax == ta) {
+      km = kc - 1;
+      kp = kc + 1;
+      odd = oa;
+    } else {
+      km = kc - 6;
+      kp = kc + 6;
+      odd = ob;
+    }
+    const float* Um = tab + km * PSTRIDE;
+    const float* Up = tab + kp * PSTRIDE;
+    const float sg = odd ? 0.25f : -0.25f;
+#pragma unroll
+    for (int v = 0; v < NV; v++) dl[v] = dl[v] + sg * minmod_<float>(Uc[v] - Um[v], Up[v] - Uc[v]);
+  }
+  const float rc = Uc[0], pc = Uc[8];
+  const float uc0 = Uc[9], uc1 = Uc[10], uc2 = Uc[11];
+  const float rf = rc + dl[0];
+  const float irf = rcp_approx(rf);
+  const float udm = uc0 * dl[1] + uc1 * dl[2] + uc2 * dl[3];
+  const float usq = uc0 * uc0 + uc1 * uc1 + uc2 * uc2;
+  const float dmsq = dl[1] * dl[1] + dl[2] * dl[2] + dl[3] * dl[3];
+  const float dK = 0.5f * ((2.f * rc * udm - rc * dl[0] * usq) + dmsq) * irf;
+  const float dM = (Uc[4] * dl[4] + Uc[5] * dl[5] + Uc[6] * dl[6]) +
+                   0.5f * (dl[4] * dl[4] + dl[5] * dl[5] + dl[6] * dl[6]);
+  w[0] = rf;
+  w[1] = uc0 + (dl[1] - uc0 * dl[0]) * irf;
+  w[2] = uc1 + (dl[2] - uc1 * dl[0]) * irf;
+  w[3] = uc2 + (dl[3] - uc2 * dl[0]) * irf;
+  w[4] = Uc[4] + dl[4];
+  w[5] = Uc[5] + dl[5];
+  w[6] = Uc[6] + dl[6];
+  w[7] = pc + gm1f * ((dl[7] - dK) - dM);
+}
+
 // Tile index of cell c (-2..9) along direction d at transverse (a, b).
 __device__ __forceinline__ int tile_index(int d, int c, int a, int b) {
   int gi = 2 * d + (c >= NC ? 1 : 0);
@@ -585,11 +797,14 @@ __device__ __forceinline__ void fill_ghost(const StageArgs& a, const GhostCtx& c
     g[0] = B.bi * NC + i;
     g[1] = B.bj * NC + j;
     g[2] = B.bk * NC + k;
-    double u[8];
-    ghost_value(cx, B.level, g, u);
     if constexpr (MIXED) {
-      prim_mixed(u, a.ph.gm1f, w);
+      float wf[8];
+      sample_w(a.Win, *cx.G, cx.blocks, cx.levmap, B.level, g, a.ph.gm1f, wf, cx.err);
+#pragma unroll
+      for (int v = 0; v < NV; v++) w[v] = wf[v];
     } else {
+      double u[8];
+      ghost_value(cx, B.level, g, u);
 #pragma unroll
       for (int v = 0; v < NV; v++) w[v] = u[v];
     }
@@ -643,6 +858,57 @@ __device__ __forceinline__ void fill_ghosts_block(const StageArgs& a, const Ghos
 #pragma unroll
         for (int v = 0; v < NV; v++) w[v] = uu[v];
       }
+      const int t = NCELL + sface * 128 + local;
+#pragma unroll
+      for (int v = 0; v < NV; v++) sT[v * NTILE + t] = w[v];
+    }
+  }
+}
+
+// Mixed form: all face-slab ghosts of block blk from W.  Faces whose
+// neighbour is coarser go through the sample table `tab` (up to three such
+// faces, PSLOTS x PSTRIDE floats each): the samples are gathered together
+// with the other ghost cells, then, after a barrier, each fine ghost cell of
+// those faces is built from the table.
+__device__ __forceinline__ void fill_ghosts_block_mixed(const StageArgs& a, const GhostCtx& cx, const BlockDev& B,
+                                                        int blk, float* sT, float* tab, int tid, int nthr) {
+  unsigned cmask = 0;
+#pragma unroll
+  for (int f = 0; f < 6; f++) cmask |= (B.ftype[f] == FACE_COARSER ? 1u : 0u) << f;
+  const int ncoarse = __popc(cmask);
+  const int nsamp = ncoarse * PSLOTS;
+  for (int q = tid; q < nsamp + NGHOST; q += nthr) {
+    if (q < nsamp) {
+      const int slot = q / PSLOTS, k = q - slot * PSLOTS;
+      unsigned m = cmask;
+      for (int r = 0; r < slot; r++) m &= m - 1;
+      const int sface = __ffs(m) - 1;
+      int gc[3];
+      if (!psample(B, sface, k, gc)) continue;
+      float w[8], u[8];
+      sample_w(a.Win, *cx.G, cx.blocks, cx.levmap, B.level - 1, gc, a.ph.gm1f, w, cx.err);
+      cons_from_prim<float>(w, a.ph.inv_gm1f, u);
+      float* e = tab + (slot * PSLOTS + k) * PSTRIDE;
+#pragma unroll
+      for (int v = 0; v < NV; v++) e[v] = u[v];
+      e[8] = w[7];
+      e[9] = w[1];
+      e[10] = w[2];
+      e[11] = w[3];
+    } else {
+      const int g = q - nsamp;
+      if (!((cmask >> (g >> 7)) & 1u)) fill_ghost<true, float>(a, cx, B, blk, g, sT);
+    }
+  }
+  if (ncoarse) {
+    __syncthreads();
+    for (int q = tid; q < ncoarse * 128; q += nthr) {
+      const int slot = q >> 7, local = q & 127;
+      unsigned m = cmask;
+      for (int r = 0; r < slot; r++) m &= m - 1;
+      const int sface = __ffs(m) - 1;
+      float w[8];
+      prolong_child_w(tab + slot * PSLOTS * PSTRIDE, sface, local, a.ph.gm1f, w);
       const int t = NCELL + sface * 128 + local;
 #pragma unroll
       for (int v = 0; v < NV; v++) sT[v * NTILE + t] = w[v];
@@ -743,8 +1009,13 @@ __global__ void __launch_bounds__(STAGE_THREADS, MIXED ? 2 : 1) k_stage(const St
         src += static_cast<int64_t>(blk) * (NV * NCELL);
 #pragma unroll
         for (int v = 0; v < NV; v++) bulk_g2s(sT + v * NTILE, src + v * NCELL, NCELL * sizeof(R), &bar);
+        // the FP64 states the cell phase reads, on their way to L2 meanwhile
+        const int64_t boff = static_cast<int64_t>(blk) * (NV * NCELL);
+        if (a.kind < 3) prefetch_l2(a.Ubase + boff, NV * NCELL * sizeof(double));
+        if (MIXED && a.kind == 1) prefetch_l2(a.Uin + boff, NV * NCELL * sizeof(double));
       }
-      fill_ghosts_block<MIXED, R>(a, cx, B, blk, sT, reinterpret_cast<double*>(sF), tid, STAGE_THREADS);
+      if constexpr (MIXED) fill_ghosts_block_mixed(a, cx, B, blk, sT, sF, tid, STAGE_THREADS);
+      else fill_ghosts_block<false, double>(a, cx, B, blk, sT, sF, tid, STAGE_THREADS);
       if (!mbar_wait_bounded(&bar, parity, a.err)) mbar_wait_bounded(&bar, parity, a.err);
       parity ^= 1u;
       __syncthreads();
@@ -1011,7 +1282,7 @@ __global__ void __launch_bounds__(STAGE_THREADS, MIXED ? 2 : 1) k_stage(const St
             }
           }
           if (!commit) continue;
-          const bool write_u = !MIXED || a.last || a.write_u_all || B.need_u;
+          const bool write_u = !MIXED || a.last || a.write_u_all;
           if (write_u || a.kind == 2) {
 #pragma unroll
             for (int v = 0; v < NV; v++) a.Uout[base + v * NCELL] = Uo[v];
@@ -1206,19 +1477,11 @@ __global__ void k_dt(int ngrids, int mode, double cfl, double fixed_dt, double* 
   }
 }
 
-// Debug view of the ghost fill: padded tiles [8][nb][12][12][12] (external
-// layout) of blocks [b0, b0+nb): the interior and the face slabs, filled by
-// the same code as the stage kernel (FP64 form); edge/corner cells are 0.
-__global__ void k_debug_fill(const StageArgs a, int b0, int nb, double* T) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  double* sT = reinterpret_cast<double*>(smem_raw);
-  const int blk = b0 + blockIdx.x;
-  const BlockDev& B = a.blocks[blk];
-  GhostCtx cx{&a.grids[B.grid], a.blocks, a.levmap, a.Uin, a.err};
-  for (int e = threadIdx.x; e < NV * NCELL; e += blockDim.x)
-    sT[(e / NCELL) * NTILE + (e % NCELL)] = a.Uin[static_cast<int64_t>(blk) * NV * NCELL + e];
-  fill_ghosts_block<false, double>(a, cx, B, blk, sT, sT + NV * NTILE, threadIdx.x, blockDim.x);
-  __syncthreads();
+// Padded tiles [8][nb][12][12][12] (external layout) of the shared-memory
+// tile of block blockIdx.x: the interior and the face slabs; edge and corner
+// cells are 0.
+template <class R>
+__device__ void write_debug_tile(const R* sT, int nb, double* T) {
   const int tile = 12 * 12 * 12;
   for (int e = threadIdx.x; e < tile; e += blockDim.x) {
     int i = e % 12 - 2, j = (e / 12) % 12 - 2, k = e / 144 - 2;
@@ -1232,8 +1495,38 @@ __global__ void k_debug_fill(const StageArgs a, int b0, int nb, double* T) {
       t = tile_index(d, c, ta, tb);
     }
     for (int v = 0; v < NV; v++)
-      T[(static_cast<int64_t>(v) * nb + blockIdx.x) * tile + e] = t >= 0 ? sT[v * NTILE + t] : 0.0;
+      T[(static_cast<int64_t>(v) * nb + blockIdx.x) * tile + e] = t >= 0 ? static_cast<double>(sT[v * NTILE + t]) : 0.0;
   }
+}
+
+// Debug view of the ghost fill of blocks [b0, b0+nb), filled by the same code
+// as the stage kernel: FP64 form, conservative variables.
+__global__ void k_debug_fill(const StageArgs a, int b0, int nb, double* T) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  double* sT = reinterpret_cast<double*>(smem_raw);
+  const int blk = b0 + blockIdx.x;
+  const BlockDev& B = a.blocks[blk];
+  GhostCtx cx{&a.grids[B.grid], a.blocks, a.levmap, a.Uin, a.err};
+  for (int e = threadIdx.x; e < NV * NCELL; e += blockDim.x)
+    sT[(e / NCELL) * NTILE + (e % NCELL)] = a.Uin[static_cast<int64_t>(blk) * NV * NCELL + e];
+  fill_ghosts_block<false, double>(a, cx, B, blk, sT, sT + NV * NTILE, threadIdx.x, blockDim.x);
+  __syncthreads();
+  write_debug_tile(sT, nb, T);
+}
+
+// The same for the mixed form: FP32 primitives from W.
+constexpr size_t kDebugFillWSmem = sizeof(float) * (NV * NTILE + 3 * PSLOTS * PSTRIDE);
+__global__ void k_debug_fill_w(const StageArgs a, int b0, int nb, double* T) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float* sT = reinterpret_cast<float*>(smem_raw);
+  const int blk = b0 + blockIdx.x;
+  const BlockDev& B = a.blocks[blk];
+  GhostCtx cx{&a.grids[B.grid], a.blocks, a.levmap, a.Uin, a.err};
+  for (int e = threadIdx.x; e < NV * NCELL; e += blockDim.x)
+    sT[(e / NCELL) * NTILE + (e % NCELL)] = a.Win[static_cast<int64_t>(blk) * NV * NCELL + e];
+  fill_ghosts_block_mixed(a, cx, B, blk, sT, sT + NV * NTILE, threadIdx.x, blockDim.x);
+  __syncthreads();
+  write_debug_tile(sT, nb, T);
 }
 
 // Conversion self-check against CUDA's own conversions: n float/double pairs.
@@ -1276,6 +1569,9 @@ cudaError_t stage_setup(int occ[2]) {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_debug_fill, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(sizeof(double) * (NV * NTILE + 3 * 128 * NV)));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_debug_fill_w, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kDebugFillWSmem));
   if (e == cudaSuccess)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], stage_fn<false>(0, false), STAGE_THREADS,
                                                       StageCfg<false>::SMEM);
@@ -1324,6 +1620,10 @@ cudaError_t launch_dt(int ngrids, int mode, double cfl, double fixed_dt, double*
 }
 cudaError_t launch_debug_fill(const StageArgs& a, int b0, int nb, double* T, cudaStream_t st) {
   k_debug_fill<<<nb, 256, sizeof(double) * (NV * NTILE + 3 * 128 * NV), st>>>(a, b0, nb, T);
+  return cudaGetLastError();
+}
+cudaError_t launch_debug_fill_w(const StageArgs& a, int b0, int nb, double* T, cudaStream_t st) {
+  k_debug_fill_w<<<nb, 256, kDebugFillWSmem, st>>>(a, b0, nb, T);
   return cudaGetLastError();
 }
 cudaError_t launch_check_conversions(const float* f, const double* d, int n, double* f2d_out, float* d2f_out) {
