@@ -324,6 +324,33 @@ __device__ __forceinline__ bool finite_d(double x) {
   return (static_cast<unsigned>(__double2hiint(x)) & 0x7ff00000u) != 0x7ff00000u;
 }
 __device__ __forceinline__ bool positive_d(double x) { return __double_as_longlong(x) > 0 && finite_d(x); }
+__device__ __forceinline__ bool finite_f(float x) { return (__float_as_uint(x) & 0x7f800000u) != 0x7f800000u; }
+
+// Primitives of U + dU from the primitives W of U (FP32 throughout).  The
+// increments of the kinetic and magnetic energies are formed from dU itself,
+// so the pressure carries no cancellation however small it is against the
+// energy:  rho' = rho + drho,  u' = u + (dm - u drho) / rho',  B' = B + dB,
+//   p' = p + (gamma - 1) [de - dK - (B.dB + |dB|^2 / 2)],
+//   dK = (2 rho u.dm - rho drho |u|^2 + |dm|^2) / (2 rho')
+// (dK is the change of |m|^2 / (2 rho) for m = rho u).
+__device__ __forceinline__ void prim_increment(const float W[8], const float dU[8], float gm1f, float Wn[8]) {
+  const float rc = W[0], u0 = W[1], u1 = W[2], u2 = W[3];
+  const float rf = rc + dU[0];
+  const float irf = rcp_approx(rf);
+  const float udm = u0 * dU[1] + u1 * dU[2] + u2 * dU[3];
+  const float usq = u0 * u0 + u1 * u1 + u2 * u2;
+  const float dmsq = dU[1] * dU[1] + dU[2] * dU[2] + dU[3] * dU[3];
+  const float dK = 0.5f * ((2.f * rc * udm - rc * dU[0] * usq) + dmsq) * irf;
+  const float dM = (W[4] * dU[4] + W[5] * dU[5] + W[6] * dU[6]) + 0.5f * (dU[4] * dU[4] + dU[5] * dU[5] + dU[6] * dU[6]);
+  Wn[0] = rf;
+  Wn[1] = u0 + (dU[1] - u0 * dU[0]) * irf;
+  Wn[2] = u1 + (dU[2] - u1 * dU[0]) * irf;
+  Wn[3] = u2 + (dU[3] - u2 * dU[0]) * irf;
+  Wn[4] = W[4] + dU[4];
+  Wn[5] = W[5] + dU[5];
+  Wn[6] = W[6] + dU[6];
+  Wn[7] = W[7] + gm1f * ((dU[7] - dK) - dM);
+}
 
 // ---------------------------------------------------------------------------
 // Ghost fill by point location (copy / restriction / prolongation / boundary).
@@ -692,11 +719,8 @@ __device__ __forceinline__ bool psample(const BlockDev& B, int s, int k, int gc[
 // Fine ghost cell `local` (0..127, as in the face slab) of COARSER face s
 // from the sample table: the coarse value plus (+-1/4) x minmod of the
 // undivided coarse differences of the conservative variables (x, then y,
-// then z), turned into primitives through the increments of the coarse
-// cell's own primitives.  With dU the increment: rho = rho_c + drho,
-// u = u_c + (dm - u_c drho) / rho, B = B_c + dB and
-// p = p_c + (gamma - 1) [de - dK - (B_c.dB + |dB|^2 / 2)],
-// dK = (2 rho_c u_c.dm - rho_c drho |u_c|^2 + |dm|^2) / (2 rho).
+// then z), turned into primitives from the coarse cell's own primitives and
+// the increment (prim_increment).
 __device__ __forceinline__ void prolong_child_w(const float* tab, int s, int local, float gm1f, float w[8]) {
   const int d = s >> 1, side = s & 1;
   const int ta = d == 0 ? 1 : 0;
@@ -730,24 +754,8 @@ __device__ __forceinline__ void prolong_child_w(const float* tab, int s, int loc
 #pragma unroll
     for (int v = 0; v < NV; v++) dl[v] = dl[v] + sg * minmod_<float>(Uc[v] - Um[v], Up[v] - Uc[v]);
   }
-  const float rc = Uc[0], pc = Uc[8];
-  const float uc0 = Uc[9], uc1 = Uc[10], uc2 = Uc[11];
-  const float rf = rc + dl[0];
-  const float irf = rcp_approx(rf);
-  const float udm = uc0 * dl[1] + uc1 * dl[2] + uc2 * dl[3];
-  const float usq = uc0 * uc0 + uc1 * uc1 + uc2 * uc2;
-  const float dmsq = dl[1] * dl[1] + dl[2] * dl[2] + dl[3] * dl[3];
-  const float dK = 0.5f * ((2.f * rc * udm - rc * dl[0] * usq) + dmsq) * irf;
-  const float dM = (Uc[4] * dl[4] + Uc[5] * dl[5] + Uc[6] * dl[6]) +
-                   0.5f * (dl[4] * dl[4] + dl[5] * dl[5] + dl[6] * dl[6]);
-  w[0] = rf;
-  w[1] = uc0 + (dl[1] - uc0 * dl[0]) * irf;
-  w[2] = uc1 + (dl[2] - uc1 * dl[0]) * irf;
-  w[3] = uc2 + (dl[3] - uc2 * dl[0]) * irf;
-  w[4] = Uc[4] + dl[4];
-  w[5] = Uc[5] + dl[5];
-  w[6] = Uc[6] + dl[6];
-  w[7] = pc + gm1f * ((dl[7] - dK) - dM);
+  const float Wc[8] = {Uc[0], Uc[9], Uc[10], Uc[11], Uc[4], Uc[5], Uc[6], Uc[8]};
+  prim_increment(Wc, dl, gm1f, w);
 }
 
 // Tile index of cell c (-2..9) along direction d at transverse (a, b).
@@ -1011,7 +1019,8 @@ __global__ void __launch_bounds__(STAGE_THREADS, MIXED ? 2 : 1) k_stage(const St
         for (int v = 0; v < NV; v++) bulk_g2s(sT + v * NTILE, src + v * NCELL, NCELL * sizeof(R), &bar);
         // the FP64 states the cell phase reads, on their way to L2 meanwhile
         const int64_t boff = static_cast<int64_t>(blk) * (NV * NCELL);
-        if (a.kind < 3) prefetch_l2(a.Ubase + boff, NV * NCELL * sizeof(double));
+        const bool reads_ubase = a.kind < 3 && !(MIXED && a.kind == 0 && !a.last && !a.write_u_all);
+        if (reads_ubase) prefetch_l2(a.Ubase + boff, NV * NCELL * sizeof(double));
         if (MIXED && a.kind == 1) prefetch_l2(a.Uin + boff, NV * NCELL * sizeof(double));
       }
       if constexpr (MIXED) fill_ghosts_block_mixed(a, cx, B, blk, sT, sF, tid, STAGE_THREADS);
@@ -1181,6 +1190,12 @@ __global__ void __launch_bounds__(STAGE_THREADS, MIXED ? 2 : 1) k_stage(const St
       auto cells = [&](const bool commit) -> bool {
         bool any_bad = false;
         R smax_loc = R(0);
+        const double cdt = a.beta * a.dt[B.grid];
+        // mixed form, first stage of the midpoint scheme: U* only feeds the
+        // second stage's FP32 primitives, so W* = W^n + the increment, in FP32
+        // (the FP64 state is read and accumulated in the last stage only)
+        const bool light = MIXED && a.kind == 0 && !a.last && !a.write_u_all;
+        const float c32 = d2f_int(cdt);
         for (int c = tid; c < NCELL; c += STAGE_THREADS) {
           const int ci = c & 7, cj = (c >> 3) & 7, ck = c >> 6;
           // face indices (line * 9 + position) of the low faces in x, y, z
@@ -1242,8 +1257,30 @@ __global__ void __launch_bounds__(STAGE_THREADS, MIXED ? 2 : 1) k_stage(const St
             S[2] = (S[2] - b1y * divb0) + (b1z * cu0 - b1x * cu2);
             S[3] = (S[3] - b1z * divb0) + (b1x * cu1 - b1y * cu0);
           }
-          const double cdt = a.beta * a.dt[B.grid];
           const int64_t base = static_cast<int64_t>(blk) * (NV * NCELL) + c;
+          if constexpr (MIXED) {
+            if (light) {
+              float dU[8], Wl[8];
+#pragma unroll
+              for (int v = 0; v < NV; v++) dU[v] = c32 * (res[v] + S[v]);
+              prim_increment(Wc, dU, ph.gm1f, Wl);
+              if (in_body) prim_mixed(G.Ubody, ph.gm1f, Wl);
+              bool badl = !(Wl[0] > 0.f) || !(Wl[7] > 0.f);
+#pragma unroll
+              for (int v = 0; v < NV; v++) badl |= !finite_f(Wl[v]);
+              if (badl && !in_body) {
+                any_bad = true;
+                if (commit) {
+                  atomicOr(&a.err[0], ERR_NONPHYSICAL);
+                  atomicMin(&a.err[1], blk);
+                }
+              }
+              if (!commit) continue;
+#pragma unroll
+              for (int v = 0; v < NV; v++) a.Wout[base + v * NCELL] = Wl[v];
+              continue;
+            }
+          }
           double Uo[8];
           bool bad = false;
 #pragma unroll
@@ -1257,10 +1294,14 @@ __global__ void __launch_bounds__(STAGE_THREADS, MIXED ? 2 : 1) k_stage(const St
             if (a.kind == 0) o = fma(cdt, rd, ub);
             else o = 0.5 * ub + 0.5 * fma(cdt, rd, a.Uin[base + v * NCELL]);
             if (a.kind == 2) o = rd;  // residual only (debug view)
-            o = in_body ? (a.kind == 2 ? 0.0 : G.Ubody[v]) : o;
             Uo[v] = o;
-            bad |= !finite_d(o);
           }
+          if (in_body) {  // a branch, not a select: no loads of the body state elsewhere
+#pragma unroll
+            for (int v = 0; v < NV; v++) Uo[v] = a.kind == 2 ? 0.0 : G.Ubody[v];
+          }
+#pragma unroll
+          for (int v = 0; v < NV; v++) bad |= !finite_d(Uo[v]);
           if (a.kind != 2) bad |= !positive_d(Uo[0]);
           R Wn[8];
           const bool need_w = MIXED || a.last || !commit;
