@@ -42,7 +42,8 @@ BYTES_PER_CELL_UPDATE = 320  # FP64 state: stage 1 reads U^n, writes U*; stage 2
 # DRAM traffic of one k_stage launch per cell, from the ncu capture summarised
 # in profiles/ (None until a capture of the current kernel source exists).
 NCU_TRAFFIC = {
-    # precision: (bytes per cell per launch, sha256 of bats_stage.cu at capture)
+    # precision: (DRAM bytes per cell per launch, mean of the two stages, sha256 of bats_stage.cu at capture)
+    "mixed": (116.9, "1c4ab7d28e40f6eaebcc3e2793ddcb062c2415151b1078e8fa4d99ac73fc7cad"),
 }
 
 

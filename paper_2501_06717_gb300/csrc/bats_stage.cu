@@ -1069,7 +1069,7 @@ __global__ void __launch_bounds__(STAGE_THREADS, MIXED ? 2 : 1) k_stage(const St
           load_rot<R>(sT, rot, cidx(f0), W0);
 #pragma unroll
           for (int v = 0; v < NV; v++) sm1[v] = limit_<R>(LIM, Wm1[v] - Wm2[v], W0[v] - Wm1[v]);
-  #pragma unroll 1
+#pragma unroll 1
           for (int k = 0; k < nf; k++) {
             const int f = f0 + k;
             R Wp[8], WL[8], WR[8], s0[8];
