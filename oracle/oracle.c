@@ -52,8 +52,8 @@
 #define MAXLEV 14
 
 enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_INFLOW = 2 };
-enum { LIM_MINMOD = 0, LIM_MC = 1 };
-enum { RK_MIDPOINT = 0, RK_SSP2 = 1 };
+enum { LIM_MINMOD = 0, LIM_MC = 1, LIM_NONE = 2 };
+enum { RK_MIDPOINT = 0, RK_SSP2 = 1, RK_EULER = 2 };
 enum { B0_NONE = 0, B0_UNIFORM = 1, B0_DIPOLE = 2, B0_LINEAR = 3 };
 enum { OR_OK = 0, OR_EINVAL = -1, OR_EUNBALANCED = -2, OR_ENOMEM = -3 };
 enum { GT_INTERIOR = 0, GT_COPY = 1, GT_RESTRICT = 2, GT_PROLONG = 3, GT_INFLOW = 4 };
@@ -79,6 +79,8 @@ typedef struct {
   int32_t learned;       /* 1 = add the MLP flux correction */
   int32_t no_fallback;   /* test switch: 1 keeps a learned block update even where it is non-physical */
   const double* mlp;     /* MLP_NPARAM weights (W1,b1,W2,b2,W3,b3), row-major [out][in] */
+  int32_t local_dt;      /* 1 = local time stepping: each cell its own dt (steady-state runs) */
+  int32_t pad2_;
 } or_desc;
 
 typedef struct {
@@ -359,6 +361,7 @@ static int grid_init(grid_t* G, const or_desc* d, double dummy_unused) {
 /* Fluxes.                                                                   */
 
 static double limiter(int kind, double a, double b) {
+  if (kind == LIM_NONE) return 0.0; /* first order: piecewise-constant faces */
   if (kind == LIM_MC) {
     /* monotonised central, beta = 2: sign(a) min(2|a|, 2|b|, |a+b|/2) */
     if (a > 0.0 && b > 0.0) {
@@ -873,7 +876,7 @@ int or_residual(const or_desc* d, const double* Uin, double* R) {
  * [8][512].  Returns 1 when every non-body cell of the result is physical:
  * all 8 values finite, rho > 0 and p > 0 (p from Eq. 5). */
 static int block_update(grid_t* G, int b, const double* Rb, const double* Uin, const double* Ubase, int kind,
-                        double c, double* Ob) {
+                        double c, const double* dtc, double* Ob) {
   const or_desc* d = G->d;
   const int32_t* L = d->leaves + 4 * b;
   int nb = G->nb, ok = 1;
@@ -887,10 +890,11 @@ static int block_update(grid_t* G, int b, const double* Rb, const double* Uin, c
         for (int v = 0; v < NV; v++) {
           long gidx = ((long)v * nb + b) * NCELL + cidx;
           double r = Rb[v * NCELL + cidx];
+          double cc = dtc ? c * dtc[(long)b * NCELL + cidx] : c;
           double o;
           if (body) o = G->Ubody[v];
-          else if (kind == 0) o = Ubase[gidx] + c * r;
-          else o = 0.5 * Ubase[gidx] + 0.5 * (Uin[gidx] + c * r);
+          else if (kind == 0) o = Ubase[gidx] + cc * r;
+          else o = 0.5 * Ubase[gidx] + 0.5 * (Uin[gidx] + cc * r);
           Ob[v * NCELL + cidx] = o;
           Uc[v] = o;
         }
@@ -903,12 +907,13 @@ static int block_update(grid_t* G, int b, const double* Rb, const double* Uin, c
   return ok;
 }
 
-/* One stage (kinds as in block_update).  With the learned correction, a block
- * whose learned update leaves a non-physical cell is recomputed with the plain
- * Rusanov flux (the fallback of the learned form); fb (nullable, one flag per
- * block) records which blocks fell back. */
+/* One stage (kinds as in block_update).  dtc (nullable, [nb][512]): local
+ * time stepping, the coefficient of cell i is c * dtc[i] instead of c.  With
+ * the learned correction, a block whose learned update leaves a non-physical
+ * cell is recomputed with the plain Rusanov flux (the fallback of the learned
+ * form); fb (nullable, one flag per block) records which blocks fell back. */
 int or_stage_ex(const or_desc* d, const double* Uin, const double* Ubase, double* Uout, int kind, double c,
-                int32_t* fb) {
+                const double* dtc, int32_t* fb) {
   grid_t G;
   int rc = grid_init(&G, d, 0.0);
   if (rc) return rc;
@@ -921,12 +926,12 @@ int or_stage_ex(const or_desc* d, const double* Uin, const double* Ubase, double
     grid_t Gl = G;
     double Rb[NV * NCELL], Ob[NV * NCELL];
     block_residual(&Gl, b, Rb);
-    int ok = block_update(&Gl, b, Rb, Uin, Ubase, kind, c, Ob);
+    int ok = block_update(&Gl, b, Rb, Uin, Ubase, kind, c, dtc, Ob);
     int fell_back = 0;
     if (!ok && d->learned && d->mlp && !d->no_fallback) {
       Gl.d = &plain;
       block_residual(&Gl, b, Rb);
-      block_update(&Gl, b, Rb, Uin, Ubase, kind, c, Ob);
+      block_update(&Gl, b, Rb, Uin, Ubase, kind, c, dtc, Ob);
       fell_back = 1;
     }
     if (fb) fb[b] = fell_back;
@@ -937,7 +942,7 @@ int or_stage_ex(const or_desc* d, const double* Uin, const double* Ubase, double
 }
 
 int or_stage(const or_desc* d, const double* Uin, const double* Ubase, double* Uout, int kind, double c) {
-  return or_stage_ex(d, Uin, Ubase, Uout, kind, c, NULL);
+  return or_stage_ex(d, Uin, Ubase, Uout, kind, c, NULL, NULL);
 }
 
 /* Largest sum_d (|u_d| + cf_d) / dx_d over non-body cells; dt = cfl / smax. */
@@ -970,8 +975,41 @@ int or_cfl_smax(const or_desc* d, const double* U, double* smax_out) {
   return OR_OK;
 }
 
-/* n full steps of the two-stage scheme.  cfl > 0: dt = cfl / smax(U^n) each
- * step; cfl <= 0: dt = fixed_dt.  Returns the last dt, the elapsed time and
+/* Local time step of every cell (steady-state runs): dt_i = cfl / s_i with
+ * s_i = sum_d (|u_d| + cf_d) / dx_d of the cell, the bound whose global
+ * maximum gives the time-accurate dt; body cells get 0.  dtc is [nb][512]. */
+int or_local_dt(const or_desc* d, const double* U, double cfl, double* dtc) {
+  grid_t G;
+  int rc = grid_init(&G, d, 0.0);
+  if (rc) return rc;
+  int nb = G.nb;
+#pragma omp parallel for schedule(static)
+  for (int b = 0; b < nb; b++) {
+    const int32_t* L = d->leaves + 4 * b;
+    int lev = L[0];
+    for (int c = 0; c < NCELL; c++) {
+      int i = c % NC, j = (c / NC) % NC, k = c / (NC * NC);
+      double xc[3], B0c[3], Uc[NV], W[NV];
+      cell_centre(&G, lev, L, i, j, k, xc);
+      if (in_body(d, xc)) { dtc[(long)b * NCELL + c] = 0.0; continue; }
+      for (int v = 0; v < NV; v++) Uc[v] = U[((long)v * nb + b) * NCELL + c];
+      prim_from_cons(d->gamma, Uc, W);
+      b0_at(d, xc, B0c);
+      double B[3] = {B0c[0] + W[4], B0c[1] + W[5], B0c[2] + W[6]};
+      double s = 0.0;
+      for (int a = 0; a < 3; a++) s = s + (fabs(W[1 + a]) + fast_speed(d->gamma, W, B, a)) / G.dx[lev][a];
+      dtc[(long)b * NCELL + c] = cfl / s;
+    }
+  }
+  grid_free(&G);
+  return OR_OK;
+}
+
+/* n full steps.  Two stages (midpoint or SSP-RK2) or one (forward Euler,
+ * RK_EULER).  cfl > 0: dt = cfl / smax(U^n) each step; cfl <= 0: dt =
+ * fixed_dt.  With local time stepping (and cfl > 0) every cell takes its own
+ * dt_i from U^n (or_local_dt) in every stage of the step, and the elapsed
+ * time advances by the global dt.  Returns the last dt, the elapsed time and
  * (nullable) the number of block-stages that fell back to the plain flux. */
 int or_run_ex(const or_desc* d, double* U, int nsteps, double cfl, double fixed_dt, double* dt_last,
               double* t_total, long* n_fallback) {
@@ -984,7 +1022,9 @@ int or_run_ex(const or_desc* d, double* U, int nsteps, double cfl, double fixed_
   double* U1 = (double*)malloc(sizeof(double) * n);
   double* U2 = (double*)malloc(sizeof(double) * n);
   int32_t* fb = (int32_t*)malloc(sizeof(int32_t) * nb);
-  if (!U1 || !U2 || !fb) { free(U1); free(U2); free(fb); return OR_ENOMEM; }
+  const int lts = d->local_dt && cfl > 0.0;
+  double* dtc = lts ? (double*)malloc(sizeof(double) * (size_t)nb * NCELL) : NULL;
+  if (!U1 || !U2 || !fb || (lts && !dtc)) { free(U1); free(U2); free(fb); free(dtc); return OR_ENOMEM; }
   double t = 0.0, dt = fixed_dt;
   long nfb = 0;
   for (int s = 0; s < nsteps; s++) {
@@ -993,10 +1033,17 @@ int or_run_ex(const or_desc* d, double* U, int nsteps, double cfl, double fixed_
       rc = or_cfl_smax(d, U, &smax);
       if (rc) break;
       dt = cfl / smax;
+      if (lts) rc = or_local_dt(d, U, cfl, dtc);
+      if (rc) break;
     }
-    for (int st = 0; st < 2 && !rc; st++) {
-      if (d->rk == RK_SSP2) rc = st == 0 ? or_stage_ex(d, U, U, U1, 0, dt, fb) : or_stage_ex(d, U1, U, U2, 1, dt, fb);
-      else rc = st == 0 ? or_stage_ex(d, U, U, U1, 0, 0.5 * dt, fb) : or_stage_ex(d, U1, U, U2, 0, dt, fb);
+    /* with local time stepping the stage coefficients are beta * dt_i */
+    const double f = lts ? 1.0 : dt;
+    const int nst = d->rk == RK_EULER ? 1 : 2;
+    for (int st = 0; st < nst && !rc; st++) {
+      if (d->rk == RK_EULER) rc = or_stage_ex(d, U, U, U2, 0, f, dtc, fb);
+      else if (d->rk == RK_SSP2)
+        rc = st == 0 ? or_stage_ex(d, U, U, U1, 0, f, dtc, fb) : or_stage_ex(d, U1, U, U2, 1, f, dtc, fb);
+      else rc = st == 0 ? or_stage_ex(d, U, U, U1, 0, 0.5 * f, dtc, fb) : or_stage_ex(d, U1, U, U2, 0, f, dtc, fb);
       for (int b = 0; b < nb && !rc; b++) nfb += fb[b];
     }
     if (rc) break;
@@ -1006,6 +1053,7 @@ int or_run_ex(const or_desc* d, double* U, int nsteps, double cfl, double fixed_
   free(U1);
   free(U2);
   free(fb);
+  free(dtc);
   if (dt_last) *dt_last = dt;
   if (t_total) *t_total = t;
   if (n_fallback) *n_fallback = nfb;

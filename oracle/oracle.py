@@ -62,6 +62,8 @@ class _Desc(ctypes.Structure):
         ("learned", ctypes.c_int32),
         ("no_fallback", ctypes.c_int32),
         ("mlp", ctypes.POINTER(ctypes.c_double)),
+        ("local_dt", ctypes.c_int32),
+        ("pad2_", ctypes.c_int32),
     ]
 
 
@@ -81,7 +83,8 @@ def lib():
         _lib.or_ghost_info.argtypes = [D, ctypes.c_int, ip, ip]
         _lib.or_residual.argtypes = [D, dp, dp]
         _lib.or_stage.argtypes = [D, dp, dp, dp, ctypes.c_int, ctypes.c_double]
-        _lib.or_stage_ex.argtypes = [D, dp, dp, dp, ctypes.c_int, ctypes.c_double, ip]
+        _lib.or_stage_ex.argtypes = [D, dp, dp, dp, ctypes.c_int, ctypes.c_double, dp, ip]
+        _lib.or_local_dt.argtypes = [D, dp, ctypes.c_double, dp]
         _lib.or_cfl_smax.argtypes = [D, dp, dp]
         _lib.or_run.argtypes = [D, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, dp]
         _lib.or_run_ex.argtypes = [D, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, dp, lp]
@@ -142,6 +145,7 @@ class _Bound:
         else:
             d.learned = 0
         d.no_fallback = int(getattr(prob, "no_fallback", 0) or 0)
+        d.local_dt = int(getattr(prob, "local_dt", 0) or 0)
         self.desc = d
         self.nb = d.n_leaves
 
@@ -194,17 +198,31 @@ def residual(prob, U):
     return R.reshape(8, b.nb, 8, 8, 8)
 
 
-def stage(prob, Uin, Ubase, kind, c, with_fallback_flags=False):
-    """One stage; with_fallback_flags also returns, per block, 1 where the
-    learned update was replaced by the plain one."""
+def stage(prob, Uin, Ubase, kind, c, with_fallback_flags=False, dtc=None):
+    """One stage; dtc (per cell, [nb][512]) makes the coefficient of cell i
+    c * dtc[i] (local time stepping).  with_fallback_flags also returns, per
+    block, 1 where the learned update was replaced by the plain one."""
     b = _Bound(prob)
     Uin = _state(prob, Uin, b.nb)
     Ubase = _state(prob, Ubase, b.nb)
     Uout = np.zeros_like(Uin)
     fb = np.zeros(b.nb, dtype=np.int32)
-    _check(lib().or_stage_ex(b.ref(), _dp(Uin), _dp(Ubase), _dp(Uout), int(kind), float(c), _ip(fb)), "stage")
+    dp_ = None
+    if dtc is not None:
+        dtc = np.ascontiguousarray(dtc, dtype=np.float64).reshape(b.nb * 512)
+        dp_ = _dp(dtc)
+    _check(lib().or_stage_ex(b.ref(), _dp(Uin), _dp(Ubase), _dp(Uout), int(kind), float(c), dp_, _ip(fb)), "stage")
     Uout = Uout.reshape(8, b.nb, 8, 8, 8)
     return (Uout, fb) if with_fallback_flags else Uout
+
+
+def local_dt(prob, U, cfl):
+    """Per-cell time steps dt_i = cfl / s_i, [nb][512] (0 in body cells)."""
+    b = _Bound(prob)
+    U = _state(prob, U, b.nb)
+    out = np.zeros(b.nb * 512)
+    _check(lib().or_local_dt(b.ref(), _dp(U), float(cfl), _dp(out)), "local_dt")
+    return out.reshape(b.nb, 512)
 
 
 def cfl_smax(prob, U):

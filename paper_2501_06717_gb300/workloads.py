@@ -31,8 +31,8 @@ import math
 import numpy as np
 
 BC_PERIODIC, BC_OUTFLOW, BC_INFLOW = 0, 1, 2
-LIM_MINMOD, LIM_MC = 0, 1
-RK_MIDPOINT, RK_SSP2 = 0, 1
+LIM_MINMOD, LIM_MC, LIM_NONE = 0, 1, 2
+RK_MIDPOINT, RK_SSP2, RK_EULER = 0, 1, 2
 B0_NONE, B0_UNIFORM, B0_DIPOLE, B0_LINEAR = 0, 1, 2, 3
 
 NC = 8  # cells per block per axis
@@ -60,6 +60,7 @@ class Problem:
     U0: np.ndarray = None       # [8][nb][8][8][8]
     learned: int = 0
     mlp: np.ndarray = None
+    local_dt: int = 0
 
     @property
     def nb(self):
