@@ -46,8 +46,8 @@ extern "C" {
 
 /* ---- enumerations ------------------------------------------------------ */
 enum { BATS_BC_PERIODIC = 0, BATS_BC_OUTFLOW = 1, BATS_BC_INFLOW = 2 };
-enum { BATS_LIM_MINMOD = 0, BATS_LIM_MC = 1 };
-enum { BATS_RK_MIDPOINT = 0, BATS_RK_SSP2 = 1 };
+enum { BATS_LIM_MINMOD = 0, BATS_LIM_MC = 1, BATS_LIM_NONE = 2 };
+enum { BATS_RK_MIDPOINT = 0, BATS_RK_SSP2 = 1, BATS_RK_EULER = 2 };
 enum { BATS_FP64 = 0, BATS_MIXED = 1 };
 enum { BATS_B0_NONE = 0, BATS_B0_UNIFORM = 1, BATS_B0_DIPOLE = 2, BATS_B0_LINEAR = 3 };
 enum { BATS_PHASE_STAGE = 0, BATS_PHASE_DT = 1, BATS_PHASE_TOTAL = 2, BATS_NUM_PHASES = 3 };
@@ -80,8 +80,10 @@ typedef struct {
 /* Physics and launch form, shared by all grids of a handle.
  *  gamma          ratio of specific heats (Eq. 5)
  *  limiter        BATS_LIM_MINMOD or BATS_LIM_MC (limited linear reconstruction
- *                 of primitives, Algorithm 1 "calc_face_value")
- *  rk             BATS_RK_MIDPOINT (default) or BATS_RK_SSP2
+ *                 of primitives, Algorithm 1 "calc_face_value"), or BATS_LIM_NONE
+ *                 (first order: face values are the cell values)
+ *  rk             BATS_RK_MIDPOINT (default), BATS_RK_SSP2, or BATS_RK_EULER (the
+ *                 one-stage scheme of Section 5.2's time-accurate session)
  *  precision      BATS_FP64: every step in FP64.  BATS_MIXED: reconstruction,
  *                 fluxes and sources in FP32; pressure recovery and the state
  *                 accumulation in FP64.
@@ -92,14 +94,21 @@ typedef struct {
  *  learned        1 = add the MLP flux correction (needs bats_set_mlp)
  *  persistent     1 = one persistent launch per stage (grid = SMs x occupancy)
  *  blocks_per_cta blocks processed per work item in the persistent launch (>= 1)
- *  ctas_per_sm    persistent CTAs per SM (0 = the occupancy limit) */
+ *  ctas_per_sm    persistent CTAs per SM (0 = the occupancy limit)
+ *  use_graph      1 = replay whole bats_step calls from a CUDA graph
+ *  local_dt       1 = local time stepping (Section 5.2's steady-state session):
+ *                 with a CFL number, every cell advances with its own
+ *                 dt_i = cfl / sum_d (|u_d| + c_f,d) / dx_d of the step's initial
+ *                 state, in every stage; the elapsed time advances by the global
+ *                 dt.  Ignored by bats_step_dt (fixed dt). */
 typedef struct {
   double gamma;
   int32_t limiter, rk, precision, b0;
   double b0_param[12];
   int32_t powell, learned, persistent, blocks_per_cta;
   int32_t ctas_per_sm, use_graph;
-  int32_t reserved[2];
+  int32_t local_dt;
+  int32_t reserved;
 } bats_physics;
 
 /* Create a solver for n_grids independent grids advanced together (batched

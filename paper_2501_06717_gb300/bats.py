@@ -23,8 +23,8 @@ BATS_ERR_TIMEOUT = -6
 BATS_ERR_NOT_TRAINED = -7
 
 BATS_BC_PERIODIC, BATS_BC_OUTFLOW, BATS_BC_INFLOW = 0, 1, 2
-BATS_LIM_MINMOD, BATS_LIM_MC = 0, 1
-BATS_RK_MIDPOINT, BATS_RK_SSP2 = 0, 1
+BATS_LIM_MINMOD, BATS_LIM_MC, BATS_LIM_NONE = 0, 1, 2
+BATS_RK_MIDPOINT, BATS_RK_SSP2, BATS_RK_EULER = 0, 1, 2
 BATS_FP64, BATS_MIXED = 0, 1
 BATS_B0_NONE, BATS_B0_UNIFORM, BATS_B0_DIPOLE, BATS_B0_LINEAR = 0, 1, 2, 3
 BATS_PHASE_STAGE, BATS_PHASE_DT, BATS_PHASE_TOTAL, BATS_NUM_PHASES = 0, 1, 2, 3
@@ -58,7 +58,8 @@ class bats_physics(ctypes.Structure):
         ("blocks_per_cta", ctypes.c_int32),
         ("ctas_per_sm", ctypes.c_int32),
         ("use_graph", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 2),
+        ("local_dt", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -173,6 +174,7 @@ def physics_from(problem, precision=BATS_FP64, persistent=0, blocks_per_cta=1, c
     ph.blocks_per_cta = int(blocks_per_cta)
     ph.ctas_per_sm = int(ctas_per_sm)
     ph.use_graph = int(use_graph)
+    ph.local_dt = int(getattr(problem, "local_dt", 0) or 0)
     return ph
 
 

@@ -29,6 +29,9 @@ cudaError_t launch_init_grid_states(GridDev* grids, int ngrids, double inv_gm1, 
 cudaError_t launch_prim_mixed(const double* U, float* Wt, int b0, int nb, float gm1f, cudaStream_t st);
 cudaError_t launch_cfl(bool mixed, const double* U, const float* Wt, const GridDev* grids, const BlockDev* blocks,
                        const PhysDev& ph, int b0, int nb, unsigned long long* smax, cudaStream_t st);
+cudaError_t launch_cfl_dt(bool mixed, const double* U, const float* Wt, const GridDev* grids,
+                          const BlockDev* blocks, const PhysDev& ph, int b0, int nb, unsigned long long* smax,
+                          double* dtc, double cfl, cudaStream_t st);
 cudaError_t launch_dt(int ngrids, int mode, double cfl, double fixed_dt, double* dt, double* t,
                       unsigned long long* smax, unsigned long long* smax_next, cudaStream_t st);
 cudaError_t launch_debug_fill(const StageArgs& a, int b0, int nb, double* T, cudaStream_t st);
@@ -63,6 +66,8 @@ struct bats {
   double* staging = nullptr;
   size_t staging_n = 0;
   int persistent = 0, bpc = 1, ctas_per_sm = 0, use_graph = 0;
+  int local_dt = 0;
+  double* dtc = nullptr;  // local time stepping: per-cell dt [nbt][512]
   int occ[2] = {1, 1};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<cudaEvent_t> stage_ev;   // pairs around the two stage launches of each step
@@ -73,6 +78,7 @@ struct bats {
   cudaGraphExec_t graph = nullptr;
   int graph_n = -1;
   double graph_cfl = 0, graph_dt = 0;
+  long long graph_launches = 0;
   // learned form
   bool learned_requested = false, learned = false;
   MlpDev mlp{};
@@ -313,6 +319,7 @@ void free_all(bats_t* h) {
   cudaFree(h->U1);
   cudaFree(h->W);
   cudaFree(h->W1);
+  cudaFree(h->dtc);
   cudaFree(h->dt);
   cudaFree(h->t);
   cudaFree(h->smax);
@@ -383,12 +390,14 @@ int launch_stage(bats_t* h, const StageArgs& a) {
   return launch_stage_one(h, u);
 }
 
-int launch_cfl(bats_t* h, int g) {
+// CFL bound of grid g's current state into smax[g]; with dtc, also every
+// cell's local dt = cfl / s_i.
+int launch_cfl(bats_t* h, int g, double* dtc = nullptr, double cfl = 0.0) {
   const GridDev& G = h->grids_h[g];
   CK(h, cudaMemsetAsync(h->smax + g, 0, sizeof(unsigned long long), h->stream));
   h->launches++;
-  CK(h, launch_cfl(h->ph.precision == BATS_MIXED, h->U, h->W, h->grids_d, h->blocks_d, h->ph, G.block0, G.nb,
-                   h->smax, h->stream));
+  CK(h, launch_cfl_dt(h->ph.precision == BATS_MIXED, h->U, h->W, h->grids_d, h->blocks_d, h->ph, G.block0, G.nb,
+                      h->smax, dtc, cfl, h->stream));
   return BATS_OK;
 }
 
@@ -404,49 +413,89 @@ int ensure_stage_events(bats_t* h, int n) {
   return BATS_OK;
 }
 
-// Enqueue n steps (no synchronisation).  The two stage launches of each of
-// the first kMaxTimedSteps steps are bracketed by an event pair.
+// Enqueue n steps (no synchronisation).  The stage launches of each of the
+// first kMaxTimedSteps steps are bracketed by an event pair.
 int enqueue_steps(bats_t* h, int n, double cfl, double fixed_dt, bool timed) {
   const bool mixed = h->ph.precision == BATS_MIXED;
   const bool ssp = h->ph.rk == BATS_RK_SSP2;
+  const bool euler = h->ph.rk == BATS_RK_EULER;
+  const bool lts = h->local_dt && cfl > 0.0;
   if (timed) {
     int rc0 = ensure_stage_events(h, n);
     if (rc0) return rc0;
   }
   h->timed_steps = timed ? std::min(n, kMaxTimedSteps) : 0;
   const int ntimed = h->timed_steps;
+  if (lts && n > 0) {
+    // every cell's dt from the current state (later steps take it from the
+    // last stage of the step before)
+    for (int g = 0; g < h->ngrids; g++) {
+      int rc = launch_cfl(h, g, h->dtc, cfl);
+      if (rc) return rc;
+    }
+  }
+  // the one-stage scheme cannot write in place (other blocks read this
+  // block's cells as ghosts): it alternates between the two state buffers
+  double* Ucur = h->U;
+  double* Uoth = h->U1;
+  float* Wcur = h->W;
+  float* Woth = h->W1;
   for (int s = 0; s < n; s++) {
     CK(h, launch_dt(h->ngrids, 0, cfl, fixed_dt, h->dt, h->t, h->smax, h->smax_next, h->stream));
     h->launches++;
     if (s < ntimed) CK(h, cudaEventRecord(h->stage_ev[2 * s], h->stream));
     StageArgs a = base_args(h);
-    // stage 1: U* = U^n + (dt/2) R(U^n)   [SSP-RK2: U^n + dt R(U^n)]
-    a.Uin = h->U;
-    a.Ubase = h->U;
-    a.Uout = h->U1;
-    a.Win = h->W;
-    a.Wout = h->W1;
-    a.kind = 0;
-    a.last = 0;
-    a.beta = ssp ? 1.0 : 0.5;
-    a.write_u_all = (!mixed || ssp) ? 1 : 0;
-    int rc = launch_stage(h, a);
-    if (rc) return rc;
-    // stage 2: U^{n+1} = U^n + dt R(U*)   [SSP-RK2: U^n/2 + (U* + dt R(U*))/2]
-    a.Uin = h->U1;
-    a.Ubase = h->U;
-    a.Uout = h->U;
-    a.Win = h->W1;
-    a.Wout = h->W;
-    a.kind = ssp ? 1 : 0;
-    a.last = 1;
-    a.beta = 1.0;
-    a.write_u_all = 1;
-    rc = launch_stage(h, a);
-    if (rc) return rc;
+    a.dtc = lts ? h->dtc : nullptr;
+    a.cfl = cfl;
+    if (euler) {
+      // U^{n+1} = U^n + dt R(U^n)
+      a.Uin = Ucur;
+      a.Ubase = Ucur;
+      a.Uout = Uoth;
+      a.Win = Wcur;
+      a.Wout = Woth;
+      a.kind = 0;
+      a.last = 1;
+      a.beta = 1.0;
+      a.write_u_all = 1;
+      int rc = launch_stage(h, a);
+      if (rc) return rc;
+      std::swap(Ucur, Uoth);
+      std::swap(Wcur, Woth);
+    } else {
+      // stage 1: U* = U^n + (dt/2) R(U^n)   [SSP-RK2: U^n + dt R(U^n)]
+      a.Uin = h->U;
+      a.Ubase = h->U;
+      a.Uout = h->U1;
+      a.Win = h->W;
+      a.Wout = h->W1;
+      a.kind = 0;
+      a.last = 0;
+      a.beta = ssp ? 1.0 : 0.5;
+      a.write_u_all = (!mixed || ssp) ? 1 : 0;
+      int rc = launch_stage(h, a);
+      if (rc) return rc;
+      // stage 2: U^{n+1} = U^n + dt R(U*)   [SSP-RK2: U^n/2 + (U* + dt R(U*))/2]
+      a.Uin = h->U1;
+      a.Ubase = h->U;
+      a.Uout = h->U;
+      a.Win = h->W1;
+      a.Wout = h->W;
+      a.kind = ssp ? 1 : 0;
+      a.last = 1;
+      a.beta = 1.0;
+      a.write_u_all = 1;
+      rc = launch_stage(h, a);
+      if (rc) return rc;
+    }
     if (s < ntimed) CK(h, cudaEventRecord(h->stage_ev[2 * s + 1], h->stream));
     CK(h, launch_dt(h->ngrids, 1, cfl, fixed_dt, h->dt, h->t, h->smax, h->smax_next, h->stream));
     h->launches++;
+  }
+  if (Ucur != h->U) {
+    const size_t ncell = static_cast<size_t>(h->nbt) * NV * NCELL;
+    CK(h, cudaMemcpyAsync(h->U, Ucur, ncell * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    if (mixed) CK(h, cudaMemcpyAsync(h->W, Wcur, ncell * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
   }
   CK(h, cudaGetLastError());
   return BATS_OK;
@@ -466,7 +515,7 @@ int run_steps(bats_t* h, int n, double cfl, double fixed_dt, double* t_out) {
       if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
       cudaGraph_t g;
       CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-      long long l0 = h->launches;
+      h->launches = 0;
       int rc = enqueue_steps(h, n, cfl, fixed_dt, false);
       cudaError_t e = cudaStreamEndCapture(h->stream, &g);
       if (rc) return rc;
@@ -477,10 +526,10 @@ int run_steps(bats_t* h, int n, double cfl, double fixed_dt, double* t_out) {
       h->graph_n = n;
       h->graph_cfl = cfl;
       h->graph_dt = fixed_dt;
-      h->launches = l0;
+      h->graph_launches = h->launches;
     }
     CK(h, cudaGraphLaunch(h->graph, h->stream));
-    h->launches = static_cast<long long>(n) * (h->learned ? 8 : 4);
+    h->launches = h->graph_launches;
     h->timed_steps = 0;
   } else {
     int rc = enqueue_steps(h, n, cfl, fixed_dt, true);
@@ -526,7 +575,8 @@ int bats_create(const bats_grid_desc* grids, int n_grids, const bats_physics* ph
   *out = nullptr;
   if (!grids || n_grids <= 0 || !phys) return fail(nullptr, BATS_ERR_INVALID_ARG, "grids/phys missing");
   if (!(phys->gamma > 1.0)) return fail(nullptr, BATS_ERR_INVALID_ARG, "gamma must exceed 1");
-  if (phys->limiter < 0 || phys->limiter > 1 || phys->rk < 0 || phys->rk > 1 || phys->precision < 0 ||
+  if (phys->limiter < 0 || phys->limiter > 2 || phys->rk < 0 || phys->rk > 2 || phys->local_dt < 0 ||
+      phys->local_dt > 1 || phys->precision < 0 ||
       phys->precision > 1 || phys->b0 < 0 || phys->b0 > 3)
     return fail(nullptr, BATS_ERR_INVALID_ARG, "bad physics enumeration");
   bats_t* h = new bats_t();
@@ -562,6 +612,7 @@ int bats_create(const bats_grid_desc* grids, int n_grids, const bats_physics* ph
   h->bpc = std::max(1, phys->blocks_per_cta);
   h->ctas_per_sm = phys->ctas_per_sm;
   h->use_graph = phys->use_graph;
+  h->local_dt = phys->local_dt ? 1 : 0;
 
   int rc = BATS_OK;
   int dev = 0;
@@ -590,6 +641,12 @@ int bats_create(const bats_grid_desc* grids, int n_grids, const bats_physics* ph
       (rc = dev_alloc(h, &h->t, h->ngrids)) || (rc = dev_alloc(h, &h->smax, h->ngrids)) ||
       (rc = dev_alloc(h, &h->smax_next, h->ngrids)) || (rc = dev_alloc(h, &h->errw, 3)) ||
       (rc = dev_alloc(h, &h->staging, h->staging_n))) {
+    free_all(h);
+    g_create_error = h->err;
+    delete h;
+    return rc;
+  }
+  if (h->local_dt && (rc = dev_alloc(h, &h->dtc, static_cast<size_t>(h->nbt) * NCELL))) {
     free_all(h);
     g_create_error = h->err;
     delete h;

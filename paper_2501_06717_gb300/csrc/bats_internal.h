@@ -51,7 +51,7 @@ struct BlockDev {
 struct PhysDev {
   double gamma, gm1, inv_gm1;
   float gammaf, gm1f, inv_gm1f, padf_;
-  int32_t limiter, rk, precision, b0, powell, learned;
+  int32_t limiter, rk, precision, b0, powell, learned;  // limiter 2: first order; rk 2: one stage
   double b0p[12];
 };
 
@@ -84,7 +84,10 @@ struct StageArgs {
                           // 4: features and plain fluxes only (Xf, Fd)
   int32_t last;           // 1: reduce the CFL bound of Uout into smax_next
   int32_t write_u_all;    // mixed: 1 = write Uout (FP64) too, 0 = only the FP32 primitives Wout
-  double beta;            // c = beta * dt[grid]
+  double beta;            // c = beta * dt[grid], or beta * dtc[cell] with local time steps
+  double* dtc;            // local time stepping: per-cell dt (read), rewritten from the new
+                          // state by the last stage (nullptr: global dt)
+  double cfl;             // CFL number for dtc
   PhysDev ph;
   // learned form; face index ((blk * 3 + d) * 576 + line * 9 + f)
   int32_t learned;        // kinds 0-2: add the clipped, rescaled correction Y

@@ -149,9 +149,10 @@ __device__ __forceinline__ R mc_(R a, R b) {
   }
   return r;
 }
+// kind 0 minmod, 1 MC, 2 none (first order: piecewise-constant faces)
 template <class R>
 __device__ __forceinline__ R limit_(int kind, R a, R b) {
-  return kind == 1 ? mc_(a, b) : minmod_(a, b);
+  return kind == 2 ? R(0) : (kind == 1 ? mc_(a, b) : minmod_(a, b));
 }
 
 // Background field B0 at point x (split field B = B0 + B1).
@@ -1190,13 +1191,16 @@ __global__ void __launch_bounds__(STAGE_THREADS, MIXED ? 2 : 1) k_stage(const St
       auto cells = [&](const bool commit) -> bool {
         bool any_bad = false;
         R smax_loc = R(0);
-        const double cdt = a.beta * a.dt[B.grid];
+        const double cdt_blk = a.beta * a.dt[B.grid];
         // mixed form, first stage of the midpoint scheme: U* only feeds the
         // second stage's FP32 primitives, so W* = W^n + the increment, in FP32
         // (the FP64 state is read and accumulated in the last stage only)
         const bool light = MIXED && a.kind == 0 && !a.last && !a.write_u_all;
-        const float c32 = d2f_int(cdt);
+        const float c32_blk = d2f_int(cdt_blk);
         for (int c = tid; c < NCELL; c += STAGE_THREADS) {
+          // local time stepping: this cell's own dt
+          const double cdt = a.dtc ? a.beta * a.dtc[static_cast<int64_t>(blk) * NCELL + c] : cdt_blk;
+          const float c32 = a.dtc ? d2f_int(cdt) : c32_blk;
           const int ci = c & 7, cj = (c >> 3) & 7, ck = c >> 6;
           // face indices (line * 9 + position) of the low faces in x, y, z
           const int tx = (ck * NC + cj) * 9 + ci;
@@ -1351,6 +1355,14 @@ __global__ void __launch_bounds__(STAGE_THREADS, MIXED ? 2 : 1) k_stage(const St
               }
             }
             smax_loc = sacc > smax_loc ? sacc : smax_loc;
+            if (a.dtc) {
+              double sd;
+              if constexpr (MIXED) sd = f2d_int(sacc);
+              else sd = sacc;
+              a.dtc[static_cast<int64_t>(blk) * NCELL + c] = a.cfl / sd;
+            }
+          } else if (a.last && a.dtc && a.kind != 2) {
+            a.dtc[static_cast<int64_t>(blk) * NCELL + c] = 0.0;  // body cell
           }
         }
         if (commit && a.last && a.kind != 2) {
@@ -1452,7 +1464,7 @@ __global__ void k_prim_mixed(const double* __restrict__ U, float* __restrict__ W
 // CFL bound of the current state for blocks [b0, b0+nb): one CTA per block.
 template <bool MIXED>
 __global__ void k_cfl(const double* __restrict__ U, const float* __restrict__ Wt, const GridDev* grids,
-                      const BlockDev* blocks, PhysDev ph, int b0, unsigned long long* smax) {
+                      const BlockDev* blocks, PhysDev ph, int b0, unsigned long long* smax, double* dtc, double cfl) {
   __shared__ double sred[NCELL / 32];
   int blk = b0 + blockIdx.x, c = threadIdx.x;
   const BlockDev B = blocks[blk];
@@ -1491,6 +1503,8 @@ __global__ void k_cfl(const double* __restrict__ U, const float* __restrict__ Wt
       }
     }
   }
+  // local time stepping: the cell's own dt (0 in the body)
+  if (dtc) dtc[static_cast<int64_t>(blk) * NCELL + c] = in_body ? 0.0 : cfl / s;
   for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
   if ((c & 31) == 0) sred[c >> 5] = s;
   __syncthreads();
@@ -1588,6 +1602,7 @@ size_t stage_smem_bytes(bool mixed) {
 using StageFn = void (*)(const StageArgs);
 template <bool MIXED, bool LRN>
 StageFn stage_fn_l(int lim, bool b0) {
+  if (lim == 2) return b0 ? k_stage<MIXED, 2, true, LRN> : k_stage<MIXED, 2, false, LRN>;
   if (lim == 1) return b0 ? k_stage<MIXED, 1, true, LRN> : k_stage<MIXED, 1, false, LRN>;
   return b0 ? k_stage<MIXED, 0, true, LRN> : k_stage<MIXED, 0, false, LRN>;
 }
@@ -1598,7 +1613,7 @@ StageFn stage_fn(int lim, bool b0, bool lrn = false) {
 
 cudaError_t stage_setup(int occ[2]) {
   cudaError_t e = cudaSuccess;
-  for (int lim = 0; lim < 2 && e == cudaSuccess; lim++)
+  for (int lim = 0; lim < 3 && e == cudaSuccess; lim++)
     for (int b0 = 0; b0 < 2 && e == cudaSuccess; b0++)
       for (int lrn = 0; lrn < 2 && e == cudaSuccess; lrn++) {
         e = cudaFuncSetAttribute(stage_fn<false>(lim, b0, lrn), cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1648,11 +1663,16 @@ cudaError_t launch_prim_mixed(const double* U, float* Wt, int b0, int nb, float 
   k_prim_mixed<<<grid_for(static_cast<int64_t>(nb) * NCELL), 256, 0, st>>>(U, Wt, b0, nb, gm1f);
   return cudaGetLastError();
 }
+cudaError_t launch_cfl_dt(bool mixed, const double* U, const float* Wt, const GridDev* grids,
+                          const BlockDev* blocks, const PhysDev& ph, int b0, int nb, unsigned long long* smax,
+                          double* dtc, double cfl, cudaStream_t st) {
+  if (mixed) k_cfl<true><<<nb, NCELL, 0, st>>>(U, Wt, grids, blocks, ph, b0, smax, dtc, cfl);
+  else k_cfl<false><<<nb, NCELL, 0, st>>>(U, Wt, grids, blocks, ph, b0, smax, dtc, cfl);
+  return cudaGetLastError();
+}
 cudaError_t launch_cfl(bool mixed, const double* U, const float* Wt, const GridDev* grids, const BlockDev* blocks,
                        const PhysDev& ph, int b0, int nb, unsigned long long* smax, cudaStream_t st) {
-  if (mixed) k_cfl<true><<<nb, NCELL, 0, st>>>(U, Wt, grids, blocks, ph, b0, smax);
-  else k_cfl<false><<<nb, NCELL, 0, st>>>(U, Wt, grids, blocks, ph, b0, smax);
-  return cudaGetLastError();
+  return launch_cfl_dt(mixed, U, Wt, grids, blocks, ph, b0, nb, smax, nullptr, 0.0, st);
 }
 cudaError_t launch_dt(int ngrids, int mode, double cfl, double fixed_dt, double* dt, double* t,
                       unsigned long long* smax, unsigned long long* smax_next, cudaStream_t st) {
