@@ -80,7 +80,7 @@ typedef struct {
   int32_t no_fallback;   /* test switch: 1 keeps a learned block update even where it is non-physical */
   const double* mlp;     /* MLP_NPARAM weights (W1,b1,W2,b2,W3,b3), row-major [out][in] */
   int32_t local_dt;      /* 1 = local time stepping: each cell its own dt (steady-state runs) */
-  int32_t pad2_;
+  int32_t reflux;        /* 1 = conservative flux correction at resolution changes */
 } or_desc;
 
 typedef struct {
@@ -666,9 +666,65 @@ static void face_flux(const grid_t* G, int dir, const double* Wt /* [12^3][8] */
   out->B0[2] = B0f[2];
 }
 
+/* Kind of the neighbour region across face s (= 2 d + side) of block b: 0
+ * same level or domain boundary, 1 one level coarser, 2 refined. */
+static int face_kind(const grid_t* G, int b, int s) {
+  const or_desc* d = G->d;
+  const int32_t* L = d->leaves + 4 * b;
+  int lev = L[0], dir = s >> 1, side = s & 1;
+  long p[3] = {L[1], L[2], L[3]};
+  p[dir] += side ? 1 : -1;
+  long n = G->nblk[lev][dir];
+  if (p[dir] < 0 || p[dir] >= n) {
+    if (d->bc[s] != BC_PERIODIC) return 0;
+    p[dir] = (p[dir] + n) % n;
+  }
+  if (G->map[lev][map_index(G, lev, p[0], p[1], p[2])] >= 0) return 0;
+  if (lev >= 1 && G->map[lev - 1][map_index(G, lev - 1, p[0] >> 1, p[1] >> 1, p[2] >> 1)] >= 0) return 1;
+  return 2;
+}
+
+/* Refluxing (conservative flux correction at resolution changes): the flux
+ * through a coarse face that borders a refined region is the mean of the 4
+ * fine fluxes through it, so that what leaves the fine cells enters the
+ * coarse cell.  fbound holds, per block, its face fluxes on the 6 block faces
+ * [nb][6][64][8] ((q, r) = the two transverse cell indices, increasing axis
+ * order), filled for every block that has a coarser neighbour. */
+static void reflux_face(const grid_t* G, int b, int s, const double* fbound, face_t* Fx) {
+  const or_desc* d = G->d;
+  const int32_t* L = d->leaves + 4 * b;
+  int lev = L[0], dir = s >> 1, side = s & 1;
+  int t1 = dir == 0 ? 1 : 0, t2 = dir == 2 ? 1 : 2;
+  long fb[3];
+  fb[dir] = side ? 2L * L[1 + dir] + 2 : 2L * L[1 + dir] - 1;
+  long n = G->nblk[lev + 1][dir];
+  fb[dir] = (fb[dir] + n) % n;
+  for (int q = 0; q < NC; q++)
+    for (int r = 0; r < NC; r++) {
+      double f[2][2][NV];
+      for (int eq = 0; eq < 2; eq++)
+        for (int er = 0; er < 2; er++) {
+          long gq = 2L * ((long)L[1 + t1] * NC + q) + eq, gr = 2L * ((long)L[1 + t2] * NC + r) + er;
+          fb[t1] = gq / NC;
+          fb[t2] = gr / NC;
+          int fine = G->map[lev + 1][map_index(G, lev + 1, fb[0], fb[1], fb[2])];
+          if (fine < 0) return; /* excluded by the 2:1 balance */
+          int qf = (int)(gq - fb[t1] * NC), rf = (int)(gr - fb[t2] * NC);
+          const double* src = fbound + (((long)fine * 6 + (s ^ 1)) * 64 + qf * NC + rf) * NV;
+          for (int v = 0; v < NV; v++) f[eq][er][v] = src[v];
+        }
+      face_t* o = &Fx[(dir * 9 + (side ? NC : 0)) * 64 + q * 8 + r];
+      for (int v = 0; v < NV; v++) o->F[v] = 0.25 * ((f[0][0][v] + f[1][0][v]) + (f[0][1][v] + f[1][1][v]));
+    }
+}
+
 /* Residual R = -sum_d (F_{d,+} - F_{d,-}) / dx_d + S for every cell of block b,
- * from the padded tile of the stage input. R is [8][512] for this block. */
-static void block_residual(grid_t* G, int b, double* R) {
+ * from the padded tile of the stage input. R is [8][512] for this block.
+ * bound_out (nullable, [6][64][8]): the block's face fluxes on its 6 faces;
+ * fbound (nullable): refluxing with the fine blocks' boundary fluxes. */
+static void block_residual_rf(grid_t* G, int b, double* R, double* bound_out, const double* fbound);
+static void block_residual(grid_t* G, int b, double* R) { block_residual_rf(G, b, R, NULL, NULL); }
+static void block_residual_rf(grid_t* G, int b, double* R, double* bound_out, const double* fbound) {
   const or_desc* d = G->d;
   const int32_t* L = d->leaves + 4 * b;
   int lev = L[0];
@@ -712,6 +768,14 @@ static void block_residual(grid_t* G, int b, double* R) {
           face_flux(G, dir, Wt, ci[0] + NG, ci[1] + NG, ci[2] + NG, B0f, &Fx[(dir * 9 + f) * 64 + q * 8 + r]);
         }
   }
+  if (bound_out)
+    for (int s = 0; s < 6; s++)
+      for (int qr = 0; qr < 64; qr++)
+        memcpy(bound_out + (s * 64 + qr) * NV, Fx[((s >> 1) * 9 + ((s & 1) ? NC : 0)) * 64 + qr].F,
+               sizeof(double) * NV);
+  if (fbound)
+    for (int s = 0; s < 6; s++)
+      if (face_kind(G, b, s) == 2) reflux_face(G, b, s, fbound, Fx);
   /* 4. sources and residual per cell */
   double idx[3] = {1.0 / G->dx[lev][0], 1.0 / G->dx[lev][1], 1.0 / G->dx[lev][2]};
   for (int k = 0; k < NC; k++)
@@ -921,11 +985,26 @@ int or_stage_ex(const or_desc* d, const double* Uin, const double* Ubase, double
   int nb = G.nb;
   or_desc plain = *d;
   plain.learned = 0;
+  double* fbound = NULL;
+  if (d->reflux) {
+    if (d->learned) { grid_free(&G); return OR_EINVAL; }
+    fbound = (double*)calloc((size_t)nb * 6 * 64 * NV, sizeof(double));
+    if (!fbound) { grid_free(&G); return OR_ENOMEM; }
+#pragma omp parallel for schedule(dynamic)
+    for (int b = 0; b < nb; b++) {
+      int has_coarser = 0;
+      for (int sf = 0; sf < 6; sf++) has_coarser |= face_kind(&G, b, sf) == 1;
+      if (!has_coarser) continue;
+      grid_t Gl = G;
+      double Rb[NV * NCELL];
+      block_residual_rf(&Gl, b, Rb, fbound + (size_t)b * 6 * 64 * NV, NULL);
+    }
+  }
 #pragma omp parallel for schedule(dynamic)
   for (int b = 0; b < nb; b++) {
     grid_t Gl = G;
     double Rb[NV * NCELL], Ob[NV * NCELL];
-    block_residual(&Gl, b, Rb);
+    block_residual_rf(&Gl, b, Rb, NULL, fbound);
     int ok = block_update(&Gl, b, Rb, Uin, Ubase, kind, c, dtc, Ob);
     int fell_back = 0;
     if (!ok && d->learned && d->mlp && !d->no_fallback) {
@@ -937,6 +1016,7 @@ int or_stage_ex(const or_desc* d, const double* Uin, const double* Ubase, double
     if (fb) fb[b] = fell_back;
     for (int v = 0; v < NV; v++) memcpy(Uout + ((long)v * nb + b) * NCELL, Ob + v * NCELL, sizeof(double) * NCELL);
   }
+  free(fbound);
   grid_free(&G);
   return OR_OK;
 }

@@ -63,7 +63,7 @@ class _Desc(ctypes.Structure):
         ("no_fallback", ctypes.c_int32),
         ("mlp", ctypes.POINTER(ctypes.c_double)),
         ("local_dt", ctypes.c_int32),
-        ("pad2_", ctypes.c_int32),
+        ("reflux", ctypes.c_int32),
     ]
 
 
@@ -146,6 +146,7 @@ class _Bound:
             d.learned = 0
         d.no_fallback = int(getattr(prob, "no_fallback", 0) or 0)
         d.local_dt = int(getattr(prob, "local_dt", 0) or 0)
+        d.reflux = int(getattr(prob, "reflux", 0) or 0)
         self.desc = d
         self.nb = d.n_leaves
 

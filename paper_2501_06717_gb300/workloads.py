@@ -61,6 +61,7 @@ class Problem:
     learned: int = 0
     mlp: np.ndarray = None
     local_dt: int = 0
+    reflux: int = 0
 
     @property
     def nb(self):
