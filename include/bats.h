@@ -100,7 +100,13 @@ typedef struct {
  *                 with a CFL number, every cell advances with its own
  *                 dt_i = cfl / sum_d (|u_d| + c_f,d) / dx_d of the step's initial
  *                 state, in every stage; the elapsed time advances by the global
- *                 dt.  Ignored by bats_step_dt (fixed dt). */
+ *                 dt.  Ignored by bats_step_dt (fixed dt).
+ *  reflux         1 = conservative flux correction at resolution changes: the
+ *                 flux through a coarse face that borders a refined region is
+ *                 replaced, for the coarse cell, by the mean of the 4 fine
+ *                 fluxes through it, so every conserved variable is conserved to
+ *                 round-off on periodic grids without sources.  Not with
+ *                 `learned` (BATS_ERR_INVALID_ARG). */
 typedef struct {
   double gamma;
   int32_t limiter, rk, precision, b0;
@@ -108,7 +114,7 @@ typedef struct {
   int32_t powell, learned, persistent, blocks_per_cta;
   int32_t ctas_per_sm, use_graph;
   int32_t local_dt;
-  int32_t reserved;
+  int32_t reflux;
 } bats_physics;
 
 /* Create a solver for n_grids independent grids advanced together (batched

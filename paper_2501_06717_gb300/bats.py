@@ -59,7 +59,7 @@ class bats_physics(ctypes.Structure):
         ("ctas_per_sm", ctypes.c_int32),
         ("use_graph", ctypes.c_int32),
         ("local_dt", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("reflux", ctypes.c_int32),
     ]
 
 
@@ -175,6 +175,7 @@ def physics_from(problem, precision=BATS_FP64, persistent=0, blocks_per_cta=1, c
     ph.ctas_per_sm = int(ctas_per_sm)
     ph.use_graph = int(use_graph)
     ph.local_dt = int(getattr(problem, "local_dt", 0) or 0)
+    ph.reflux = int(getattr(problem, "reflux", 0) or 0)
     return ph
 
 

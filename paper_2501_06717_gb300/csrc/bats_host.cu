@@ -29,6 +29,8 @@ cudaError_t launch_init_grid_states(GridDev* grids, int ngrids, double inv_gm1, 
 cudaError_t launch_prim_mixed(const double* U, float* Wt, int b0, int nb, float gm1f, cudaStream_t st);
 cudaError_t launch_cfl(bool mixed, const double* U, const float* Wt, const GridDev* grids, const BlockDev* blocks,
                        const PhysDev& ph, int b0, int nb, unsigned long long* smax, cudaStream_t st);
+cudaError_t launch_reflux(bool mixed, const StageArgs& a, const RefluxTask* tasks, const int32_t* rblocks, int nrb,
+                          cudaStream_t st);
 cudaError_t launch_cfl_dt(bool mixed, const double* U, const float* Wt, const GridDev* grids,
                           const BlockDev* blocks, const PhysDev& ph, int b0, int nb, unsigned long long* smax,
                           double* dtc, double cfl, cudaStream_t st);
@@ -68,6 +70,13 @@ struct bats {
   int persistent = 0, bpc = 1, ctas_per_sm = 0, use_graph = 0;
   int local_dt = 0;
   double* dtc = nullptr;  // local time stepping: per-cell dt [nbt][512]
+  // refluxing
+  int reflux = 0, nslots = 0;
+  std::vector<RefluxTask> rtasks_h;
+  std::vector<int32_t> rblocks_h;        // per corrected block: first task, task count
+  double* freg = nullptr;
+  RefluxTask* rtasks_d = nullptr;
+  int32_t* rblocks_d = nullptr;
   int occ[2] = {1, 1};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<cudaEvent_t> stage_ev;   // pairs around the two stage launches of each step
@@ -188,6 +197,7 @@ int build_grid(bats_t* h, const bats_grid_desc& d, int gidx, int block0, std::ve
     B.bi = L[1];
     B.bj = L[2];
     B.bk = L[3];
+    for (int f = 0; f < 6; f++) B.rslot[f] = -1;
     for (int dk = -1; dk <= 1; dk++)
       for (int dj = -1; dj <= 1; dj++)
         for (int di = -1; di <= 1; di++) {
@@ -246,6 +256,44 @@ int build_grid(bats_t* h, const bats_grid_desc& d, int gidx, int block0, std::ve
     for (int s = 0; s < 6; s++)
       if (B.ftype[s] == FACE_COARSER || B.ftype[s] == FACE_FINER) B.amr = 1;
     blocks[block0 + b] = B;
+  }
+  // refluxing: a flux-register slot for every face at a resolution change,
+  // and one task per coarse face that borders a refined region
+  for (int b = 0; b < d.n_leaves; b++) {
+    BlockDev& B = blocks[block0 + b];
+    for (int f = 0; f < 6; f++)
+      if (B.ftype[f] == FACE_COARSER || B.ftype[f] == FACE_FINER) B.rslot[f] = h->nslots++;
+  }
+  for (int b = 0; b < d.n_leaves; b++) {
+    const BlockDev& B = blocks[block0 + b];
+    int first = static_cast<int>(h->rtasks_h.size());
+    for (int f = 0; f < 6; f++) {
+      if (B.ftype[f] != FACE_FINER) continue;
+      const int dir = f >> 1, side = f & 1, l = B.level;
+      const int t1 = dir == 0 ? 1 : 0, t2 = dir == 2 ? 1 : 2;
+      const int64_t bc[3] = {B.bi, B.bj, B.bk};
+      RefluxTask T{};
+      T.blk = block0 + b;
+      T.s = f;
+      T.cslot = B.rslot[f];
+      for (int q = 0; q < 4; q++) {
+        int64_t p[3];
+        const int64_t n = H.nblk(l + 1, dir);
+        p[dir] = ((side ? 2 * bc[dir] + 2 : 2 * bc[dir] - 1) + n) % n;
+        p[t1] = 2 * bc[t1] + (q & 1);
+        p[t2] = 2 * bc[t2] + (q >> 1);
+        int32_t id = H.at(l + 1, p[0], p[1], p[2]);
+        if (id < 0) return fail(h, BATS_ERR_UNBALANCED_TREE, "grid " + std::to_string(gidx) + ": refined face without fine leaves");
+        T.fslot[q] = blocks[block0 + id].rslot[f ^ 1];
+        if (T.fslot[q] < 0) return fail(h, BATS_ERR_UNBALANCED_TREE, "grid " + std::to_string(gidx) + ": fine face without a slot");
+      }
+      h->rtasks_h.push_back(T);
+    }
+    int cnt = static_cast<int>(h->rtasks_h.size()) - first;
+    if (cnt) {
+      h->rblocks_h.push_back(first);
+      h->rblocks_h.push_back(cnt);
+    }
   }
   // grid record + level maps with global block indices
   std::memset(&gd, 0, sizeof(gd));
@@ -320,6 +368,9 @@ void free_all(bats_t* h) {
   cudaFree(h->W);
   cudaFree(h->W1);
   cudaFree(h->dtc);
+  cudaFree(h->freg);
+  cudaFree(h->rtasks_d);
+  cudaFree(h->rblocks_d);
   cudaFree(h->dt);
   cudaFree(h->t);
   cudaFree(h->smax);
@@ -372,10 +423,23 @@ int launch_stage_one(bats_t* h, const StageArgs& a) {
   return BATS_OK;
 }
 
+// Refluxing after a stage (kinds 0, 1): the coarse cells at refined faces
+// take the fine fluxes' mean instead of their own face flux.
+int launch_reflux(bats_t* h, const StageArgs& a) {
+  if (!a.freg || a.kind > 1) return BATS_OK;
+  h->launches++;
+  CK(h, launch_reflux(h->ph.precision == BATS_MIXED, a, h->rtasks_d, h->rblocks_d,
+                      static_cast<int>(h->rblocks_h.size() / 2), h->stream));
+  return BATS_OK;
+}
+
 // One stage; with the learned form, three launches: the network inputs of
 // every face, the network, and the stage with the correction.
 int launch_stage(bats_t* h, const StageArgs& a) {
-  if (!h->learned || a.kind >= 3) return launch_stage_one(h, a);
+  if (!h->learned || a.kind >= 3) {
+    int rc = launch_stage_one(h, a);
+    return rc ? rc : launch_reflux(h, a);
+  }
   StageArgs f = a;
   f.kind = 3;
   f.learned = 0;
@@ -447,6 +511,7 @@ int enqueue_steps(bats_t* h, int n, double cfl, double fixed_dt, bool timed) {
     StageArgs a = base_args(h);
     a.dtc = lts ? h->dtc : nullptr;
     a.cfl = cfl;
+    a.freg = h->freg;
     if (euler) {
       // U^{n+1} = U^n + dt R(U^n)
       a.Uin = Ucur;
@@ -575,6 +640,8 @@ int bats_create(const bats_grid_desc* grids, int n_grids, const bats_physics* ph
   *out = nullptr;
   if (!grids || n_grids <= 0 || !phys) return fail(nullptr, BATS_ERR_INVALID_ARG, "grids/phys missing");
   if (!(phys->gamma > 1.0)) return fail(nullptr, BATS_ERR_INVALID_ARG, "gamma must exceed 1");
+  if (phys->reflux && phys->learned)
+    return fail(nullptr, BATS_ERR_INVALID_ARG, "refluxing is not available with the learned correction");
   if (phys->limiter < 0 || phys->limiter > 2 || phys->rk < 0 || phys->rk > 2 || phys->local_dt < 0 ||
       phys->local_dt > 1 || phys->precision < 0 ||
       phys->precision > 1 || phys->b0 < 0 || phys->b0 > 3)
@@ -613,6 +680,7 @@ int bats_create(const bats_grid_desc* grids, int n_grids, const bats_physics* ph
   h->ctas_per_sm = phys->ctas_per_sm;
   h->use_graph = phys->use_graph;
   h->local_dt = phys->local_dt ? 1 : 0;
+  h->reflux = phys->reflux ? 1 : 0;
 
   int rc = BATS_OK;
   int dev = 0;
@@ -646,6 +714,14 @@ int bats_create(const bats_grid_desc* grids, int n_grids, const bats_physics* ph
     delete h;
     return rc;
   }
+  if (h->reflux && !h->rtasks_h.empty() &&
+      ((rc = dev_alloc(h, &h->freg, static_cast<size_t>(h->nslots) * 64 * NV)) ||
+       (rc = dev_alloc(h, &h->rtasks_d, h->rtasks_h.size())) || (rc = dev_alloc(h, &h->rblocks_d, h->rblocks_h.size())))) {
+    free_all(h);
+    g_create_error = h->err;
+    delete h;
+    return rc;
+  }
   if (h->local_dt && (rc = dev_alloc(h, &h->dtc, static_cast<size_t>(h->nbt) * NCELL))) {
     free_all(h);
     g_create_error = h->err;
@@ -665,6 +741,12 @@ int bats_create(const bats_grid_desc* grids, int n_grids, const bats_physics* ph
     e = cudaMemcpyAsync(h->blocks_d, h->blocks_h.data(), sizeof(BlockDev) * h->nbt, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->levmap_d, h->levmap_h.data(), sizeof(int32_t) * h->levmap_h.size(),
+                        cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess && h->rtasks_d)
+    e = cudaMemcpyAsync(h->rtasks_d, h->rtasks_h.data(), sizeof(RefluxTask) * h->rtasks_h.size(),
+                        cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess && h->rblocks_d)
+    e = cudaMemcpyAsync(h->rblocks_d, h->rblocks_h.data(), sizeof(int32_t) * h->rblocks_h.size(),
                         cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->t, 0, sizeof(double) * h->ngrids, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->smax, 0, sizeof(unsigned long long) * h->ngrids, h->stream);

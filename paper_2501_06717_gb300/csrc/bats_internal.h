@@ -45,6 +45,7 @@ struct BlockDev {
   int32_t fnb[6];                // neighbour block (global index) for SAME / COARSER
   int32_t amr;                   // 1 if any face is COARSER or FINER
   int32_t body;                  // 1 if some cell centre lies inside the inner body
+  int32_t rslot[6];              // refluxing: flux-register slot of a COARSER/FINER face, else -1
   int32_t pad_[2];
 };
 
@@ -62,6 +63,13 @@ constexpr int MLP_NPARAM = MLP_H * MLP_IN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_
 struct MlpDev {
   uint32_t *w1, *w2, *w3, *w2t, *w3t;  // [64][24], [64][32], [8][32], [64][32], [64][8]
   float *b1, *b2, *b3;
+};
+
+// Refluxing: one coarse face that borders a refined region.  The register
+// slot cslot holds the coarse block's own 8 x 8 face fluxes, fslot[q] those of
+// the fine block in transverse quadrant q (= q1 + 2 q2) on its opposite face.
+struct RefluxTask {
+  int32_t blk, s, cslot, fslot[4];
 };
 
 // Arguments of one stage launch.
@@ -88,6 +96,7 @@ struct StageArgs {
   double* dtc;            // local time stepping: per-cell dt (read), rewritten from the new
                           // state by the last stage (nullptr: global dt)
   double cfl;             // CFL number for dtc
+  double* freg;           // refluxing: flux register [slot][64][8] (nullptr: off)
   PhysDev ph;
   // learned form; face index ((blk * 3 + d) * 576 + line * 9 + f)
   int32_t learned;        // kinds 0-2: add the clipped, rescaled correction Y

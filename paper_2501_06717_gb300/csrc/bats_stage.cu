@@ -1183,6 +1183,27 @@ __global__ void __launch_bounds__(STAGE_THREADS, MIXED ? 2 : 1) k_stage(const St
             fcol[(4 + fd2) * NFACE + fi] = Fr[6];
             fcol[7 * NFACE + fi] = Fr[7];
             fcol[8 * NFACE + fi] = R(0.5) * (WL[4] + WR[4]);
+            // refluxing: the block-face fluxes of faces at resolution changes
+            if (a.freg && (f == 0 || f == NC)) {
+              const int sl = B.rslot[2 * fd + (f == NC ? 1 : 0)];
+              if (sl >= 0) {
+                double* o = a.freg + (static_cast<int64_t>(sl) * 64 + fta * NC + ftb) * NV;
+                double Fd[8];
+#pragma unroll
+                for (int v = 0; v < NV; v++) {
+                  if constexpr (MIXED) Fd[v] = f2d_int(Fr[v]);
+                  else Fd[v] = Fr[v];
+                }
+                o[0] = Fd[0];
+                o[1 + fd] = Fd[1];
+                o[1 + fd1] = Fd[2];
+                o[1 + fd2] = Fd[3];
+                o[4 + fd] = Fd[4];
+                o[4 + fd1] = Fd[5];
+                o[4 + fd2] = Fd[6];
+                o[7] = Fd[7];
+              }
+            }
           }
       };
       // 4. per cell: flux differences, sources, update, CFL bound.  commit =
@@ -1338,8 +1359,12 @@ __global__ void __launch_bounds__(STAGE_THREADS, MIXED ? 2 : 1) k_stage(const St
               for (int v = 0; v < NV; v++) a.Wout[base + v * NCELL] = Wn[v];
             }
           }
-          // CFL bound of the new state: sum_d (|u_d| + c_f,d) / dx_d
-          if (a.last && !in_body && a.kind != 2) {
+          // CFL bound of the new state: sum_d (|u_d| + c_f,d) / dx_d (cells that
+          // refluxing corrects afterwards are bounded by the correction kernel)
+          const bool refl = a.freg && ((ci == 0 && B.ftype[0] == FACE_FINER) || (ci == NC - 1 && B.ftype[1] == FACE_FINER) ||
+                                       (cj == 0 && B.ftype[2] == FACE_FINER) || (cj == NC - 1 && B.ftype[3] == FACE_FINER) ||
+                                       (ck == 0 && B.ftype[4] == FACE_FINER) || (ck == NC - 1 && B.ftype[5] == FACE_FINER));
+          if (a.last && !in_body && a.kind != 2 && !refl) {
             R Bt[3] = {B0c[0] + Wn[4], B0c[1] + Wn[5], B0c[2] + Wn[6]};
             R sacc = R(0);
 #pragma unroll
@@ -1361,7 +1386,7 @@ __global__ void __launch_bounds__(STAGE_THREADS, MIXED ? 2 : 1) k_stage(const St
               else sd = sacc;
               a.dtc[static_cast<int64_t>(blk) * NCELL + c] = a.cfl / sd;
             }
-          } else if (a.last && a.dtc && a.kind != 2) {
+          } else if (a.last && a.dtc && a.kind != 2 && in_body) {
             a.dtc[static_cast<int64_t>(blk) * NCELL + c] = 0.0;  // body cell
           }
         }
@@ -1512,6 +1537,163 @@ __global__ void k_cfl(const double* __restrict__ U, const float* __restrict__ Wt
     double m = 0.0;
     for (int w = 0; w < NCELL / 32; w++) m = fmax(m, sred[w]);
     if (m > 0.0) atomicMax(&smax[B.grid], static_cast<unsigned long long>(__double_as_longlong(m)));
+  }
+}
+
+// Refluxing after a stage.  One CTA per corrected block, one thread per face
+// position (q, r) of a refined face: the coarse cell next to it trades its own
+// face flux for the mean of the 4 fine fluxes through the face (summed in the
+// oracle's order), i.e. its stage update gains c * dR with
+// dR = -+ (mean - F_coarse) / dx.  Faces are taken one at a time (a cell on an
+// edge of two refined faces gets both corrections in turn); in the last stage
+// the corrected cells' CFL bounds follow from the final state.
+__device__ __forceinline__ void reflux_cell(const StageArgs& a, const RefluxTask& T, int tid, int& c, bool& in_body) {
+  const BlockDev& B = a.blocks[T.blk];
+  const GridDev& G = a.grids[B.grid];
+  const int d = T.s >> 1, side = T.s & 1;
+  const int q = tid >> 3, r = tid & 7;
+  int cc[3];
+  cc[d] = side ? NC - 1 : 0;
+  cc[d == 0 ? 1 : 0] = q;
+  cc[d == 2 ? 1 : 2] = r;
+  c = (cc[2] * NC + cc[1]) * NC + cc[0];
+  in_body = false;
+  if (B.body) {
+    const int lev = B.level;
+    double x = G.lo[0] + ((static_cast<double>(B.bi * NC) + cc[0]) + 0.5) * G.dx[lev][0];
+    double y = G.lo[1] + ((static_cast<double>(B.bj * NC) + cc[1]) + 0.5) * G.dx[lev][1];
+    double z = G.lo[2] + ((static_cast<double>(B.bk * NC) + cc[2]) + 0.5) * G.dx[lev][2];
+    in_body = (x * x + y * y + z * z) < G.body_r * G.body_r;
+  }
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(64) k_reflux(const StageArgs a, const RefluxTask* __restrict__ tasks,
+                                               const int32_t* __restrict__ rblocks) {
+  const int first = rblocks[2 * blockIdx.x], cnt = rblocks[2 * blockIdx.x + 1];
+  const int tid = threadIdx.x;
+  const PhysDev& ph = a.ph;
+  for (int t = first; t < first + cnt; t++) {
+    const RefluxTask T = tasks[t];
+    const BlockDev& B = a.blocks[T.blk];
+    const GridDev& G = a.grids[B.grid];
+    int c;
+    bool in_body;
+    reflux_cell(a, T, tid, c, in_body);
+    if (!in_body) {
+      const int d = T.s >> 1, side = T.s & 1;
+      const int q = tid >> 3, r = tid & 7;
+      const double* Fc = a.freg + (static_cast<int64_t>(T.cslot) * 64 + tid) * NV;
+      const double* Ff = a.freg + static_cast<int64_t>(T.fslot[(q >> 2) + 2 * (r >> 2)]) * 64 * NV;
+      const int qf = 2 * (q & 3), rf = 2 * (r & 3);
+      const double idx_d = G.idx[B.level][d];
+      double dR[8];
+#pragma unroll
+      for (int v = 0; v < NV; v++) {
+        const double f00 = Ff[(qf * NC + rf) * NV + v], f10 = Ff[((qf + 1) * NC + rf) * NV + v];
+        const double f01 = Ff[(qf * NC + rf + 1) * NV + v], f11 = Ff[((qf + 1) * NC + rf + 1) * NV + v];
+        const double dF = 0.25 * ((f00 + f10) + (f01 + f11)) - Fc[v];
+        dR[v] = (side ? -dF : dF) * idx_d;
+      }
+      const int64_t cell = static_cast<int64_t>(T.blk) * NCELL + c;
+      const int64_t base = static_cast<int64_t>(T.blk) * (NV * NCELL) + c;
+      const double cdt = a.beta * (a.dtc ? a.dtc[cell] : a.dt[B.grid]);
+      bool bad = false;
+      if (MIXED && !(a.last || a.write_u_all)) {
+        // first midpoint stage of the mixed form: only W* exists
+        float Wo[8], dU[8], Wn[8];
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+          Wo[v] = a.Wout[base + v * NCELL];
+          dU[v] = d2f_int(cdt * dR[v]);
+        }
+        prim_increment(Wo, dU, ph.gm1f, Wn);
+        bad = !(Wn[0] > 0.f) || !(Wn[7] > 0.f);
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+          bad |= !finite_f(Wn[v]);
+          a.Wout[base + v * NCELL] = Wn[v];
+        }
+      } else {
+        double Uo[8];
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+          double u = a.Uout[base + v * NCELL];
+          u = a.kind == 1 ? u + 0.5 * (cdt * dR[v]) : fma(cdt, dR[v], u);
+          Uo[v] = u;
+          a.Uout[base + v * NCELL] = u;
+          bad |= !finite_d(u);
+        }
+        bad |= !positive_d(Uo[0]);
+        if constexpr (MIXED) {
+          float Wn[8];
+          double p64;
+          prim_mixed(Uo, ph.gm1f, Wn, &p64);
+          bad |= !positive_d(p64);
+#pragma unroll
+          for (int v = 0; v < NV; v++) a.Wout[base + v * NCELL] = Wn[v];
+        } else {
+          double Wn[8];
+          prim64(Uo, ph.gm1, Wn);
+          bad |= !positive_d(Wn[7]);
+        }
+      }
+      if (bad) {
+        atomicOr(&a.err[0], ERR_NONPHYSICAL);
+        atomicMin(&a.err[1], T.blk);
+      }
+    }
+    __syncthreads();
+  }
+  if (!a.last) return;
+  // CFL bounds (and local dt) of the corrected cells, as in the stage epilogue
+  for (int t = first; t < first + cnt; t++) {
+    const RefluxTask T = tasks[t];
+    const BlockDev& B = a.blocks[T.blk];
+    const GridDev& G = a.grids[B.grid];
+    int c;
+    bool in_body;
+    reflux_cell(a, T, tid, c, in_body);
+    if (in_body) continue;
+    const int ci = c & 7, cj = (c >> 3) & 7, ck = c >> 6;
+    const int lev = B.level;
+    const int gb0 = B.bi * NC, gb1 = B.bj * NC, gb2 = B.bk * NC;
+    const int64_t base = static_cast<int64_t>(T.blk) * (NV * NCELL) + c;
+    double md;
+    if constexpr (MIXED) {
+      float Wn[8], B0c[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+      for (int v = 0; v < NV; v++) Wn[v] = a.Wout[base + v * NCELL];
+      if (ph.b0 != B0_NONE)
+        b0_face<float>(ph, -1, ci, cj, ck, gb0, gb1, gb2, G.lof[0], G.lof[1], G.lof[2], G.dxf[lev][0],
+                       G.dxf[lev][1], G.dxf[lev][2], B0c);
+      const float Bt[3] = {B0c[0] + Wn[4], B0c[1] + Wn[5], B0c[2] + Wn[6]};
+      float sacc = 0.f;
+#pragma unroll
+      for (int e = 0; e < 3; e++) {
+        const float cf = fast_speed_n<float>(ph.gammaf, Wn[0], Wn[7], Bt[e], Bt[(e + 1) % 3], Bt[(e + 2) % 3]);
+        sacc = sacc + (fabsf(Wn[1 + e]) + cf) * G.idxf[lev][e];
+      }
+      md = f2d_int(sacc);
+    } else {
+      double U[8], Wn[8], B0c[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+      for (int v = 0; v < NV; v++) U[v] = a.Uout[base + v * NCELL];
+      prim64(U, ph.gm1, Wn);
+      if (ph.b0 != B0_NONE)
+        b0_face<double>(ph, -1, ci, cj, ck, gb0, gb1, gb2, G.lo[0], G.lo[1], G.lo[2], G.dx[lev][0], G.dx[lev][1],
+                        G.dx[lev][2], B0c);
+      const double Bt[3] = {B0c[0] + Wn[4], B0c[1] + Wn[5], B0c[2] + Wn[6]};
+      double sacc = 0.0;
+#pragma unroll
+      for (int e = 0; e < 3; e++) {
+        const double cf = fast_speed_exact(ph.gamma, Wn[0], Wn[7], Bt[e], Bt[(e + 1) % 3], Bt[(e + 2) % 3]);
+        sacc = sacc + (fabs(Wn[1 + e]) + cf) / G.dx[lev][e];
+      }
+      md = sacc;
+    }
+    if (md > 0.0) atomicMax(&a.smax_next[B.grid], static_cast<unsigned long long>(__double_as_longlong(md)));
+    if (a.dtc) a.dtc[static_cast<int64_t>(T.blk) * NCELL + c] = a.cfl / md;
   }
 }
 
@@ -1668,6 +1850,13 @@ cudaError_t launch_cfl_dt(bool mixed, const double* U, const float* Wt, const Gr
                           double* dtc, double cfl, cudaStream_t st) {
   if (mixed) k_cfl<true><<<nb, NCELL, 0, st>>>(U, Wt, grids, blocks, ph, b0, smax, dtc, cfl);
   else k_cfl<false><<<nb, NCELL, 0, st>>>(U, Wt, grids, blocks, ph, b0, smax, dtc, cfl);
+  return cudaGetLastError();
+}
+cudaError_t launch_reflux(bool mixed, const StageArgs& a, const RefluxTask* tasks, const int32_t* rblocks, int nrb,
+                          cudaStream_t st) {
+  if (nrb <= 0) return cudaSuccess;
+  if (mixed) k_reflux<true><<<nrb, 64, 0, st>>>(a, tasks, rblocks);
+  else k_reflux<false><<<nrb, 64, 0, st>>>(a, tasks, rblocks);
   return cudaGetLastError();
 }
 cudaError_t launch_cfl(bool mixed, const double* U, const float* Wt, const GridDev* grids, const BlockDev* blocks,
