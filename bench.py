@@ -176,8 +176,8 @@ def learned_form_summary(stream, steps=32):
     import torch
     from paper_2501_06717_gb300 import bats, learn
     t0 = time.perf_counter()
-    X, Y = learn.make_pairs(variants=[101, 102, 103, 104, 105, 106], snapshots=(4, 12), keep=0.3)
-    P, hist = learn.train(X, Y, epochs=6, lr=1e-3)
+    X, Y = learn.make_pairs(variants=list(range(101, 117)), snapshots=(4, 12, 20), keep=0.3)
+    P, hist = learn.train(X, Y, epochs=20, lr=2e-3)
     t_train = time.perf_counter() - t0
     e_plain, e_learn = learn.evaluate(P, nsteps=16)
     coarse, fine = W.blast(), W.blast(resolution=2)
