@@ -29,6 +29,7 @@ cudaError_t launch_init_grid_states(GridDev* grids, int ngrids, double inv_gm1, 
 cudaError_t launch_prim_mixed(const double* U, float* Wt, int b0, int nb, float gm1f, cudaStream_t st);
 cudaError_t launch_cfl(bool mixed, const double* U, const float* Wt, const GridDev* grids, const BlockDev* blocks,
                        const PhysDev& ph, int b0, int nb, unsigned long long* smax, cudaStream_t st);
+cudaError_t launch_amr_ghosts(const StageArgs& a, const GhostTask* tasks, int ntasks, cudaStream_t st);
 cudaError_t launch_reflux(bool mixed, const StageArgs& a, const RefluxTask* tasks, const int32_t* rblocks, int nrb,
                           cudaStream_t st);
 cudaError_t launch_cfl_dt(bool mixed, const double* U, const float* Wt, const GridDev* grids,
@@ -77,6 +78,10 @@ struct bats {
   double* freg = nullptr;
   RefluxTask* rtasks_d = nullptr;
   int32_t* rblocks_d = nullptr;
+  // mixed form: ghost slabs of faces at resolution changes, computed ahead of each stage
+  std::vector<GhostTask> gtasks_h;
+  GhostTask* gtasks_d = nullptr;
+  float* gbuf = nullptr;
   int occ[2] = {1, 1};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<cudaEvent_t> stage_ev;   // pairs around the two stage launches of each step
@@ -262,7 +267,10 @@ int build_grid(bats_t* h, const bats_grid_desc& d, int gidx, int block0, std::ve
   for (int b = 0; b < d.n_leaves; b++) {
     BlockDev& B = blocks[block0 + b];
     for (int f = 0; f < 6; f++)
-      if (B.ftype[f] == FACE_COARSER || B.ftype[f] == FACE_FINER) B.rslot[f] = h->nslots++;
+      if (B.ftype[f] == FACE_COARSER || B.ftype[f] == FACE_FINER) {
+        B.rslot[f] = h->nslots++;
+        h->gtasks_h.push_back(GhostTask{block0 + b, f, B.rslot[f]});
+      }
   }
   for (int b = 0; b < d.n_leaves; b++) {
     const BlockDev& B = blocks[block0 + b];
@@ -369,6 +377,8 @@ void free_all(bats_t* h) {
   cudaFree(h->W1);
   cudaFree(h->dtc);
   cudaFree(h->freg);
+  cudaFree(h->gbuf);
+  cudaFree(h->gtasks_d);
   cudaFree(h->rtasks_d);
   cudaFree(h->rblocks_d);
   cudaFree(h->dt);
@@ -409,8 +419,15 @@ StageArgs base_args(bats_t* h) {
   return a;
 }
 
-int launch_stage_one(bats_t* h, const StageArgs& a) {
+int launch_stage_one(bats_t* h, const StageArgs& a0) {
   bool mixed = h->ph.precision == BATS_MIXED;
+  StageArgs a = a0;
+  if (mixed && h->gbuf) {
+    // the ghost slabs of faces at resolution changes, from this stage's input
+    a.gbuf = h->gbuf;
+    h->launches++;
+    CK(h, launch_amr_ghosts(a, h->gtasks_d, static_cast<int>(h->gtasks_h.size()), h->stream));
+  }
   int nitems = (a.nblocks + a.blocks_per_item - 1) / a.blocks_per_item;
   int grid = nitems;
   if (h->persistent) {
@@ -722,6 +739,14 @@ int bats_create(const bats_grid_desc* grids, int n_grids, const bats_physics* ph
     delete h;
     return rc;
   }
+  if (h->ph.precision == BATS_MIXED && !h->gtasks_h.empty() &&
+      ((rc = dev_alloc(h, &h->gbuf, static_cast<size_t>(h->nslots) * NV * 128)) ||
+       (rc = dev_alloc(h, &h->gtasks_d, h->gtasks_h.size())))) {
+    free_all(h);
+    g_create_error = h->err;
+    delete h;
+    return rc;
+  }
   if (h->local_dt && (rc = dev_alloc(h, &h->dtc, static_cast<size_t>(h->nbt) * NCELL))) {
     free_all(h);
     g_create_error = h->err;
@@ -741,6 +766,9 @@ int bats_create(const bats_grid_desc* grids, int n_grids, const bats_physics* ph
     e = cudaMemcpyAsync(h->blocks_d, h->blocks_h.data(), sizeof(BlockDev) * h->nbt, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->levmap_d, h->levmap_h.data(), sizeof(int32_t) * h->levmap_h.size(),
+                        cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess && h->gtasks_d)
+    e = cudaMemcpyAsync(h->gtasks_d, h->gtasks_h.data(), sizeof(GhostTask) * h->gtasks_h.size(),
                         cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess && h->rtasks_d)
     e = cudaMemcpyAsync(h->rtasks_d, h->rtasks_h.data(), sizeof(RefluxTask) * h->rtasks_h.size(),
@@ -881,8 +909,10 @@ int bats_debug_fill_ghosts_w(bats_t* h, int grid, double* T, size_t n) {
   StageArgs a = base_args(h);
   a.Uin = h->U;
   a.Win = h->W;
+  a.gbuf = h->gbuf;
   int32_t init[3] = {0, INT_MAX, 0};
   CK(h, cudaMemcpyAsync(h->errw, init, sizeof(init), cudaMemcpyHostToDevice, h->stream));
+  if (h->gbuf) CK(h, launch_amr_ghosts(a, h->gtasks_d, static_cast<int>(h->gtasks_h.size()), h->stream));
   CK(h, launch_debug_fill_w(a, G.block0, G.nb, dst, h->stream));
   if (!dev) CK(h, cudaMemcpyAsync(T, h->staging, need * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));

@@ -72,6 +72,13 @@ struct RefluxTask {
   int32_t blk, s, cslot, fslot[4];
 };
 
+// Mixed form: one face of a block at a resolution change (COARSER or FINER),
+// whose face-slab ghosts are computed ahead of the stage into slot `slot` of
+// the ghost-slab buffer.
+struct GhostTask {
+  int32_t blk, s, slot;
+};
+
 // Arguments of one stage launch.
 struct StageArgs {
   const double* Uin;      // stage input, block-major FP64
@@ -97,6 +104,7 @@ struct StageArgs {
                           // state by the last stage (nullptr: global dt)
   double cfl;             // CFL number for dtc
   double* freg;           // refluxing: flux register [slot][64][8] (nullptr: off)
+  float* gbuf;            // mixed form: ghost slabs of faces at resolution changes [slot][8][128]
   PhysDev ph;
   // learned form; face index ((blk * 3 + d) * 576 + line * 9 + f)
   int32_t learned;        // kinds 0-2: add the clipped, rescaled correction Y

@@ -874,55 +874,67 @@ __device__ __forceinline__ void fill_ghosts_block(const StageArgs& a, const Ghos
   }
 }
 
-// Mixed form: all face-slab ghosts of block blk from W.  Faces whose
-// neighbour is coarser go through the sample table `tab` (up to three such
-// faces, PSLOTS x PSTRIDE floats each): the samples are gathered together
-// with the other ghost cells, then, after a barrier, each fine ghost cell of
-// those faces is built from the table.
+// Mixed form: the face-slab ghosts of block blk from W.  Faces at a
+// resolution change come precomputed from the ghost-slab buffer (k_amr_ghosts,
+// launched before the stage): the stage kernel copies those slabs with bulk
+// copies; with copy_amr the threads copy them here (debug view).
 __device__ __forceinline__ void fill_ghosts_block_mixed(const StageArgs& a, const GhostCtx& cx, const BlockDev& B,
-                                                        int blk, float* sT, float* tab, int tid, int nthr) {
-  unsigned cmask = 0;
+                                                        int blk, float* sT, int tid, int nthr, bool copy_amr) {
+  unsigned amask = 0;
 #pragma unroll
-  for (int f = 0; f < 6; f++) cmask |= (B.ftype[f] == FACE_COARSER ? 1u : 0u) << f;
-  const int ncoarse = __popc(cmask);
-  const int nsamp = ncoarse * PSLOTS;
-  for (int q = tid; q < nsamp + NGHOST; q += nthr) {
-    if (q < nsamp) {
-      const int slot = q / PSLOTS, k = q - slot * PSLOTS;
-      unsigned m = cmask;
-      for (int r = 0; r < slot; r++) m &= m - 1;
-      const int sface = __ffs(m) - 1;
+  for (int f = 0; f < 6; f++) amask |= (B.ftype[f] == FACE_COARSER || B.ftype[f] == FACE_FINER ? 1u : 0u) << f;
+  for (int q = tid; q < NGHOST; q += nthr) {
+    if (!((amask >> (q >> 7)) & 1u)) fill_ghost<true, float>(a, cx, B, blk, q, sT);
+    else if (copy_amr) {
+      const int s = q >> 7, local = q & 127;
+      const float* src = a.gbuf + static_cast<int64_t>(B.rslot[s]) * (NV * 128) + local;
+#pragma unroll
+      for (int v = 0; v < NV; v++) sT[v * NTILE + NCELL + q] = src[v * 128];
+    }
+  }
+}
+
+// Mixed form: the face-slab ghosts of one face at a resolution change, one CTA
+// of 128 threads per face, one ghost cell per thread, into gbuf[slot][8][128].
+// Coarser neighbour: the coarse samples into a shared table, then every fine
+// ghost cell by the prolongation; finer neighbour: the restriction of each
+// ghost cell's 8 children.
+__global__ void __launch_bounds__(128) k_amr_ghosts(const StageArgs a, const GhostTask* __restrict__ tasks) {
+  __shared__ float tab[PSLOTS * PSTRIDE];
+  const GhostTask T = tasks[blockIdx.x];
+  const BlockDev& B = a.blocks[T.blk];
+  const GridDev& G = a.grids[B.grid];
+  const int tid = threadIdx.x;
+  float w[8];
+  if (B.ftype[T.s] == FACE_COARSER) {
+    if (tid < PSLOTS) {
       int gc[3];
-      if (!psample(B, sface, k, gc)) continue;
-      float w[8], u[8];
-      sample_w(a.Win, *cx.G, cx.blocks, cx.levmap, B.level - 1, gc, a.ph.gm1f, w, cx.err);
-      cons_from_prim<float>(w, a.ph.inv_gm1f, u);
-      float* e = tab + (slot * PSLOTS + k) * PSTRIDE;
+      if (psample(B, T.s, tid, gc)) {
+        float ws[8], u[8];
+        sample_w(a.Win, G, a.blocks, a.levmap, B.level - 1, gc, a.ph.gm1f, ws, a.err);
+        cons_from_prim<float>(ws, a.ph.inv_gm1f, u);
+        float* e = tab + tid * PSTRIDE;
 #pragma unroll
-      for (int v = 0; v < NV; v++) e[v] = u[v];
-      e[8] = w[7];
-      e[9] = w[1];
-      e[10] = w[2];
-      e[11] = w[3];
-    } else {
-      const int g = q - nsamp;
-      if (!((cmask >> (g >> 7)) & 1u)) fill_ghost<true, float>(a, cx, B, blk, g, sT);
+        for (int v = 0; v < NV; v++) e[v] = u[v];
+        e[8] = ws[7];
+        e[9] = ws[1];
+        e[10] = ws[2];
+        e[11] = ws[3];
+      }
     }
-  }
-  if (ncoarse) {
     __syncthreads();
-    for (int q = tid; q < ncoarse * 128; q += nthr) {
-      const int slot = q >> 7, local = q & 127;
-      unsigned m = cmask;
-      for (int r = 0; r < slot; r++) m &= m - 1;
-      const int sface = __ffs(m) - 1;
-      float w[8];
-      prolong_child_w(tab + slot * PSLOTS * PSTRIDE, sface, local, a.ph.gm1f, w);
-      const int t = NCELL + sface * 128 + local;
-#pragma unroll
-      for (int v = 0; v < NV; v++) sT[v * NTILE + t] = w[v];
-    }
+    prolong_child_w(tab, T.s, tid, a.ph.gm1f, w);
+  } else {
+    const int d = T.s >> 1, side = T.s & 1;
+    const int layer = tid & 1, ta = (tid >> 1) & 7, tb = tid >> 4;
+    const int c = side ? NC + layer : layer - 2;
+    const int i = d == 0 ? c : ta, j = d == 1 ? c : (d == 0 ? ta : tb), k = d == 2 ? c : tb;
+    int g[3] = {B.bi * NC + i, B.bj * NC + j, B.bk * NC + k};
+    sample_w(a.Win, G, a.blocks, a.levmap, B.level, g, a.ph.gm1f, w, a.err);
   }
+  float* o = a.gbuf + static_cast<int64_t>(T.slot) * (NV * 128) + tid;
+#pragma unroll
+  for (int v = 0; v < NV; v++) o[v * 128] = w[v];
 }
 
 // ---------------------------------------------------------------------------
@@ -1013,18 +1025,36 @@ __global__ void __launch_bounds__(STAGE_THREADS, MIXED ? 2 : 1) k_stage(const St
       // 1. interior by TMA bulk copies (one per variable), ghosts by threads
       if (tid == 0) {
         fence_proxy_async();
-        mbar_expect_tx(&bar, NV * NCELL * sizeof(R));
+        // mixed form: the ghost slabs of faces at resolution changes come
+        // precomputed, by bulk copies on the same barrier
+        unsigned amask = 0;
+        if constexpr (MIXED) {
+          if (a.gbuf) {
+#pragma unroll
+            for (int f = 0; f < 6; f++)
+              amask |= (B.ftype[f] == FACE_COARSER || B.ftype[f] == FACE_FINER ? 1u : 0u) << f;
+          }
+        }
+        mbar_expect_tx(&bar, NV * NCELL * sizeof(R) + __popc(amask) * (NV * 128 * sizeof(float)));
         const R* src = MIXED ? reinterpret_cast<const R*>(a.Win) : reinterpret_cast<const R*>(a.Uin);
         src += static_cast<int64_t>(blk) * (NV * NCELL);
 #pragma unroll
         for (int v = 0; v < NV; v++) bulk_g2s(sT + v * NTILE, src + v * NCELL, NCELL * sizeof(R), &bar);
+        if constexpr (MIXED) {
+          for (int f = 0; f < 6; f++) {
+            if (!((amask >> f) & 1u)) continue;
+            const float* g = a.gbuf + static_cast<int64_t>(B.rslot[f]) * (NV * 128);
+#pragma unroll
+            for (int v = 0; v < NV; v++) bulk_g2s(sT + v * NTILE + NCELL + f * 128, g + v * 128, 128 * sizeof(float), &bar);
+          }
+        }
         // the FP64 states the cell phase reads, on their way to L2 meanwhile
         const int64_t boff = static_cast<int64_t>(blk) * (NV * NCELL);
         const bool reads_ubase = a.kind < 3 && !(MIXED && a.kind == 0 && !a.last && !a.write_u_all);
         if (reads_ubase) prefetch_l2(a.Ubase + boff, NV * NCELL * sizeof(double));
         if (MIXED && a.kind == 1) prefetch_l2(a.Uin + boff, NV * NCELL * sizeof(double));
       }
-      if constexpr (MIXED) fill_ghosts_block_mixed(a, cx, B, blk, sT, sF, tid, STAGE_THREADS);
+      if constexpr (MIXED) fill_ghosts_block_mixed(a, cx, B, blk, sT, tid, STAGE_THREADS, false);
       else fill_ghosts_block<false, double>(a, cx, B, blk, sT, sF, tid, STAGE_THREADS);
       if (!mbar_wait_bounded(&bar, parity, a.err)) mbar_wait_bounded(&bar, parity, a.err);
       parity ^= 1u;
@@ -1752,7 +1782,7 @@ __global__ void k_debug_fill(const StageArgs a, int b0, int nb, double* T) {
 }
 
 // The same for the mixed form: FP32 primitives from W.
-constexpr size_t kDebugFillWSmem = sizeof(float) * (NV * NTILE + 3 * PSLOTS * PSTRIDE);
+constexpr size_t kDebugFillWSmem = sizeof(float) * NV * NTILE;
 __global__ void k_debug_fill_w(const StageArgs a, int b0, int nb, double* T) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float* sT = reinterpret_cast<float*>(smem_raw);
@@ -1761,7 +1791,7 @@ __global__ void k_debug_fill_w(const StageArgs a, int b0, int nb, double* T) {
   GhostCtx cx{&a.grids[B.grid], a.blocks, a.levmap, a.Uin, a.err};
   for (int e = threadIdx.x; e < NV * NCELL; e += blockDim.x)
     sT[(e / NCELL) * NTILE + (e % NCELL)] = a.Win[static_cast<int64_t>(blk) * NV * NCELL + e];
-  fill_ghosts_block_mixed(a, cx, B, blk, sT, sT + NV * NTILE, threadIdx.x, blockDim.x);
+  fill_ghosts_block_mixed(a, cx, B, blk, sT, threadIdx.x, blockDim.x, true);
   __syncthreads();
   write_debug_tile(sT, nb, T);
 }
@@ -1850,6 +1880,11 @@ cudaError_t launch_cfl_dt(bool mixed, const double* U, const float* Wt, const Gr
                           double* dtc, double cfl, cudaStream_t st) {
   if (mixed) k_cfl<true><<<nb, NCELL, 0, st>>>(U, Wt, grids, blocks, ph, b0, smax, dtc, cfl);
   else k_cfl<false><<<nb, NCELL, 0, st>>>(U, Wt, grids, blocks, ph, b0, smax, dtc, cfl);
+  return cudaGetLastError();
+}
+cudaError_t launch_amr_ghosts(const StageArgs& a, const GhostTask* tasks, int ntasks, cudaStream_t st) {
+  if (ntasks <= 0) return cudaSuccess;
+  k_amr_ghosts<<<ntasks, 128, 0, st>>>(a, tasks);
   return cudaGetLastError();
 }
 cudaError_t launch_reflux(bool mixed, const StageArgs& a, const RefluxTask* tasks, const int32_t* rblocks, int nrb,
