@@ -16,7 +16,11 @@ constexpr int NFACE = 576;     // faces per block per direction (9 x 8 x 8)
 constexpr int NGHOST = 768;    // face-slab ghost cells (6 x 2 x 64)
 constexpr int NTILE = 1280;    // interior + face-slab ghosts
 constexpr int MAXLEV = 14;
-constexpr int STAGE_THREADS = 384;  // two threads per grid line, three directions
+constexpr int FACE_THREADS = 384;   // face phase: two threads per grid line, three directions
+// stage CTA threads per form: 384 both (2 CTAs per SM at 80 registers in the
+// mixed form, 1 at 168 in FP64).  512 threads (one per cell in the cell phase)
+// measured slower in the mixed form: 64 registers spill in the face phase.
+constexpr int STAGE_THREADS_MIXED = 384, STAGE_THREADS_FP64 = 384;
 
 enum FaceType : int32_t { FACE_SAME = 0, FACE_COARSER = 1, FACE_FINER = 2, FACE_OUTFLOW = 3, FACE_INFLOW = 4 };
 enum B0Mode : int32_t { B0_NONE = 0, B0_UNIFORM = 1, B0_DIPOLE = 2, B0_LINEAR = 3 };

@@ -943,6 +943,7 @@ __global__ void __launch_bounds__(128) k_amr_ghosts(const StageArgs a, const Gho
 template <bool MIXED>
 struct StageCfg {
   using R = typename std::conditional<MIXED, float, double>::type;
+  static constexpr int THREADS = MIXED ? STAGE_THREADS_MIXED : STAGE_THREADS_FP64;
   static constexpr int NFC = 9;  // per face: 8 fluxes and the face-averaged normal B1
   static constexpr size_t SMEM = sizeof(R) * (NV * NTILE + 3 * NFC * NFACE);
 };
@@ -967,15 +968,17 @@ __device__ __forceinline__ void b0_face(const PhysDev& ph, int d, int i, int j, 
   b0_at<R>(ph, x, B0);
 }
 
-// The fused stage.  Per block: (1) interior by TMA, face-slab ghosts by
-// threads; (2) FP64 form: primitives in place; (3) faces of all three
-// directions at once, two threads per grid line (faces 0-4 and 5-8), each
-// sliding a window along its line so that every cell is loaded and every
-// limited slope computed once; (4) per cell: flux differences x, y, z, the
-// sources, the update and (last stage) the CFL bound.
+// The fused stage (StageCfg::THREADS threads).  Per block: (1) interior by TMA, face-slab
+// ghosts by threads; (2) FP64 form: primitives in place; (3) faces of all
+// three directions at once on the first FACE_THREADS threads, two per grid
+// line (faces 0-4 and 5-8), each sliding a window along its line so that
+// every cell is loaded and every limited slope computed once; (4) per cell:
+// flux differences x, y, z, the sources, the update and (last stage) the CFL
+// bound.
 template <bool MIXED, int LIM, bool HAS_B0, bool LRN>
-__global__ void __launch_bounds__(STAGE_THREADS, MIXED ? 2 : 1) k_stage(const StageArgs a) {
+__global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1) k_stage(const StageArgs a) {
   using R = typename StageCfg<MIXED>::R;
+  constexpr int STAGE_THREADS = StageCfg<MIXED>::THREADS;
   constexpr int NFC = StageCfg<MIXED>::NFC;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   R* sT = reinterpret_cast<R*>(smem_raw);       // [8][1280] tile
@@ -1441,7 +1444,7 @@ __global__ void __launch_bounds__(STAGE_THREADS, MIXED ? 2 : 1) k_stage(const St
         return any_bad;
       };
 
-      faces(true);
+      if (tid < FACE_THREADS) faces(true);
       __syncthreads();
       if (a.kind >= 3) continue;  // features / dumps only
       if constexpr (LRN) {
@@ -1450,7 +1453,7 @@ __global__ void __launch_bounds__(STAGE_THREADS, MIXED ? 2 : 1) k_stage(const St
         // with the plain Rusanov flux
         if (a.learned && a.kind < 2) {
           if (__syncthreads_or(cells(false))) {
-            faces(false);
+            if (tid < FACE_THREADS) faces(false);
             __syncthreads();
             if (tid == 0) atomicAdd(&a.err[2], 1);
           }
@@ -1841,10 +1844,10 @@ cudaError_t stage_setup(int occ[2]) {
     e = cudaFuncSetAttribute(k_debug_fill_w, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(kDebugFillWSmem));
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], stage_fn<false>(0, false), STAGE_THREADS,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], stage_fn<false>(0, false), StageCfg<false>::THREADS,
                                                       StageCfg<false>::SMEM);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], stage_fn<true>(0, false), STAGE_THREADS,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], stage_fn<true>(0, false), StageCfg<true>::THREADS,
                                                       StageCfg<true>::SMEM);
   return e;
 }
@@ -1852,8 +1855,8 @@ cudaError_t stage_setup(int occ[2]) {
 cudaError_t launch_stage_kernel(bool mixed, int grid, cudaStream_t st, const StageArgs& a) {
   const bool b0 = a.ph.b0 != B0_NONE;
   const bool lrn = a.learned || a.kind >= 3;
-  if (mixed) stage_fn<true>(a.ph.limiter, b0, lrn)<<<grid, STAGE_THREADS, StageCfg<true>::SMEM, st>>>(a);
-  else stage_fn<false>(a.ph.limiter, b0, lrn)<<<grid, STAGE_THREADS, StageCfg<false>::SMEM, st>>>(a);
+  if (mixed) stage_fn<true>(a.ph.limiter, b0, lrn)<<<grid, StageCfg<true>::THREADS, StageCfg<true>::SMEM, st>>>(a);
+  else stage_fn<false>(a.ph.limiter, b0, lrn)<<<grid, StageCfg<false>::THREADS, StageCfg<false>::SMEM, st>>>(a);
   return cudaGetLastError();
 }
 
