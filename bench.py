@@ -43,7 +43,7 @@ BYTES_PER_CELL_UPDATE = 320  # FP64 state: stage 1 reads U^n, writes U*; stage 2
 # in profiles/ (None until a capture of the current kernel source exists).
 NCU_TRAFFIC = {
     # precision: (DRAM bytes per cell per launch, mean of the two stages, sha256 of bats_stage.cu at capture)
-    "mixed": (116.9, "1c4ab7d28e40f6eaebcc3e2793ddcb062c2415151b1078e8fa4d99ac73fc7cad"),
+    "mixed": (121.2, "65609c2a75f382f6f83ecd55e26b241896f377a6b1b549200332f211bffbfbc6"),
 }
 
 
@@ -450,7 +450,8 @@ def main():
                        "cfl": cfl},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "k_stage<%s>" % ("true" if prec == bats.BATS_MIXED else "false"),
+                         "kernel": ("k_stage<true> with its ghost pre-pass k_amr_ghosts" if prec == bats.BATS_MIXED
+                                    else "k_stage<false>"),
                          "peak_source": peak_kind, "bytes_per_launch": alg_bytes,
                          "mean_launch_ms": per_launch_ms},
             "cpu_baseline": cpu,

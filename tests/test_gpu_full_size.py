@@ -1,0 +1,49 @@
+"""The benchmark's workload at full size (64 grids, 60,194 blocks, 30.8 M
+cells) in the launch form the benchmark times (one non-persistent launch per
+stage, whole steps replayed from a CUDA graph): one step of the whole batch on
+the GPU, checked grid by grid against the oracle on a sample of the grids (the
+largest, the smallest and two others), in both precisions."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2501_06717_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def grids():
+    return W.batched_grids(processes=min(16, os.cpu_count() or 1))
+
+
+def _scaled(g, o):
+    g = np.asarray(g).reshape(8, -1)
+    o = np.asarray(o).reshape(8, -1)
+    s = np.abs(o).max(1)
+    s[1:4] = s[1:4].max()
+    s[4:7] = s[4:7].max()
+    s = np.where(s > 0, s, 1.0)
+    return np.abs(g - o).max(1) / s
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 1e-5), (0, 1e-12)])
+def test_full_batched_workload_sampled_against_the_oracle(grids, prec, tol):
+    from paper_2501_06717_gb300 import bats as B
+    assert sum(p.nb for p in grids) == 60194
+    sizes = np.array([p.nb for p in grids])
+    sample = sorted({int(np.argmax(sizes)), int(np.argmin(sizes)), 17, 41})
+    with B.Solver(grids, precision=prec) as s:
+        s.set_states()
+        s.set_launch(0, 1, 0, 1)
+        s.step(1, 0.8)
+        got = {g: (s.get_state(g), s.time(g)) for g in sample}
+    for g in sample:
+        p = grids[g]
+        Uo, dto, to = O.run(p, p.U0, 1, cfl=p.cfl)
+        err = _scaled(got[g][0], Uo)
+        print("grid", g, "blocks", p.nb, "scaled error per variable", err)
+        assert err.max() <= tol, (g, err)
+        assert got[g][1] == pytest.approx(to, rel=1e-6 if prec == 1 else 1e-13)
