@@ -159,6 +159,15 @@ __device__ __forceinline__ R mc_(R a, R b) {
   return r;
 }
 // kind 0 minmod, 1 MC, 2 none (first order: piecewise-constant faces)
+// FP32: the same selection by the sign bits (2|a|, 2|b| and |a+b|/2 when the
+// signs agree, else 0).
+template <>
+__device__ __forceinline__ float mc_<float>(float a, float b) {
+  const uint32_t ua = __float_as_uint(a), ub = __float_as_uint(b);
+  const float m = fminf(fminf(2.f * fabsf(a), 2.f * fabsf(b)), fabsf(0.5f * (a + b)));
+  const float r = __uint_as_float((__float_as_uint(m) & 0x7fffffffu) | (ua & 0x80000000u));
+  return static_cast<int32_t>(ua ^ ub) < 0 ? 0.f : r;
+}
 template <class R>
 __device__ __forceinline__ R limit_(int kind, R a, R b) {
   return kind == 2 ? R(0) : (kind == 1 ? mc_(a, b) : minmod_(a, b));
