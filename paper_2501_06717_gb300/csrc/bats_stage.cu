@@ -1114,22 +1114,32 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1) k_sta
       auto faces = [&](const bool corr) {
           auto cidx = [&](int c) { return c < 0 ? flo + (c + 2) : (c >= NC ? fhi + (c - NC) : fibase + c * fstride); };
           const int f0 = fhalf ? 5 : 0, nf = fhalf ? 4 : 5;
+          // window along the line.  Plain: the cell W0, the difference d = W0 - W-1
+          // and the left state WL of the next face, W-1 + s-1 / 2 (each difference
+          // and slope formed once).  Learned: the cells f-2..f, kept for the
+          // network's inputs.
           R Wm1[8], W0[8], sm1[8];
-          R Wm2[8];  // kept along the line only for the network's inputs
+          R Wm2[8];
           load_rot<R>(sT, rot, cidx(f0 - 2), Wm2);
           load_rot<R>(sT, rot, cidx(f0 - 1), Wm1);
           load_rot<R>(sT, rot, cidx(f0), W0);
+          R d[8], WL[8];
 #pragma unroll
-          for (int v = 0; v < NV; v++) sm1[v] = limit_<R>(LIM, Wm1[v] - Wm2[v], W0[v] - Wm1[v]);
+          for (int v = 0; v < NV; v++) {
+            const R dm = Wm1[v] - Wm2[v];
+            d[v] = W0[v] - Wm1[v];
+            sm1[v] = limit_<R>(LIM, dm, d[v]);
+            WL[v] = Wm1[v] + R(0.5) * sm1[v];
+          }
 #pragma unroll 1
           for (int k = 0; k < nf; k++) {
             const int f = f0 + k;
-            R Wp[8], WL[8], WR[8], s0[8];
+            R Wp[8], WR[8], s0[8], dn[8];
             load_rot<R>(sT, rot, cidx(f + 1), Wp);
 #pragma unroll
             for (int v = 0; v < NV; v++) {
-              s0[v] = limit_<R>(LIM, W0[v] - Wm1[v], Wp[v] - W0[v]);
-              WL[v] = Wm1[v] + R(0.5) * sm1[v];
+              dn[v] = Wp[v] - W0[v];
+              s0[v] = limit_<R>(LIM, d[v], dn[v]);
               WR[v] = W0[v] - R(0.5) * s0[v];
             }
             R B0f[3] = {R(0), R(0), R(0)}, B0r[3];
@@ -1217,12 +1227,16 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1) k_sta
                 }
               }
             }
+            const R bnf = R(0.5) * (WL[4] + WR[4]);  // face-averaged normal B1 (Powell)
 #pragma unroll
             for (int v = 0; v < NV; v++) {
-              Wm2[v] = Wm1[v];
-              sm1[v] = s0[v];
-              Wm1[v] = W0[v];
+              if constexpr (LRN) {
+                Wm2[v] = Wm1[v];
+                Wm1[v] = W0[v];
+              }
+              WL[v] = W0[v] + R(0.5) * s0[v];
               W0[v] = Wp[v];
+              d[v] = dn[v];
             }
             if (a.kind >= 3) continue;
             fcol[0 * NFACE + fi] = Fr[0];
@@ -1233,7 +1247,7 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1) k_sta
             fcol[(4 + fd1) * NFACE + fi] = Fr[5];
             fcol[(4 + fd2) * NFACE + fi] = Fr[6];
             fcol[7 * NFACE + fi] = Fr[7];
-            fcol[8 * NFACE + fi] = R(0.5) * (WL[4] + WR[4]);
+            fcol[8 * NFACE + fi] = bnf;
             // refluxing: the block-face fluxes of faces at resolution changes
             if (a.freg && (f == 0 || f == NC)) {
               const int sl = B.rslot[2 * fd + (f == NC ? 1 : 0)];
