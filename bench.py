@@ -394,17 +394,18 @@ def main():
     tr = NCU_TRAFFIC.get(args.precision)
     traffic = tr[0] * cells if (tr and tr[1] == _kernel_sha()) else None
 
-    # end to end through the public API with host buffers: per step, the
-    # state goes in from pinned host memory and comes back out
-    host = [torch.from_numpy(np.ascontiguousarray(p.U0)).pin_memory() for p in problems] if args.e2e_steps else []
+    # end to end through the public API with host buffers: per step, every
+    # grid's state goes in from pinned host memory and comes back out (one
+    # transfer each way for the whole batch)
+    host = None
+    if args.e2e_steps:
+        host = torch.from_numpy(np.concatenate([np.ascontiguousarray(p.U0).reshape(-1) for p in problems])).pin_memory()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
-        for g in range(len(problems)):
-            bats.bats_set_state(solver.h, g, host[g])
+        bats.bats_set_states(solver.h, host)
         solver.step(1, cfl)
-        for g in range(len(problems)):
-            bats.bats_get_state(solver.h, g, host[g])
+        bats.bats_get_states(solver.h, host)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     state_bytes = cells * 8 * 8

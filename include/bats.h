@@ -144,6 +144,14 @@ int bats_set_state(bats_t* h, int grid, const double* U, size_t n);
 /* Copy the state of grid `grid` into U (host or device, n doubles). */
 int bats_get_state(bats_t* h, int grid, double* U, size_t n);
 
+/* All grids at once: U holds every grid's state back to back in grid order,
+ * each in the layout above (n = 8 * 512 * total blocks doubles), host or
+ * device.  One transfer each way instead of one per grid; the effect is that
+ * of bats_set_state / bats_get_state on every grid (elapsed times reset to 0,
+ * CFL bounds recomputed).  Both return after the copy has completed. */
+int bats_set_states(bats_t* h, const double* U, size_t n);
+int bats_get_states(bats_t* h, double* U, size_t n);
+
 /* Advance every grid by n steps of the two-stage scheme (Section 5.2) with
  * dt = cfl / max over non-body cells of sum_d (|u_d| + c_f,d)/dx_d, per grid,
  * from the state at the start of each step.  Each stage fills ghost cells,

@@ -90,6 +90,8 @@ def lib():
     L.bats_last_error.restype = ctypes.c_char_p
     L.bats_set_state.argtypes = [vp, ctypes.c_int, dp, ctypes.c_size_t]
     L.bats_get_state.argtypes = [vp, ctypes.c_int, dp, ctypes.c_size_t]
+    L.bats_set_states.argtypes = [vp, dp, ctypes.c_size_t]
+    L.bats_get_states.argtypes = [vp, dp, ctypes.c_size_t]
     L.bats_step.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
     L.bats_step_dt.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
     L.bats_get_dt.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
@@ -215,6 +217,17 @@ def bats_set_state(h, grid, U):
 def bats_get_state(h, grid, out):
     p, n = _ptr_and_size(out)
     _check(h, lib().bats_get_state(h, int(grid), p, n))
+    return out
+
+
+def bats_set_states(h, U):
+    p, n = _ptr_and_size(U)
+    _check(h, lib().bats_set_states(h, p, n))
+
+
+def bats_get_states(h, out):
+    p, n = _ptr_and_size(out)
+    _check(h, lib().bats_get_states(h, p, n))
     return out
 
 

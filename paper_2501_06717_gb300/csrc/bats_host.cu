@@ -366,6 +366,17 @@ bool is_device_ptr(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Page-locked host memory the device can address directly (kernels then move
+// it across the host link themselves, fused with the layout change).
+const void* device_view_of_pinned(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 void free_all(bats_t* h) {
   if (h->graph) cudaGraphExecDestroy(h->graph);
   cudaFree(h->grids_d);
@@ -835,6 +846,54 @@ int bats_get_state(bats_t* h, int grid, double* U, size_t n) {
   double* dst = dev ? U : h->staging;
   CK(h, launch_to_external(h->U, dst, G.block0, G.nb, h->stream));
   if (!dev) CK(h, cudaMemcpyAsync(U, h->staging, need * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return BATS_OK;
+}
+
+int bats_set_states(bats_t* h, const double* U, size_t n) {
+  if (!h) return BATS_ERR_INVALID_ARG;
+  const size_t need = static_cast<size_t>(h->nbt) * NV * NCELL;
+  if (!U || n != need) return fail(h, BATS_ERR_INVALID_ARG, "state size mismatch: expected " + std::to_string(need));
+  // device or page-locked host memory: the layout change reads it directly;
+  // pageable host memory: staged through the second state buffer, free
+  // between steps
+  const double* src = U;
+  if (!is_device_ptr(U)) {
+    const void* view = device_view_of_pinned(U);
+    if (view) {
+      src = static_cast<const double*>(view);
+    } else {
+      CK(h, cudaMemcpyAsync(h->U1, U, need * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+      src = h->U1;
+    }
+  }
+  for (int g = 0; g < h->ngrids; g++) {
+    const GridDev& G = h->grids_h[g];
+    CK(h, launch_to_internal(src + static_cast<size_t>(G.block0) * NV * NCELL, h->U, G.block0, G.nb, h->stream));
+  }
+  if (h->ph.precision == BATS_MIXED)
+    CK(h, launch_prim_mixed(h->U, h->W, 0, h->nbt, static_cast<float>(h->ph.gm1), h->stream));
+  for (int g = 0; g < h->ngrids; g++) {
+    int rc = launch_cfl(h, g);
+    if (rc) return rc;
+  }
+  CK(h, cudaMemsetAsync(h->t, 0, sizeof(double) * h->ngrids, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return BATS_OK;
+}
+
+int bats_get_states(bats_t* h, double* U, size_t n) {
+  if (!h) return BATS_ERR_INVALID_ARG;
+  const size_t need = static_cast<size_t>(h->nbt) * NV * NCELL;
+  if (!U || n != need) return fail(h, BATS_ERR_INVALID_ARG, "state size mismatch: expected " + std::to_string(need));
+  const bool dev = is_device_ptr(U);
+  double* pinned = dev ? nullptr : static_cast<double*>(const_cast<void*>(device_view_of_pinned(U)));
+  double* dst = dev ? U : (pinned ? pinned : h->U1);
+  for (int g = 0; g < h->ngrids; g++) {
+    const GridDev& G = h->grids_h[g];
+    CK(h, launch_to_external(h->U, dst + static_cast<size_t>(G.block0) * NV * NCELL, G.block0, G.nb, h->stream));
+  }
+  if (!dev && !pinned) CK(h, cudaMemcpyAsync(U, h->U1, need * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
   return BATS_OK;
 }

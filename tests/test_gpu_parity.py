@@ -339,3 +339,35 @@ def test_graph_replay_of_many_steps(B):
         s.step(60, 0.8)
         assert np.array_equal(s.get_state(0), ref)
         assert s.launch_count() == 4 * 60
+
+
+def test_batched_state_transfer_equals_per_grid_transfer(B):
+    """bats_set_states / bats_get_states over the whole batch (host and
+    device buffers) act like bats_set_state / bats_get_state on every grid."""
+    import torch
+    probs = [_amr_problem(9, True), W.orszag_tang(), _amr_problem(10, False)]
+    flat = np.concatenate([np.ascontiguousarray(p.U0).reshape(-1) for p in probs])
+    for prec in (B.BATS_FP64, B.BATS_MIXED):
+        with B.Solver(probs, precision=prec) as s:
+            s.set_states()
+            s.step(2, 0.8)
+            ref = [s.get_state(g) for g in range(3)]
+        with B.Solver(probs, precision=prec) as s:
+            B.bats_set_states(s.h, flat.copy())
+            s.step(2, 0.8)
+            out = B.bats_get_states(s.h, np.zeros_like(flat))
+            dev = torch.zeros(flat.size, dtype=torch.float64, device="cuda")
+            B.bats_get_states(s.h, dev)
+            assert np.array_equal(dev.cpu().numpy(), out)
+            pinned = torch.zeros(flat.size, dtype=torch.float64).pin_memory()
+            B.bats_get_states(s.h, pinned)
+            assert np.array_equal(pinned.numpy(), out)
+            B.bats_set_states(s.h, dev)
+            assert np.array_equal(np.concatenate([s.get_state(g).reshape(-1) for g in range(3)]), out)
+            B.bats_set_states(s.h, pinned)
+            assert np.array_equal(np.concatenate([s.get_state(g).reshape(-1) for g in range(3)]), out)
+        off = 0
+        for g, p in enumerate(probs):
+            n = p.U0.size
+            assert np.array_equal(out[off:off + n].reshape(p.U0.shape), ref[g]), (prec, g)
+            off += n
