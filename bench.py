@@ -171,8 +171,10 @@ def run_reference(args, rank, world):
 
 def learned_form_summary(stream, steps=32):
     """Blast at 1x (120 blocks) with the trained network against the plain
-    scheme at 1x and 2x (960 blocks), FP64 state, fixed dt; times from CUDA
-    events around graph replays of `steps` coarse steps (2 * steps fine)."""
+    scheme at 1x and 2x (960 blocks), fixed dt, FP64 and mixed forms; times
+    from CUDA events around graph replays of `steps` coarse steps (2 * steps
+    fine).  Errors are against the plain 2x run of the same precision,
+    restricted to 1x."""
     import torch
     from paper_2501_06717_gb300 import bats, learn
     t0 = time.perf_counter()
@@ -180,10 +182,11 @@ def learned_form_summary(stream, steps=32):
     P, hist = learn.train(X, Y, epochs=20, lr=2e-3)
     t_train = time.perf_counter() - t0
     e_plain, e_learn = learn.evaluate(P, nsteps=16)
+    e_plain_m, e_learn_m = learn.evaluate(P, nsteps=16, precision=bats.BATS_MIXED)
     coarse, fine = W.blast(), W.blast(resolution=2)
 
-    def timed(prob, params, nsteps, dt):
-        with bats.Solver(prob, stream=stream, persistent=1, use_graph=1) as s:
+    def timed(prob, params, nsteps, dt, precision):
+        with bats.Solver(prob, precision=precision, stream=stream, persistent=1, use_graph=1) as s:
             if params is not None:
                 s.set_mlp(params)
             s.set_state(0, prob.U0)
@@ -195,21 +198,23 @@ def learned_form_summary(stream, steps=32):
             s.step_dt(nsteps, dt)
             e1.record(stream)
             torch.cuda.synchronize()
-            return e0.elapsed_time(e1)
+            return e0.elapsed_time(e1) / steps
 
     with bats.Solver(coarse) as s:
         s.set_state(0, coarse.U0)
         dtc = 0.5 * s.dt(0, 0.8)
-    ms_learn = timed(coarse, P, steps, dtc)
-    ms_plain1 = timed(coarse, None, steps, dtc)
-    ms_plain2 = timed(fine, None, 2 * steps, 0.5 * dtc)
+    ms = {}
+    for name, prec in (("fp64", bats.BATS_FP64), ("mixed", bats.BATS_MIXED)):
+        ms[name] = {"learned_1x": timed(coarse, P, steps, dtc, prec),
+                    "plain_1x": timed(coarse, None, steps, dtc, prec),
+                    "plain_2x_two_fine_steps": timed(fine, None, 2 * steps, 0.5 * dtc, prec)}
     return {"workload": "spherical blast: 120 blocks (1x) with the trained network vs plain 1x and plain 2x "
-                        "(960 blocks), FP64 state, fixed dt, CUDA graph",
+                        "(960 blocks), fixed dt, CUDA graph",
             "pairs": int(X.shape[0]), "train_s": t_train, "loss_first_last_epoch": [hist[0], hist[-1]],
-            "error_vs_restricted_2x": {"plain_1x": e_plain, "learned_1x": e_learn},
-            "ms_per_coarse_step": {"learned_1x": ms_learn / steps, "plain_1x": ms_plain1 / steps,
-                                   "plain_2x_two_fine_steps": ms_plain2 / steps},
-            "cell_updates_per_s_learned_1x": coarse.ncells * steps / (ms_learn * 1e-3)}
+            "error_vs_restricted_2x": {"plain_1x": e_plain, "learned_1x": e_learn,
+                                       "plain_1x_mixed": e_plain_m, "learned_1x_mixed": e_learn_m},
+            "ms_per_coarse_step": ms,
+            "cell_updates_per_s_learned_1x": {k: coarse.ncells / (v["learned_1x"] * 1e-3) for k, v in ms.items()}}
 
 
 # --------------------------------------------------------------------------
