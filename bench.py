@@ -43,7 +43,7 @@ BYTES_PER_CELL_UPDATE = 320  # FP64 state: stage 1 reads U^n, writes U*; stage 2
 # in profiles/ (None until a capture of the current kernel source exists).
 NCU_TRAFFIC = {
     # precision: (DRAM bytes per cell per launch, mean of the two stages, sha256 of bats_stage.cu at capture)
-    "mixed": (121.0, "f9a459215097bb24131f84287402b76f7196add10fbbba352bfa3799b7b78619"),
+    "mixed": (121.0, "9564eefe595977c05b62f084219f95b1d332aa8c32176d481eccab14dee5c3ea"),
 }
 
 
