@@ -22,7 +22,8 @@
  *    the conservative variables (prolongation).
  *  - Primitive recovery p = (gamma-1)(e1 - m.u/2 - B1.B1/2) (Eq. 5).
  *  - Limited linear reconstruction of primitives (minmod or MC).
- *  - Rusanov flux of the split-field ideal-MHD fluxes of Eqs. 1-4.
+ *  - Rusanov flux of the split-field ideal-MHD fluxes of Eqs. 1-4 (the HLL
+ *    two-state flux as an option).
  *  - Powell 8-wave source terms (right-hand sides of Eqs. 2-4) and the
  *    split-field B0 correction.
  *  - Conservative update; two-stage second-order time stepping (Section 5.2
@@ -55,6 +56,7 @@ enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_INFLOW = 2 };
 enum { LIM_MINMOD = 0, LIM_MC = 1, LIM_NONE = 2 };
 enum { RK_MIDPOINT = 0, RK_SSP2 = 1, RK_EULER = 2 };
 enum { B0_NONE = 0, B0_UNIFORM = 1, B0_DIPOLE = 2, B0_LINEAR = 3 };
+enum { FLUX_RUSANOV = 0, FLUX_HLL = 1 };
 enum { OR_OK = 0, OR_EINVAL = -1, OR_EUNBALANCED = -2, OR_ENOMEM = -3 };
 enum { GT_INTERIOR = 0, GT_COPY = 1, GT_RESTRICT = 2, GT_PROLONG = 3, GT_INFLOW = 4 };
 
@@ -81,6 +83,7 @@ typedef struct {
   const double* mlp;     /* MLP_NPARAM weights (W1,b1,W2,b2,W3,b3), row-major [out][in] */
   int32_t local_dt;      /* 1 = local time stepping: each cell its own dt (steady-state runs) */
   int32_t reflux;        /* 1 = conservative flux correction at resolution changes */
+  int32_t flux;          /* FLUX_RUSANOV, or FLUX_HLL (two-state HLL, Davis wave-speed bounds) */
 } or_desc;
 
 typedef struct {
@@ -272,6 +275,8 @@ static int grid_init(grid_t* G, const or_desc* d, double dummy_unused) {
   G->d = d;
   if (!d || !d->leaves || d->n_leaves <= 0) return OR_EINVAL;
   if (!(d->gamma > 1.0)) return OR_EINVAL;
+  if (d->flux < FLUX_RUSANOV || d->flux > FLUX_HLL) return OR_EINVAL;
+  if (d->flux != FLUX_RUSANOV && d->learned) return OR_EINVAL; /* the correction is defined on Rusanov */
   for (int a = 0; a < 3; a++) {
     if (d->root[a] <= 0 || !(d->hi[a] > d->lo[a])) return OR_EINVAL;
     int lo_p = d->bc[2 * a] == BC_PERIODIC, hi_p = d->bc[2 * a + 1] == BC_PERIODIC;
@@ -611,8 +616,39 @@ static int in_body(const or_desc* d, const double x[3]) {
   return x[0] * x[0] + x[1] * x[1] + x[2] * x[2] < d->body_r * d->body_r;
 }
 
+/* Numerical flux from the two face states' physical fluxes F, states U,
+ * normal speeds un and fast speeds cf.
+ *  Rusanov: F = (F_L + F_R)/2 - cmax (U_R - U_L)/2,
+ *           cmax = max(|un_L| + cf_L, |un_R| + cf_R).
+ *  HLL (Harten, Lax and van Leer 1983), with the wave-speed bounds of Davis
+ *  (1988) S_L = min(un_L - cf_L, un_R - cf_R), S_R = max(un_L + cf_L,
+ *  un_R + cf_R): F = F_L where S_L >= 0, F = F_R where S_R <= 0, else
+ *  F = (S_R F_L - S_L F_R + S_L S_R (U_R - U_L)) / (S_R - S_L).
+ *  The paper's solver uses the Linde flux, which adds a contact-restoring
+ *  term to HLL; it is not given in the paper, so HLL stands in for it. */
+static void numerical_flux(int kind, const double FL[NV], const double FR[NV], const double UL[NV],
+                           const double UR[NV], double unL, double unR, double cfL, double cfR,
+                           double F[NV]) {
+  if (kind == FLUX_HLL) {
+    double SL = fmin(unL - cfL, unR - cfR);
+    double SR = fmax(unL + cfL, unR + cfR);
+    if (SL >= 0.0) {
+      for (int v = 0; v < NV; v++) F[v] = FL[v];
+    } else if (SR <= 0.0) {
+      for (int v = 0; v < NV; v++) F[v] = FR[v];
+    } else {
+      for (int v = 0; v < NV; v++)
+        F[v] = (SR * FL[v] - SL * FR[v] + SL * SR * (UR[v] - UL[v])) / (SR - SL);
+    }
+    return;
+  }
+  double aL = fabs(unL) + cfL, aR = fabs(unR) + cfR;
+  double cmax = aL > aR ? aL : aR;
+  for (int v = 0; v < NV; v++) F[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * cmax * (UR[v] - UL[v]);
+}
+
 /* Face flux between tile cells m1 = p0 - e_dir and p0 (tile coords 0..11),
- * with the limited reconstruction of primitives, the Rusanov flux and, when
+ * with the limited reconstruction of primitives, the numerical flux and, when
  * learned, the clipped MLP correction. */
 static void face_flux(const grid_t* G, int dir, const double* Wt /* [12^3][8] */, int ti, int tj, int tk,
                       const double B0f[3], face_t* out) {
@@ -635,7 +671,7 @@ static void face_flux(const grid_t* G, int dir, const double* Wt /* [12^3][8] */
   phys_flux(d, dir, WR, B0f, FR, UR, &unR, &cfR);
   double aL = fabs(unL) + cfL, aR = fabs(unR) + cfR;
   double cmax = aL > aR ? aL : aR;
-  for (int v = 0; v < NV; v++) out->F[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * cmax * (UR[v] - UL[v]);
+  numerical_flux(d->flux, FL, FR, UL, UR, unL, unR, cfL, cfR, out->F);
   if (d->learned && d->mlp) {
     double Ws[32], x[MLP_IN], h1[MLP_H], h2[MLP_H], y[MLP_OUT], sc[MLP_OUT];
     memcpy(Ws, Wm2, 64); memcpy(Ws + 8, Wm1, 64); memcpy(Ws + 16, Wp0, 64); memcpy(Ws + 24, Wp1, 64);
@@ -1160,3 +1196,13 @@ void or_cons_from_prim(double gamma, const double* W, double* U, long n) {
 void or_b0_at(const or_desc* d, const double x[3], double B0[3]) { b0_at(d, x, B0); }
 
 double or_limiter(int kind, double a, double b) { return limiter(kind, a, b); }
+
+/* The numerical flux (d->flux) through a face along dir between the face
+ * states WL, WR (primitive) with B0 at the face. */
+void or_numerical_flux(const or_desc* d, int dir, const double WL[NV], const double WR[NV], const double B0[3],
+                       double F[NV]) {
+  double FL[NV], FR[NV], UL[NV], UR[NV], unL, unR, cfL, cfR;
+  phys_flux(d, dir, WL, B0, FL, UL, &unL, &cfL);
+  phys_flux(d, dir, WR, B0, FR, UR, &unR, &cfR);
+  numerical_flux(d->flux, FL, FR, UL, UR, unL, unR, cfL, cfR, F);
+}

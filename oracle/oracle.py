@@ -64,6 +64,7 @@ class _Desc(ctypes.Structure):
         ("mlp", ctypes.POINTER(ctypes.c_double)),
         ("local_dt", ctypes.c_int32),
         ("reflux", ctypes.c_int32),
+        ("flux", ctypes.c_int32),
     ]
 
 
@@ -95,6 +96,7 @@ def lib():
         _lib.or_b0_at.argtypes = [D, dp, dp]
         _lib.or_limiter.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double]
         _lib.or_limiter.restype = ctypes.c_double
+        _lib.or_numerical_flux.argtypes = [D, ctypes.c_int, dp, dp, dp, dp]
         _lib.or_num_threads.restype = ctypes.c_int
         _lib.or_set_threads.argtypes = [ctypes.c_int]
         _lib.or_mlp_forward.argtypes = [dp, dp, dp, dp, dp]
@@ -147,6 +149,7 @@ class _Bound:
         d.no_fallback = int(getattr(prob, "no_fallback", 0) or 0)
         d.local_dt = int(getattr(prob, "local_dt", 0) or 0)
         d.reflux = int(getattr(prob, "reflux", 0) or 0)
+        d.flux = int(getattr(prob, "flux", 0) or 0)
         self.desc = d
         self.nb = d.n_leaves
 
@@ -293,8 +296,16 @@ def set_threads(n):
     lib().or_set_threads(int(n))
 
 
-def set_threads(n):
-    lib().or_set_threads(int(n))
+def numerical_flux(prob, direction, WL, WR, B0=(0.0, 0.0, 0.0)):
+    """The numerical flux (prob.flux: Rusanov or HLL) through a face along
+    `direction` between the primitive face states WL and WR."""
+    b = _Bound(prob)
+    WL = np.ascontiguousarray(WL, dtype=np.float64).reshape(8)
+    WR = np.ascontiguousarray(WR, dtype=np.float64).reshape(8)
+    B0 = np.ascontiguousarray(B0, dtype=np.float64).reshape(3)
+    out = np.zeros(8)
+    lib().or_numerical_flux(b.ref(), int(direction), _dp(WL), _dp(WR), _dp(B0), _dp(out))
+    return out
 
 
 def mlp_forward(params, x):

@@ -34,6 +34,7 @@ BC_PERIODIC, BC_OUTFLOW, BC_INFLOW = 0, 1, 2
 LIM_MINMOD, LIM_MC, LIM_NONE = 0, 1, 2
 RK_MIDPOINT, RK_SSP2, RK_EULER = 0, 1, 2
 B0_NONE, B0_UNIFORM, B0_DIPOLE, B0_LINEAR = 0, 1, 2, 3
+FLUX_RUSANOV, FLUX_HLL = 0, 1
 
 NC = 8  # cells per block per axis
 
@@ -62,6 +63,7 @@ class Problem:
     mlp: np.ndarray = None
     local_dt: int = 0
     reflux: int = 0
+    flux: int = 0               # FLUX_RUSANOV or FLUX_HLL
 
     @property
     def nb(self):
@@ -547,6 +549,20 @@ def divb_advection(axis, ncells, amplitude=1e-3, speed=1.0, t_shift=0.0, powell=
     u = _axis_vec(axis, speed * one, 0 * one, 0 * one)
     B = _axis_vec(axis, bn, 0 * one, 0 * one)
     W = [one, u[0], u[1], u[2], B[0], B[1], B[2], one]
+    return _finish(prob, W)
+
+
+def entropy_wave(axis, ncells, amplitude=0.2, speed=1.0, t_shift=0.0, limiter=LIM_MC):
+    """A density wave rho = 1 + A sin(2 pi s) carried by the uniform flow
+    u_n = speed at uniform pressure 1 and B = (0.3, 0.2, 0.1): an exact
+    solution that moves at the flow speed."""
+    prob = _line_problem("entropy_wave", axis, ncells, limiter=limiter)
+    X = cell_centres(prob.lo, prob.hi, prob.root, prob.leaves)
+    s = X[axis] - speed * t_shift
+    one = np.ones_like(s)
+    u = _axis_vec(axis, speed * one, 0 * one, 0 * one)
+    B = _axis_vec(axis, 0.3 * one, 0.2 * one, 0.1 * one)
+    W = [one + amplitude * np.sin(2 * math.pi * s), u[0], u[1], u[2], B[0], B[1], B[2], one]
     return _finish(prob, W)
 
 
