@@ -43,7 +43,7 @@ BYTES_PER_CELL_UPDATE = 320  # FP64 state: stage 1 reads U^n, writes U*; stage 2
 # in profiles/ (None until a capture of the current kernel source exists).
 NCU_TRAFFIC = {
     # precision: (DRAM bytes per cell per launch, mean of the two stages, sha256 of bats_stage.cu at capture)
-    "mixed": (121.0, "9564eefe595977c05b62f084219f95b1d332aa8c32176d481eccab14dee5c3ea"),
+    "mixed": (121.0, "e7610965f156d47e7b6ccdd9c618e494de67bc90cebdfd004bcdbb7a4b20e939"),
 }
 
 
@@ -223,14 +223,21 @@ def learned_form_summary(stream, steps=32):
 
 def other_workloads(stream, steps=20, fp64_steps=4):
     """Mixed and FP64 throughput on the blast at 16^3 roots, the magnetosphere
-    stand-in and the Table 2 fast-wave grid at m = 12, each one grid in one
-    persistent launch per stage replayed from a CUDA graph."""
+    stand-in and the Table 2 fast-wave grid at m = 12 (with the Rusanov and
+    with the HLL flux), each one grid in one persistent launch per stage
+    replayed from a CUDA graph."""
     import torch
     from paper_2501_06717_gb300 import bats
+
+    def with_hll(prob):
+        prob.flux = W.FLUX_HLL
+        return prob
+
     out = {}
     for name, make in (("blast_16cube_roots", lambda: W.blast(roots_per_axis=16)),
                        ("magnetosphere", W.magnetosphere),
-                       ("fast_wave_table2_m12", lambda: W.fast_wave(m=12))):
+                       ("fast_wave_table2_m12", lambda: W.fast_wave(m=12)),
+                       ("fast_wave_table2_m12_hll", lambda: with_hll(W.fast_wave(m=12)))):
         prob = make()
         row = {"blocks": prob.nb, "cells": prob.ncells}
         for pname, prec, n in (("mixed", bats.BATS_MIXED, steps), ("fp64", bats.BATS_FP64, fp64_steps)):

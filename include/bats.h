@@ -50,6 +50,7 @@ enum { BATS_LIM_MINMOD = 0, BATS_LIM_MC = 1, BATS_LIM_NONE = 2 };
 enum { BATS_RK_MIDPOINT = 0, BATS_RK_SSP2 = 1, BATS_RK_EULER = 2 };
 enum { BATS_FP64 = 0, BATS_MIXED = 1 };
 enum { BATS_B0_NONE = 0, BATS_B0_UNIFORM = 1, BATS_B0_DIPOLE = 2, BATS_B0_LINEAR = 3 };
+enum { BATS_FLUX_RUSANOV = 0, BATS_FLUX_HLL = 1 };
 enum { BATS_PHASE_STAGE = 0, BATS_PHASE_DT = 1, BATS_PHASE_TOTAL = 2, BATS_NUM_PHASES = 3 };
 
 typedef struct bats bats_t;
@@ -106,7 +107,16 @@ typedef struct {
  *                 replaced, for the coarse cell, by the mean of the 4 fine
  *                 fluxes through it, so every conserved variable is conserved to
  *                 round-off on periodic grids without sources.  Not with
- *                 `learned` (BATS_ERR_INVALID_ARG). */
+ *                 `learned` (BATS_ERR_INVALID_ARG).
+ *  flux           numerical face flux: BATS_FLUX_RUSANOV (Algorithm 1's
+ *                 "calc_face_flux" with the Rusanov flux, the default), or
+ *                 BATS_FLUX_HLL, the two-state Harten-Lax-van Leer flux with
+ *                 the wave-speed bounds S_L = min(un_L - cf_L, un_R - cf_R),
+ *                 S_R = max(un_L + cf_L, un_R + cf_R) (the base of the Linde
+ *                 flux that Section 5 names; its contact-restoring term is not
+ *                 given in the paper and not included).  HLL is not available
+ *                 with `learned` (the correction is clipped by the Rusanov
+ *                 dissipation): BATS_ERR_INVALID_ARG. */
 typedef struct {
   double gamma;
   int32_t limiter, rk, precision, b0;
@@ -115,6 +125,7 @@ typedef struct {
   int32_t ctas_per_sm, use_graph;
   int32_t local_dt;
   int32_t reflux;
+  int32_t flux;
 } bats_physics;
 
 /* Create a solver for n_grids independent grids advanced together (batched
@@ -239,7 +250,8 @@ int bats_debug_check_conversions(const float* f, const double* d, int n, double*
 /* Install network weights in a solver (host or device pointer, copied) and
  * turn the learned form on for its next steps; params == NULL turns it off.
  * Each stage then runs three launches: face inputs, the network, the fused
- * stage with the correction. */
+ * stage with the correction.  BATS_ERR_INVALID_ARG on a handle created with
+ * refluxing or the HLL flux (the correction is defined on the Rusanov flux). */
 int bats_set_mlp(bats_t* h, const float* params);
 
 /* Training-data view of grid `grid`: for every face of every block (index
@@ -250,7 +262,9 @@ int bats_set_mlp(bats_t* h, const float* params);
  * (8, x/y/z components) and the face's rho_ref and c_ref, of the current
  * state (stage_input 0) or of the midpoint
  * stage-2 input U* = U + (dt/2) R(U) (stage_input 1, dt > 0).  The state is
- * not changed.  n_faces = 1728 * n_blocks of the grid. */
+ * not changed.  n_faces = 1728 * n_blocks of the grid.  Rusanov handles only
+ * (the fluxes are the learned correction's targets): BATS_ERR_INVALID_ARG
+ * with BATS_FLUX_HLL. */
 int bats_debug_face_data(bats_t* h, int grid, int stage_input, double dt, float* X, double* F, size_t n_faces);
 
 /* Trainer: FP32 master weights, Adam state, GPU forward and backward. */

@@ -27,6 +27,7 @@ BATS_LIM_MINMOD, BATS_LIM_MC, BATS_LIM_NONE = 0, 1, 2
 BATS_RK_MIDPOINT, BATS_RK_SSP2, BATS_RK_EULER = 0, 1, 2
 BATS_FP64, BATS_MIXED = 0, 1
 BATS_B0_NONE, BATS_B0_UNIFORM, BATS_B0_DIPOLE, BATS_B0_LINEAR = 0, 1, 2, 3
+BATS_FLUX_RUSANOV, BATS_FLUX_HLL = 0, 1
 BATS_PHASE_STAGE, BATS_PHASE_DT, BATS_PHASE_TOTAL, BATS_NUM_PHASES = 0, 1, 2, 3
 
 
@@ -60,6 +61,7 @@ class bats_physics(ctypes.Structure):
         ("use_graph", ctypes.c_int32),
         ("local_dt", ctypes.c_int32),
         ("reflux", ctypes.c_int32),
+        ("flux", ctypes.c_int32),
     ]
 
 
@@ -178,6 +180,7 @@ def physics_from(problem, precision=BATS_FP64, persistent=0, blocks_per_cta=1, c
     ph.use_graph = int(use_graph)
     ph.local_dt = int(getattr(problem, "local_dt", 0) or 0)
     ph.reflux = int(getattr(problem, "reflux", 0) or 0)
+    ph.flux = int(getattr(problem, "flux", 0) or 0)
     return ph
 
 

@@ -670,6 +670,10 @@ int bats_create(const bats_grid_desc* grids, int n_grids, const bats_physics* ph
   if (!(phys->gamma > 1.0)) return fail(nullptr, BATS_ERR_INVALID_ARG, "gamma must exceed 1");
   if (phys->reflux && phys->learned)
     return fail(nullptr, BATS_ERR_INVALID_ARG, "refluxing is not available with the learned correction");
+  if (phys->flux < BATS_FLUX_RUSANOV || phys->flux > BATS_FLUX_HLL)
+    return fail(nullptr, BATS_ERR_INVALID_ARG, "bad flux kind");
+  if (phys->flux != BATS_FLUX_RUSANOV && phys->learned)
+    return fail(nullptr, BATS_ERR_INVALID_ARG, "the learned correction is defined on the Rusanov flux only");
   if (phys->limiter < 0 || phys->limiter > 2 || phys->rk < 0 || phys->rk > 2 || phys->local_dt < 0 ||
       phys->local_dt > 1 || phys->precision < 0 ||
       phys->precision > 1 || phys->b0 < 0 || phys->b0 > 3)
@@ -702,6 +706,7 @@ int bats_create(const bats_grid_desc* grids, int n_grids, const bats_physics* ph
   h->ph.b0 = phys->b0;
   h->ph.powell = phys->powell ? 1 : 0;
   h->ph.learned = 0;
+  h->ph.flux = phys->flux;
   for (int i = 0; i < 12; i++) h->ph.b0p[i] = phys->b0_param[i];
   h->persistent = phys->persistent;
   h->bpc = std::max(1, phys->blocks_per_cta);
@@ -1030,6 +1035,9 @@ int bats_set_mlp(bats_t* h, const float* params) {
     h->learned_requested = false;
     return BATS_OK;
   }
+  if (h->reflux || h->ph.flux != BATS_FLUX_RUSANOV)
+    return fail(h, BATS_ERR_INVALID_ARG,
+                "the learned correction needs the Rusanov flux and is not available with refluxing");
   if (!h->mlp_params) {
     int rc;
     const size_t nf = static_cast<size_t>(h->nbt) * 3 * NFACE;
@@ -1049,6 +1057,8 @@ int bats_set_mlp(bats_t* h, const float* params) {
 int bats_debug_face_data(bats_t* h, int grid, int stage_input, double dt, float* X, double* F, size_t n_faces) {
   int rc = grid_check(h, grid);
   if (rc) return rc;
+  if (h->ph.flux != BATS_FLUX_RUSANOV)
+    return fail(h, BATS_ERR_INVALID_ARG, "face data (the learned correction's inputs and targets) needs the Rusanov flux");
   const GridDev& G = h->grids_h[grid];
   const size_t nf = static_cast<size_t>(G.nb) * 3 * NFACE;
   if (!F || n_faces != nf) return fail(h, BATS_ERR_INVALID_ARG, "face buffer size mismatch");

@@ -271,7 +271,8 @@ extern "C" int bats_step_noalloc(const bats_grid_desc* grid, const bats_physics*
   if (!(phys->gamma > 1.0)) return report(err, err_len, BATS_ERR_INVALID_ARG, "gamma must exceed 1");
   if (phys->precision != BATS_FP64 || phys->learned)
     return report(err, err_len, BATS_ERR_INVALID_ARG, "bats_step_noalloc runs the FP64 form only");
-  if (phys->limiter < 0 || phys->limiter > 1 || phys->rk < 0 || phys->rk > 1 || phys->b0 < 0 || phys->b0 > 3)
+  if (phys->limiter < 0 || phys->limiter > 1 || phys->rk < 0 || phys->rk > 1 || phys->b0 < 0 || phys->b0 > 3 ||
+      phys->flux < BATS_FLUX_RUSANOV || phys->flux > BATS_FLUX_HLL)
     return report(err, err_len, BATS_ERR_INVALID_ARG, "bad physics enumeration");
   if (grid->n_leaves > kMaxBlocks)
     return report(err, err_len, BATS_ERR_INVALID_ARG,
@@ -314,6 +315,7 @@ extern "C" int bats_step_noalloc(const bats_grid_desc* grid, const bats_physics*
   ph.precision = BATS_FP64;
   ph.b0 = phys->b0;
   ph.powell = phys->powell ? 1 : 0;
+  ph.flux = phys->flux;
   for (int i = 0; i < 12; i++) ph.b0p[i] = phys->b0_param[i];
   const int nb = grid->n_leaves;
   int64_t map_entries = 0;

@@ -993,7 +993,7 @@ __device__ __forceinline__ void b0_face(const PhysDev& ph, int d, int i, int j, 
 // every cell is loaded and every limited slope computed once; (4) per cell:
 // flux differences x, y, z, the sources, the update and (last stage) the CFL
 // bound.
-template <bool MIXED, int LIM, bool HAS_B0, bool LRN>
+template <bool MIXED, int LIM, bool HAS_B0, bool LRN, int FLX>
 __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1) k_stage(const StageArgs a) {
   using R = typename StageCfg<MIXED>::R;
   constexpr int STAGE_THREADS = StageCfg<MIXED>::THREADS;
@@ -1157,8 +1157,24 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1) k_sta
             R cmax = aL > aR ? aL : aR;
             const int fi = fline * 9 + f;
             R Fr[8];
+            if constexpr (FLX == FLUX_HLL) {
+              // HLL with S_L = min(unL - cfL, unR - cfR, 0), S_R = max(unL + cfL,
+              // unR + cfR, 0):  F = F_L - S_L/(S_R - S_L) ((F_R - F_L) - S_R (U_R - U_L)),
+              // which is F_L when every wave moves right (S_L = 0), F_R when every
+              // wave moves left (S_R = 0), else the two-state HLL flux
+              const R zero = R(0);
+              R sl = unL - cfL < unR - cfR ? unL - cfL : unR - cfR;
+              R sr = unL + cfL > unR + cfR ? unL + cfL : unR + cfR;
+              sl = sl < zero ? sl : zero;
+              sr = sr > zero ? sr : zero;
+              const R den = sr - sl;
+              const R kk = den > zero ? Ops<R>::div_(sl, den) : zero;
 #pragma unroll
-            for (int v = 0; v < NV; v++) Fr[v] = R(0.5) * (FL[v] + FR[v]) - R(0.5) * cmax * (UR[v] - UL[v]);
+              for (int v = 0; v < NV; v++) Fr[v] = FL[v] - kk * ((FR[v] - FL[v]) - sr * (UR[v] - UL[v]));
+            } else {
+#pragma unroll
+              for (int v = 0; v < NV; v++) Fr[v] = R(0.5) * (FL[v] + FR[v]) - R(0.5) * cmax * (UR[v] - UL[v]);
+            }
             if constexpr (LRN) {
               // network inputs: the 4 stencil cells f-2..f+1 and (WL + WR)/2 in
               // the face frame, scaled by rho_ref = mean stencil density and
@@ -1847,26 +1863,32 @@ size_t stage_smem_bytes(bool mixed) {
 }
 
 using StageFn = void (*)(const StageArgs);
-template <bool MIXED, bool LRN>
+template <bool MIXED, bool LRN, int FLX>
 StageFn stage_fn_l(int lim, bool b0) {
-  if (lim == 2) return b0 ? k_stage<MIXED, 2, true, LRN> : k_stage<MIXED, 2, false, LRN>;
-  if (lim == 1) return b0 ? k_stage<MIXED, 1, true, LRN> : k_stage<MIXED, 1, false, LRN>;
-  return b0 ? k_stage<MIXED, 0, true, LRN> : k_stage<MIXED, 0, false, LRN>;
+  if (lim == 2) return b0 ? k_stage<MIXED, 2, true, LRN, FLX> : k_stage<MIXED, 2, false, LRN, FLX>;
+  if (lim == 1) return b0 ? k_stage<MIXED, 1, true, LRN, FLX> : k_stage<MIXED, 1, false, LRN, FLX>;
+  return b0 ? k_stage<MIXED, 0, true, LRN, FLX> : k_stage<MIXED, 0, false, LRN, FLX>;
 }
+// The learned correction is defined on the Rusanov flux only (the host rejects
+// learned + HLL), so HLL is instantiated for the plain kernels only.
 template <bool MIXED>
-StageFn stage_fn(int lim, bool b0, bool lrn = false) {
-  return lrn ? stage_fn_l<MIXED, true>(lim, b0) : stage_fn_l<MIXED, false>(lim, b0);
+StageFn stage_fn(int lim, bool b0, bool lrn = false, int flux = FLUX_RUSANOV) {
+  if (lrn) return stage_fn_l<MIXED, true, FLUX_RUSANOV>(lim, b0);
+  return flux == FLUX_HLL ? stage_fn_l<MIXED, false, FLUX_HLL>(lim, b0)
+                          : stage_fn_l<MIXED, false, FLUX_RUSANOV>(lim, b0);
 }
 
 cudaError_t stage_setup(int occ[2]) {
   cudaError_t e = cudaSuccess;
   for (int lim = 0; lim < 3 && e == cudaSuccess; lim++)
     for (int b0 = 0; b0 < 2 && e == cudaSuccess; b0++)
-      for (int lrn = 0; lrn < 2 && e == cudaSuccess; lrn++) {
-        e = cudaFuncSetAttribute(stage_fn<false>(lim, b0, lrn), cudaFuncAttributeMaxDynamicSharedMemorySize,
+      for (int kv = 0; kv < 3 && e == cudaSuccess; kv++) {  // Rusanov, learned, HLL
+        const bool lrn = kv == 1;
+        const int flux = kv == 2 ? FLUX_HLL : FLUX_RUSANOV;
+        e = cudaFuncSetAttribute(stage_fn<false>(lim, b0, lrn, flux), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(StageCfg<false>::SMEM));
         if (e == cudaSuccess)
-          e = cudaFuncSetAttribute(stage_fn<true>(lim, b0, lrn), cudaFuncAttributeMaxDynamicSharedMemorySize,
+          e = cudaFuncSetAttribute(stage_fn<true>(lim, b0, lrn, flux), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    static_cast<int>(StageCfg<true>::SMEM));
       }
   if (e == cudaSuccess)
@@ -1887,8 +1909,11 @@ cudaError_t stage_setup(int occ[2]) {
 cudaError_t launch_stage_kernel(bool mixed, int grid, cudaStream_t st, const StageArgs& a) {
   const bool b0 = a.ph.b0 != B0_NONE;
   const bool lrn = a.learned || a.kind >= 3;
-  if (mixed) stage_fn<true>(a.ph.limiter, b0, lrn)<<<grid, StageCfg<true>::THREADS, StageCfg<true>::SMEM, st>>>(a);
-  else stage_fn<false>(a.ph.limiter, b0, lrn)<<<grid, StageCfg<false>::THREADS, StageCfg<false>::SMEM, st>>>(a);
+  const int flux = a.ph.flux;
+  if (mixed)
+    stage_fn<true>(a.ph.limiter, b0, lrn, flux)<<<grid, StageCfg<true>::THREADS, StageCfg<true>::SMEM, st>>>(a);
+  else
+    stage_fn<false>(a.ph.limiter, b0, lrn, flux)<<<grid, StageCfg<false>::THREADS, StageCfg<false>::SMEM, st>>>(a);
   return cudaGetLastError();
 }
 
