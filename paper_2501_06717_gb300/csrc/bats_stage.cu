@@ -1290,19 +1290,28 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1) k_sta
       // 4. per cell: flux differences, sources, update, CFL bound.  commit =
       //    false only checks the update (learned form): returns whether this
       //    thread met a non-physical cell, writes nothing
-      auto cells = [&](const bool commit) -> bool {
+      auto cells = [&](const bool commit, auto fast_c) -> bool {
+        // FAST (compile time): kind 0, no local time steps, no body cell in the
+        // block.  The general form keeps those paths, whose FP64 work the
+        // compiler would otherwise issue predicated off for every cell (GB300
+        // runs FP64 at 1/64 of the FP32 rate, so even dead FP64 instructions
+        // cost).
+        constexpr bool FAST = decltype(fast_c)::value;
+        const int kind = FAST ? 0 : a.kind;
+        double* const dtc = FAST ? nullptr : a.dtc;
+        const bool blk_body = FAST ? false : B.body != 0;
         bool any_bad = false;
         R smax_loc = R(0);
         const double cdt_blk = a.beta * a.dt[B.grid];
         // mixed form, first stage of the midpoint scheme: U* only feeds the
         // second stage's FP32 primitives, so W* = W^n + the increment, in FP32
         // (the FP64 state is read and accumulated in the last stage only)
-        const bool light = MIXED && a.kind == 0 && !a.last && !a.write_u_all;
+        const bool light = MIXED && kind == 0 && !a.last && !a.write_u_all;
         const float c32_blk = d2f_int(cdt_blk);
         for (int c = tid; c < NCELL; c += STAGE_THREADS) {
           // local time stepping: this cell's own dt
-          const double cdt = a.dtc ? a.beta * a.dtc[static_cast<int64_t>(blk) * NCELL + c] : cdt_blk;
-          const float c32 = a.dtc ? d2f_int(cdt) : c32_blk;
+          const double cdt = dtc ? a.beta * dtc[static_cast<int64_t>(blk) * NCELL + c] : cdt_blk;
+          const float c32 = dtc ? d2f_int(cdt) : c32_blk;
           const int ci = c & 7, cj = (c >> 3) & 7, ck = c >> 6;
           // face indices (line * 9 + position) of the low faces in x, y, z
           const int tx = (ck * NC + cj) * 9 + ci;
@@ -1323,7 +1332,7 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1) k_sta
                           (Fy[8 * NFACE + ty + 1] - Fy[8 * NFACE + ty]) * idx1) +
                          (Fz[8 * NFACE + tz + 1] - Fz[8 * NFACE + tz]) * idx2;
           bool in_body = false;
-          if (B.body) {  // FP64, the same centre formula as the host and the oracle
+          if (blk_body) {  // FP64, the same centre formula as the host and the oracle
             double x = G.lo[0] + ((static_cast<double>(gb0) + ci) + 0.5) * G.dx[lev][0];
             double y = G.lo[1] + ((static_cast<double>(gb1) + cj) + 0.5) * G.dx[lev][1];
             double z = G.lo[2] + ((static_cast<double>(gb2) + ck) + 0.5) * G.dx[lev][2];
@@ -1397,21 +1406,21 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1) k_sta
             else rd = r;
             double ub = a.Ubase[base + v * NCELL];
             double o;
-            if (a.kind == 0) o = fma(cdt, rd, ub);
+            if (kind == 0) o = fma(cdt, rd, ub);
             else o = 0.5 * ub + 0.5 * fma(cdt, rd, a.Uin[base + v * NCELL]);
-            if (a.kind == 2) o = rd;  // residual only (debug view)
+            if (kind == 2) o = rd;  // residual only (debug view)
             Uo[v] = o;
           }
           if (in_body) {  // a branch, not a select: no loads of the body state elsewhere
 #pragma unroll
-            for (int v = 0; v < NV; v++) Uo[v] = a.kind == 2 ? 0.0 : G.Ubody[v];
+            for (int v = 0; v < NV; v++) Uo[v] = kind == 2 ? 0.0 : G.Ubody[v];
           }
 #pragma unroll
           for (int v = 0; v < NV; v++) bad |= !finite_d(Uo[v]);
-          if (a.kind != 2) bad |= !positive_d(Uo[0]);
+          if (kind != 2) bad |= !positive_d(Uo[0]);
           R Wn[8];
           const bool need_w = MIXED || a.last || !commit;
-          if (need_w && a.kind != 2) {
+          if (need_w && kind != 2) {
             if constexpr (MIXED) {
               double p64;
               prim_mixed(Uo, ph.gm1f, Wn, &p64);
@@ -1421,7 +1430,7 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1) k_sta
               bad |= !positive_d(Wn[7]);
             }
           }
-          if (bad && !in_body && a.kind != 2) {
+          if (bad && !in_body && kind != 2) {
             any_bad = true;
             if (commit) {
               atomicOr(&a.err[0], ERR_NONPHYSICAL);
@@ -1430,12 +1439,12 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1) k_sta
           }
           if (!commit) continue;
           const bool write_u = !MIXED || a.last || a.write_u_all;
-          if (write_u || a.kind == 2) {
+          if (write_u || kind == 2) {
 #pragma unroll
             for (int v = 0; v < NV; v++) a.Uout[base + v * NCELL] = Uo[v];
           }
           if constexpr (MIXED) {
-            if (a.kind != 2) {
+            if (kind != 2) {
 #pragma unroll
               for (int v = 0; v < NV; v++) a.Wout[base + v * NCELL] = Wn[v];
             }
@@ -1445,7 +1454,7 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1) k_sta
           const bool refl = a.freg && ((ci == 0 && B.ftype[0] == FACE_FINER) || (ci == NC - 1 && B.ftype[1] == FACE_FINER) ||
                                        (cj == 0 && B.ftype[2] == FACE_FINER) || (cj == NC - 1 && B.ftype[3] == FACE_FINER) ||
                                        (ck == 0 && B.ftype[4] == FACE_FINER) || (ck == NC - 1 && B.ftype[5] == FACE_FINER));
-          if (a.last && !in_body && a.kind != 2 && !refl) {
+          if (a.last && !in_body && kind != 2 && !refl) {
             R Bt[3] = {B0c[0] + Wn[4], B0c[1] + Wn[5], B0c[2] + Wn[6]};
             R sacc = R(0);
 #pragma unroll
@@ -1461,17 +1470,17 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1) k_sta
               }
             }
             smax_loc = sacc > smax_loc ? sacc : smax_loc;
-            if (a.dtc) {
+            if (dtc) {
               double sd;
               if constexpr (MIXED) sd = f2d_int(sacc);
               else sd = sacc;
-              a.dtc[static_cast<int64_t>(blk) * NCELL + c] = a.cfl / sd;
+              dtc[static_cast<int64_t>(blk) * NCELL + c] = a.cfl / sd;
             }
-          } else if (a.last && a.dtc && a.kind != 2 && in_body) {
-            a.dtc[static_cast<int64_t>(blk) * NCELL + c] = 0.0;  // body cell
+          } else if (a.last && dtc && kind != 2 && in_body) {
+            dtc[static_cast<int64_t>(blk) * NCELL + c] = 0.0;  // body cell
           }
         }
-        if (commit && a.last && a.kind != 2) {
+        if (commit && a.last && kind != 2) {
           R m = smax_loc;
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) {
@@ -1495,19 +1504,23 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1) k_sta
       if (tid < FACE_THREADS) faces(true);
       __syncthreads();
       if (a.kind >= 3) continue;  // features / dumps only
+      const bool fast = a.kind == 0 && !a.dtc && !B.body;
+      auto run_cells = [&](const bool commit) -> bool {
+        return fast ? cells(commit, std::true_type{}) : cells(commit, std::false_type{});
+      };
       if constexpr (LRN) {
         // fallback of the learned form: a block whose learned update leaves a
         // non-physical cell (rho <= 0, p <= 0 or not finite) is recomputed
         // with the plain Rusanov flux
         if (a.learned && a.kind < 2) {
-          if (__syncthreads_or(cells(false))) {
+          if (__syncthreads_or(run_cells(false))) {
             if (tid < FACE_THREADS) faces(false);
             __syncthreads();
             if (tid == 0) atomicAdd(&a.err[2], 1);
           }
         }
       }
-      cells(true);
+      run_cells(true);
       __syncthreads();
     }
   }
