@@ -208,6 +208,12 @@ int bats_debug_fill_ghosts_w(bats_t* h, int grid, double* T, size_t n);
  * (fluxes, sources; body cells 0), double [8][n_blocks][8][8][8]. */
 int bats_debug_residual(bats_t* h, int grid, double* R, size_t n);
 
+/* Test hook for the bounded device waits (the stage kernel's waits on its
+ * bulk-copy barrier give up after about 1 s and report instead of hanging):
+ * one CTA waits on a barrier that nothing completes.  Returns
+ * BATS_ERR_TIMEOUT after about 1 s; the handle stays usable. */
+int bats_debug_wait_timeout(bats_t* h);
+
 /* Launch-form controls (the autotuner's knobs): persistent launch on/off,
  * blocks per work item, CTAs per SM, CUDA-graph replay of whole steps. */
 int bats_set_launch(bats_t* h, int persistent, int blocks_per_cta, int ctas_per_sm, int use_graph);

@@ -11,7 +11,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libbats.so")
+# BATS_LIB selects another build of the same library (the checked build in
+# the tests)
+LIB_PATH = os.environ.get("BATS_LIB") or os.path.join(_HERE, "_build", "libbats.so")
 
 BATS_OK = 0
 BATS_ERR_INVALID_ARG = -1
@@ -102,6 +104,7 @@ def lib():
     L.bats_debug_fill_ghosts.argtypes = [vp, ctypes.c_int, dp, ctypes.c_size_t]
     L.bats_debug_fill_ghosts_w.argtypes = [vp, ctypes.c_int, dp, ctypes.c_size_t]
     L.bats_debug_residual.argtypes = [vp, ctypes.c_int, dp, ctypes.c_size_t]
+    L.bats_debug_wait_timeout.argtypes = [vp]
     L.bats_set_launch.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     L.bats_get_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     L.bats_get_fallbacks.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
@@ -274,6 +277,10 @@ def bats_debug_fill_ghosts_w(h, grid, out):
     p, n = _ptr_and_size(out)
     _check(h, lib().bats_debug_fill_ghosts_w(h, int(grid), p, n))
     return out
+
+
+def bats_debug_wait_timeout(h):
+    _check(h, lib().bats_debug_wait_timeout(h))
 
 
 def bats_debug_residual(h, grid, out):

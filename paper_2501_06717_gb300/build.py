@@ -15,6 +15,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libbats.so")
+# the checked build: every kernel index range-tested (tests only)
+OUT_CHECKED = os.path.join(HERE, "_build_checked")
 SOURCES = ["bats_stage.cu", "bats_host.cu", "bats_noalloc.cu", "bats_mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
@@ -35,15 +37,17 @@ def _stale(obj, src):
     return any(os.path.getmtime(d) > os.path.getmtime(obj) for d in deps)
 
 
-def build(verbose=False, force=False):
-    os.makedirs(OUT, exist_ok=True)
+def build(verbose=False, force=False, checked=False):
+    out = OUT_CHECKED if checked else OUT
+    lib = os.path.join(out, "libbats.so")
+    os.makedirs(out, exist_ok=True)
     nvcc = _nvcc()
     jobs = []
     for s in SOURCES:
         src = os.path.join(CSRC, s)
-        obj = os.path.join(OUT, s.replace(".cu", ".o"))
+        obj = os.path.join(out, s.replace(".cu", ".o"))
         if force or _stale(obj, src):
-            cmd = [nvcc, *ARCH, *FLAGS, "-c", src, "-o", obj]
+            cmd = [nvcc, *ARCH, *FLAGS, *(["-DBATS_CHECKED"] if checked else []), "-c", src, "-o", obj]
             if verbose:
                 cmd += ["-Xptxas", "-v"]
             jobs.append(cmd)
@@ -54,13 +58,13 @@ def build(verbose=False, force=False):
             sys.stderr.write(r.stdout + r.stderr)
         if r.returncode:
             raise RuntimeError("nvcc failed: %s" % " ".join(c))
-    objs = [os.path.join(OUT, s.replace(".cu", ".o")) for s in SOURCES]
-    if jobs or not os.path.exists(LIB):
-        tmp = LIB + ".tmp%d" % os.getpid()
+    objs = [os.path.join(out, s.replace(".cu", ".o")) for s in SOURCES]
+    if jobs or not os.path.exists(lib):
+        tmp = lib + ".tmp%d" % os.getpid()
         subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs], check=True)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(verbose="--verbose" in sys.argv, force="--force" in sys.argv))
+    print(build(verbose="--verbose" in sys.argv, force="--force" in sys.argv, checked="--checked" in sys.argv))

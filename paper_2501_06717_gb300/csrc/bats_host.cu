@@ -40,6 +40,8 @@ cudaError_t launch_dt(int ngrids, int mode, double cfl, double fixed_dt, double*
 cudaError_t launch_debug_fill(const StageArgs& a, int b0, int nb, double* T, cudaStream_t st);
 cudaError_t launch_debug_fill_w(const StageArgs& a, int b0, int nb, double* T, cudaStream_t st);
 cudaError_t launch_check_conversions(const float* f, const double* d, int n, double* f2d_out, float* d2f_out);
+cudaError_t read_index_flag(int32_t* out);
+cudaError_t launch_debug_wait_timeout(int32_t* err, cudaStream_t st);
 cudaError_t mlp_alloc(MlpDev* w);
 void mlp_free(MlpDev* w);
 cudaError_t launch_mlp_pack(const float* P, const MlpDev& m, cudaStream_t st);
@@ -425,6 +427,7 @@ StageArgs base_args(bats_t* h) {
   a.smax_next = h->smax_next;
   a.err = h->errw;
   a.nblocks = h->nbt;
+  a.nslots = h->nslots;
   a.blocks_per_item = std::max(1, h->bpc);
   a.ph = h->ph;
   return a;
@@ -594,6 +597,15 @@ int enqueue_steps(bats_t* h, int n, double cfl, double fixed_dt, bool timed) {
   return BATS_OK;
 }
 
+// Checked build: an index outside its range anywhere in the kernels since the
+// last call is an error (the flag is always clear in the normal build).
+int index_check(bats_t* h) {
+  int32_t f = 0;
+  CK(h, read_index_flag(&f));
+  if (f) return fail(h, BATS_ERR_CUDA, "index check failed (checked build): an index left its range");
+  return BATS_OK;
+}
+
 int run_steps(bats_t* h, int n, double cfl, double fixed_dt, double* t_out) {
   if (n < 0) return fail(h, BATS_ERR_INVALID_ARG, "negative step count");
   if (h->learned_requested && !h->learned)
@@ -647,6 +659,7 @@ int run_steps(bats_t* h, int n, double cfl, double fixed_dt, double* t_out) {
   h->ms_last[BATS_PHASE_DT] = h->timed_steps > 0 ? ms - stage_ms : -1.0;
   h->ms_last[BATS_PHASE_TOTAL] = ms;
   if (t_out) CK(h, cudaMemcpy(t_out, h->t, sizeof(double), cudaMemcpyDeviceToHost));
+  if (int rc = index_check(h)) return rc;
   if (ew[0] & ERR_TIMEOUT) return fail(h, BATS_ERR_TIMEOUT, "a bounded device wait ran out");
   if (ew[0] & ERR_BOUNDS) return fail(h, BATS_ERR_CUDA, "ghost fill met a source two levels away (unbalanced tree)");
   if (ew[0] & ERR_NONPHYSICAL)
@@ -958,7 +971,7 @@ int bats_debug_fill_ghosts(bats_t* h, int grid, double* T, size_t n) {
   CK(h, launch_debug_fill(a, G.block0, G.nb, dst, h->stream));
   if (!dev) CK(h, cudaMemcpyAsync(T, h->staging, need * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
-  return BATS_OK;
+  return index_check(h);
 }
 
 int bats_debug_fill_ghosts_w(bats_t* h, int grid, double* T, size_t n) {
@@ -980,7 +993,7 @@ int bats_debug_fill_ghosts_w(bats_t* h, int grid, double* T, size_t n) {
   CK(h, launch_debug_fill_w(a, G.block0, G.nb, dst, h->stream));
   if (!dev) CK(h, cudaMemcpyAsync(T, h->staging, need * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
-  return BATS_OK;
+  return index_check(h);
 }
 
 int bats_debug_residual(bats_t* h, int grid, double* R, size_t n) {
@@ -1008,6 +1021,18 @@ int bats_debug_residual(bats_t* h, int grid, double* R, size_t n) {
   CK(h, launch_to_external(h->U1, dst, G.block0, G.nb, h->stream));
   if (!dev) CK(h, cudaMemcpyAsync(R, h->staging, need * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
+  return index_check(h);
+}
+
+int bats_debug_wait_timeout(bats_t* h) {
+  if (!h) return BATS_ERR_INVALID_ARG;
+  int32_t init[3] = {0, INT_MAX, 0};
+  CK(h, cudaMemcpyAsync(h->errw, init, sizeof(init), cudaMemcpyHostToDevice, h->stream));
+  CK(h, launch_debug_wait_timeout(h->errw, h->stream));
+  int32_t ew[3];
+  CK(h, cudaMemcpyAsync(ew, h->errw, sizeof(ew), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  if (ew[0] & ERR_TIMEOUT) return fail(h, BATS_ERR_TIMEOUT, "a bounded device wait ran out");
   return BATS_OK;
 }
 

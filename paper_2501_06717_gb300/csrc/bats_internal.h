@@ -111,6 +111,7 @@ struct StageArgs {
   double cfl;             // CFL number for dtc
   double* freg;           // refluxing: flux register [slot][64][8] (nullptr: off)
   float* gbuf;            // mixed form: ghost slabs of faces at resolution changes [slot][8][128]
+  int32_t nslots;         // slots of freg and gbuf (index checks of the checked build)
   PhysDev ph;
   // learned form; face index ((blk * 3 + d) * 576 + line * 9 + f)
   int32_t learned;        // kinds 0-2: add the clipped, rescaled correction Y

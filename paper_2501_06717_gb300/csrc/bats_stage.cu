@@ -20,6 +20,27 @@
 namespace batsk {
 
 // ---------------------------------------------------------------------------
+// Checked build (-DBATS_CHECKED, a separate library used by the tests in
+// place of a memory checker): every index into the shared tile and face
+// arrays, the state arrays, the block maps and the slot buffers is tested
+// against its range before use; a failing index sets g_index_err and is
+// replaced by the range's first value, so the access stays in bounds and the
+// kernel runs to its end.  The normal build compiles the checks away.
+#ifdef BATS_CHECKED
+__device__ int32_t g_index_err;
+__device__ __forceinline__ int64_t chk(int64_t i, int64_t lo, int64_t hi) {
+  if (i < lo || i >= hi) {
+    atomicOr(&g_index_err, 1);
+    return lo;
+  }
+  return i;
+}
+#else
+__device__ __forceinline__ int64_t chk(int64_t i, int64_t, int64_t) { return i; }
+#endif
+__device__ __forceinline__ int chki(int i, int lo, int hi) { return static_cast<int>(chk(i, lo, hi)); }
+
+// ---------------------------------------------------------------------------
 // PTX helpers: mbarrier + 1-D bulk copy (TMA), bounded waits.
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -384,7 +405,11 @@ struct GhostCtx {
 
 __device__ __forceinline__ int32_t map_lookup(const GridDev& G, const int32_t* levmap, int l, int bi, int bj,
                                               int bk) {
+  l = chki(l, 0, G.maxlev + 1);
   int64_t nbi = static_cast<int64_t>(G.root[0]) << l, nbj = static_cast<int64_t>(G.root[1]) << l;
+  bi = static_cast<int>(chk(bi, 0, nbi));
+  bj = static_cast<int>(chk(bj, 0, nbj));
+  bk = static_cast<int>(chk(bk, 0, static_cast<int64_t>(G.root[2]) << l));
   return levmap[G.map_off[l] + (static_cast<int64_t>(bk) * nbj + bj) * nbi + bi];
 }
 // Leaf containing cell g of level lev (g inside the domain): same level or
@@ -392,11 +417,11 @@ __device__ __forceinline__ int32_t map_lookup(const GridDev& G, const int32_t* l
 __device__ __forceinline__ int locate(const GridDev& G, const int32_t* levmap, int lev, const int g[3], int& ll) {
   if (lev <= G.maxlev) {
     int id = map_lookup(G, levmap, lev, g[0] >> 3, g[1] >> 3, g[2] >> 3);
-    if (id >= 0) { ll = lev; return id; }
+    if (id >= 0) { ll = lev; return chki(id, G.block0, G.block0 + G.nb); }
   }
   if (lev >= 1) {
     int id = map_lookup(G, levmap, lev - 1, g[0] >> 4, g[1] >> 4, g[2] >> 4);
-    if (id >= 0) { ll = lev - 1; return id; }
+    if (id >= 0) { ll = lev - 1; return chki(id, G.block0, G.block0 + G.nb); }
   }
   ll = lev + 1;
   return -1;
@@ -418,7 +443,7 @@ __device__ __forceinline__ bool bc_map(const GridDev& G, int lev, int g[3]) {
 }
 __device__ __forceinline__ void load_cell(const GhostCtx& cx, int leaf, const int g[3], double out[8]) {
   const BlockDev& B = cx.blocks[leaf];
-  int li = g[0] - B.bi * NC, lj = g[1] - B.bj * NC, lk = g[2] - B.bk * NC;
+  int li = chki(g[0] - B.bi * NC, 0, NC), lj = chki(g[1] - B.bj * NC, 0, NC), lk = chki(g[2] - B.bk * NC, 0, NC);
   const double* p = cx.U + static_cast<int64_t>(leaf) * (NV * NCELL) + (lk * NC + lj) * NC + li;
 #pragma unroll
   for (int v = 0; v < NV; v++) out[v] = p[v * NCELL];
@@ -435,7 +460,8 @@ __device__ __noinline__ void restrict_cell(const GhostCtx& cx, int lev, const in
     return;
   }
   const BlockDev& B = cx.blocks[leaf];
-  int li = f[0] - B.bi * NC, lj = f[1] - B.bj * NC, lk = f[2] - B.bk * NC;
+  int li = chki(f[0] - B.bi * NC, 0, NC - 1), lj = chki(f[1] - B.bj * NC, 0, NC - 1),
+      lk = chki(f[2] - B.bk * NC, 0, NC - 1);
   const double* p = cx.U + static_cast<int64_t>(leaf) * (NV * NCELL) + (lk * NC + lj) * NC + li;
 #pragma unroll
   for (int v = 0; v < NV; v++) {
@@ -601,7 +627,7 @@ __device__ __noinline__ void prolong_item(const GhostCtx& cx, const BlockDev& B,
 // Primitives of cell g (global, level of `leaf`) from W.
 __device__ __forceinline__ void load_w(const float* Wt, const BlockDev* blocks, int leaf, const int g[3], float w[8]) {
   const BlockDev& B = blocks[leaf];
-  const int li = g[0] - B.bi * NC, lj = g[1] - B.bj * NC, lk = g[2] - B.bk * NC;
+  const int li = chki(g[0] - B.bi * NC, 0, NC), lj = chki(g[1] - B.bj * NC, 0, NC), lk = chki(g[2] - B.bk * NC, 0, NC);
   const float* p = Wt + static_cast<int64_t>(leaf) * (NV * NCELL) + (lk * NC + lj) * NC + li;
 #pragma unroll
   for (int v = 0; v < NV; v++) w[v] = p[v * NCELL];
@@ -630,7 +656,8 @@ __device__ __noinline__ void restrict_w(const float* Wt, const GridDev& G, const
     return;
   }
   const BlockDev& B = blocks[leaf];
-  const int li = f[0] - B.bi * NC, lj = f[1] - B.bj * NC, lk = f[2] - B.bk * NC;
+  const int li = chki(f[0] - B.bi * NC, 0, NC - 1), lj = chki(f[1] - B.bj * NC, 0, NC - 1),
+            lk = chki(f[2] - B.bk * NC, 0, NC - 1);
   const float* p = Wt + static_cast<int64_t>(leaf) * (NV * NCELL) + (lk * NC + lj) * NC + li;
   const int off[8] = {0, 1, NC, NC + 1, NC * NC, NC * NC + 1, NC * NC + NC, NC * NC + NC + 1};
   float rho[8], c[8];
@@ -797,10 +824,10 @@ __device__ __forceinline__ void fill_ghost(const StageArgs& a, const GhostCtx& c
   int ft = B.ftype[s];
   R w[8];
   if (ft == FACE_SAME || ft == FACE_OUTFLOW) {
-    int src = ft == FACE_SAME ? B.fnb[s] : blk;
+    int src = chki(ft == FACE_SAME ? B.fnb[s] : blk, 0, a.nblocks);
     int cn = ft == FACE_SAME ? (side ? c - NC : c + NC) : (side ? NC - 1 : 0);
     int i = d == 0 ? cn : ta, j = d == 1 ? cn : (d == 0 ? ta : tb), k = d == 2 ? cn : tb;
-    int cell = (k * NC + j) * NC + i;
+    int cell = chki((k * NC + j) * NC + i, 0, NCELL);
     if constexpr (MIXED) {
       const float* p = a.Win + static_cast<int64_t>(src) * (NV * NCELL) + cell;
 #pragma unroll
@@ -836,7 +863,7 @@ __device__ __forceinline__ void fill_ghost(const StageArgs& a, const GhostCtx& c
       for (int v = 0; v < NV; v++) w[v] = u[v];
     }
   }
-  int t = NCELL + q;
+  int t = chki(NCELL + q, NCELL, NTILE);
 #pragma unroll
   for (int v = 0; v < NV; v++) sT[v * NTILE + t] = w[v];
 }
@@ -905,7 +932,7 @@ __device__ __forceinline__ void fill_ghosts_block_mixed(const StageArgs& a, cons
     if (!((amask >> (q >> 7)) & 1u)) fill_ghost<true, float>(a, cx, B, blk, q, sT);
     else if (copy_amr) {
       const int s = q >> 7, local = q & 127;
-      const float* src = a.gbuf + static_cast<int64_t>(B.rslot[s]) * (NV * 128) + local;
+      const float* src = a.gbuf + chk(B.rslot[s], 0, a.nslots) * (NV * 128) + local;
 #pragma unroll
       for (int v = 0; v < NV; v++) sT[v * NTILE + NCELL + q] = src[v * 128];
     }
@@ -920,7 +947,7 @@ __device__ __forceinline__ void fill_ghosts_block_mixed(const StageArgs& a, cons
 __global__ void __launch_bounds__(128) k_amr_ghosts(const StageArgs a, const GhostTask* __restrict__ tasks) {
   __shared__ float tab[PSLOTS * PSTRIDE];
   const GhostTask T = tasks[blockIdx.x];
-  const BlockDev& B = a.blocks[T.blk];
+  const BlockDev& B = a.blocks[chki(T.blk, 0, a.nblocks)];
   const GridDev& G = a.grids[B.grid];
   const int tid = threadIdx.x;
   float w[8];
@@ -950,7 +977,7 @@ __global__ void __launch_bounds__(128) k_amr_ghosts(const StageArgs a, const Gho
     int g[3] = {B.bi * NC + i, B.bj * NC + j, B.bk * NC + k};
     sample_w(a.Win, G, a.blocks, a.levmap, B.level, g, a.ph.gm1f, w, a.err);
   }
-  float* o = a.gbuf + static_cast<int64_t>(T.slot) * (NV * 128) + tid;
+  float* o = a.gbuf + chk(T.slot, 0, a.nslots) * (NV * 128) + tid;
 #pragma unroll
   for (int v = 0; v < NV; v++) o[v * 128] = w[v];
 }
@@ -970,6 +997,7 @@ struct StageCfg {
 // offsets o[v] already select the rotated component's column.
 template <class R>
 __device__ __forceinline__ void load_rot(const R* sT, const int o[8], int idx, R w[8]) {
+  idx = chki(idx, 0, NTILE);
 #pragma unroll
   for (int v = 0; v < NV; v++) w[v] = sT[o[v] + idx];
 }
@@ -1064,7 +1092,7 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1) k_sta
         if constexpr (MIXED) {
           for (int f = 0; f < 6; f++) {
             if (!((amask >> f) & 1u)) continue;
-            const float* g = a.gbuf + static_cast<int64_t>(B.rslot[f]) * (NV * 128);
+            const float* g = a.gbuf + chk(B.rslot[f], 0, a.nslots) * (NV * 128);
 #pragma unroll
             for (int v = 0; v < NV; v++) bulk_g2s(sT + v * NTILE + NCELL + f * 128, g + v * 128, 128 * sizeof(float), &bar);
           }
@@ -1155,7 +1183,7 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1) k_sta
             phys_flux<R>(WR, B0r, gamma, inv_gm1, FR, UR, unR, cfR);
             R aL = Ops<R>::abs_(unL) + cfL, aR = Ops<R>::abs_(unR) + cfR;
             R cmax = aL > aR ? aL : aR;
-            const int fi = fline * 9 + f;
+            const int fi = chki(fline * 9 + f, 0, NFACE);
             R Fr[8];
             if constexpr (FLX == FLUX_HLL) {
               // HLL with S_L = min(unL - cfL, unR - cfR, 0), S_R = max(unL + cfL,
@@ -1266,7 +1294,7 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1) k_sta
             fcol[8 * NFACE + fi] = bnf;
             // refluxing: the block-face fluxes of faces at resolution changes
             if (a.freg && (f == 0 || f == NC)) {
-              const int sl = B.rslot[2 * fd + (f == NC ? 1 : 0)];
+              const int sl = chki(B.rslot[2 * fd + (f == NC ? 1 : 0)], -1, a.nslots);
               if (sl >= 0) {
                 double* o = a.freg + (static_cast<int64_t>(sl) * 64 + fta * NC + ftb) * NV;
                 double Fd[8];
@@ -1314,9 +1342,9 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1) k_sta
           const float c32 = dtc ? d2f_int(cdt) : c32_blk;
           const int ci = c & 7, cj = (c >> 3) & 7, ck = c >> 6;
           // face indices (line * 9 + position) of the low faces in x, y, z
-          const int tx = (ck * NC + cj) * 9 + ci;
-          const int ty = (ck * NC + ci) * 9 + cj;
-          const int tz = (cj * NC + ci) * 9 + ck;
+          const int tx = chki((ck * NC + cj) * 9 + ci, 0, NFACE - 1);
+          const int ty = chki((ck * NC + ci) * 9 + cj, 0, NFACE - 1);
+          const int tz = chki((cj * NC + ci) * 9 + ck, 0, NFACE - 1);
           const R* Fx = sF;
           const R* Fy = sF + NFC * NFACE;
           const R* Fz = sF + 2 * NFC * NFACE;
@@ -1677,8 +1705,8 @@ __global__ void __launch_bounds__(64) k_reflux(const StageArgs a, const RefluxTa
     if (!in_body) {
       const int d = T.s >> 1, side = T.s & 1;
       const int q = tid >> 3, r = tid & 7;
-      const double* Fc = a.freg + (static_cast<int64_t>(T.cslot) * 64 + tid) * NV;
-      const double* Ff = a.freg + static_cast<int64_t>(T.fslot[(q >> 2) + 2 * (r >> 2)]) * 64 * NV;
+      const double* Fc = a.freg + (chk(T.cslot, 0, a.nslots) * 64 + tid) * NV;
+      const double* Ff = a.freg + chk(T.fslot[(q >> 2) + 2 * (r >> 2)], 0, a.nslots) * 64 * NV;
       const int qf = 2 * (q & 3), rf = 2 * (r & 3);
       const double idx_d = G.idx[B.level][d];
       double dR[8];
@@ -1984,6 +2012,33 @@ cudaError_t launch_debug_fill_w(const StageArgs& a, int b0, int nb, double* T, c
   k_debug_fill_w<<<nb, 256, kDebugFillWSmem, st>>>(a, b0, nb, T);
   return cudaGetLastError();
 }
+// Checked build: read and clear the index-check flag (always 0 otherwise).
+cudaError_t read_index_flag(int32_t* out) {
+#ifdef BATS_CHECKED
+  cudaError_t e = cudaMemcpyFromSymbol(out, g_index_err, sizeof(int32_t));
+  const int32_t zero = 0;
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_index_err, &zero, sizeof(int32_t));
+  return e;
+#else
+  *out = 0;
+  return cudaSuccess;
+#endif
+}
+
+// Bounded-wait test hook: one thread waits on an mbarrier that nothing
+// arrives at; after the wait's limit it records ERR_TIMEOUT and returns.
+__global__ void k_debug_wait_timeout(int32_t* err) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_wait_bounded(&bar, 0, err);
+  }
+}
+cudaError_t launch_debug_wait_timeout(int32_t* err, cudaStream_t st) {
+  k_debug_wait_timeout<<<1, 32, 0, st>>>(err);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_check_conversions(const float* f, const double* d, int n, double* f2d_out, float* d2f_out) {
   k_check_conversions<<<(n + 255) / 256, 256>>>(f, d, n, f2d_out, d2f_out);
   return cudaGetLastError();
