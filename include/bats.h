@@ -281,7 +281,10 @@ int bats_mlp_create(const float* params, uint64_t seed, void* cuda_stream, bats_
 void bats_mlp_destroy(bats_mlp_t* m);
 int bats_mlp_set_params(bats_mlp_t* m, const float* params);
 int bats_mlp_get_params(bats_mlp_t* m, float* params);
-/* Y (n x 8) = network(X (n x 40)); host or device pointers. */
+/* Y (n x 8) = network(X (n x 40)); host or device pointers.  The inputs are
+ * rounded to BF16; the network runs on the tensor cores (tcgen05, FP32
+ * accumulation in tensor memory).  BATS_ERR_TIMEOUT if a bounded device wait
+ * ran out (the handle stays usable). */
 int bats_mlp_forward(bats_mlp_t* m, const float* X, int64_t n, float* Y);
 /* Loss L = (1/(8n)) sum (y - t)^2 over n samples (X n x 40, T n x 8) and its
  * gradient (grad nullable, BATS_MLP_NPARAM floats); inputs are rounded to

@@ -45,7 +45,8 @@ cudaError_t launch_debug_wait_timeout(int32_t* err, cudaStream_t st);
 cudaError_t mlp_alloc(MlpDev* w);
 void mlp_free(MlpDev* w);
 cudaError_t launch_mlp_pack(const float* P, const MlpDev& m, cudaStream_t st);
-cudaError_t launch_mlp_infer(const uint32_t* X, float* Y, int64_t n, const MlpDev& m, int nsm, cudaStream_t st);
+cudaError_t launch_mlp_infer(const uint32_t* X, float* Y, int64_t n, const MlpDev& m, int nsm, int32_t* err,
+                             cudaStream_t st);
 
 }  // namespace batsk
 
@@ -478,7 +479,8 @@ int launch_stage(bats_t* h, const StageArgs& a) {
   int rc = launch_stage_one(h, f);
   if (rc) return rc;
   h->launches++;
-  CK(h, launch_mlp_infer(h->Xb, h->Yb, static_cast<int64_t>(h->nbt) * 3 * NFACE, h->mlp, h->num_sms, h->stream));
+  CK(h, launch_mlp_infer(h->Xb, h->Yb, static_cast<int64_t>(h->nbt) * 3 * NFACE, h->mlp, h->num_sms, h->errw,
+                         h->stream));
   StageArgs u = a;
   u.learned = 1;
   u.Y = h->Yb;

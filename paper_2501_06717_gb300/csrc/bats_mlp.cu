@@ -1,13 +1,17 @@
 // bats_mlp.cu -- the learned flux correction's network on tensor cores:
 // a 40 -> 64 -> 64 -> 8 MLP with tanh-form GELU (Hendrycks & Gimpel), BF16
-// weights and activations, FP32 accumulation, on mma.sync m16n8k16 BF16.
+// weights and activations, FP32 accumulation.
 //
 //  * k_mlp_infer: Y = MLP(X) for face feature rows X (BF16, 48 columns: the
-//    40 features and 8 zeros); each warp carries 16-row tiles through the
-//    three layers with the accumulators of one layer re-packed in registers
-//    as the A operand of the next.
+//    40 features and 8 zeros) on the 5th-generation tensor cores: per CTA a
+//    persistent loop over 128-row tiles; each layer is a tcgen05.mma chain
+//    (M = 128, K = 16 per instruction) from shared-memory operands into a
+//    tensor-memory accumulator, whose rows the four warps read back
+//    (tcgen05.ld), add the bias to, pass through GELU and store as the next
+//    layer's BF16 operand.
 //  * k_mlp_train: the mean-squared-error loss and its gradient for a batch;
-//    forward and the backward data products on tensor cores, the weight
+//    forward and the backward data products on tensor cores (warp-level
+//    mma.sync m16n8k16 BF16, activations kept in registers), the weight
 //    gradients (outer products over the tile's samples) on the CUDA cores,
 //    accumulated per CTA in shared memory and once per CTA in global memory.
 //  * k_mlp_adam, k_mlp_pack: the Adam update of the FP32 master weights and
@@ -138,30 +142,242 @@ __device__ __forceinline__ void mlp_tile_forward(const MlpSmem& s, const uint32_
   for (int kt = 0; kt < 4; kt++) mma_bf16(y, a3[kt], s.w3[g * W3S + kt * 8 + t], s.w3[g * W3S + kt * 8 + 4 + t]);
 }
 
-// Y[n][8] = MLP(X[n][48] BF16).
-__global__ void __launch_bounds__(128) k_mlp_infer(const uint32_t* __restrict__ X, float* __restrict__ Y,
-                                                   int64_t n, MlpDev m) {
-  __shared__ MlpSmem s;
-  load_mlp_smem(m, s);
-  __syncthreads();
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const int64_t warp = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
-  for (int64_t r0 = warp * 16; r0 < n; r0 += nwarps * 16) {
-    const int64_t ra = r0 + g, rb = r0 + g + 8;
-    uint32_t a1[3][4];
+// ---------------------------------------------------------------------------
+// Inference on tcgen05.  Operands in shared memory use the no-swizzle K-major
+// canonical layout: "core matrices" of 8 rows x 16 bytes (8 BF16 along K)
+// stored as 128 contiguous bytes; core matrices adjacent along K are LBO =
+// 128 bytes apart, those adjacent along M (or N) SBO = 16 K bytes apart.
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+// byte offset of the 16-byte chunk (row r, K chunk kc) in a canonical tile
+__device__ __forceinline__ uint32_t cm_off(int r, int kc, uint32_t sbo) {
+  return static_cast<uint32_t>(r >> 3) * sbo + static_cast<uint32_t>(kc) * 128u + static_cast<uint32_t>(r & 7) * 16u;
+}
+// Shared-memory matrix descriptor: start address >> 4 (bits 0-13), LBO >> 4
+// (16-29), SBO >> 4 (32-45), the fixed value 1 in bits 46-48, base offset 0,
+// relative LBO, no swizzle (bits 61-63 = 0).
+__device__ __forceinline__ uint64_t umma_sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4) | (static_cast<uint64_t>(lbo >> 4) << 16) |
+         (static_cast<uint64_t>(sbo >> 4) << 32) | (1ull << 46);
+}
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16
+// A and B (bits 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 in
+// bits 17-22, M >> 4 in bits 24-28.
+constexpr uint32_t umma_idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+// D[tmem] (+)= A B^T for one K = 16 slice; accum = 0 overwrites D.
+__device__ __forceinline__ void umma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+      : "memory");
+}
+// The mbarrier completes one phase once every tcgen05.mma this thread issued
+// before has finished.
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void proxy_fence_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// 16 consecutive FP32 columns of this thread's tensor-memory lane (the wait
+// for the load sits in the same statement, so no use of the registers can be
+// scheduled ahead of it).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
 #pragma unroll
-    for (int kt = 0; kt < 3; kt++) {
-      a1[kt][0] = ra < n ? X[ra * 24 + kt * 8 + t] : 0u;
-      a1[kt][1] = rb < n ? X[rb * 24 + kt * 8 + t] : 0u;
-      a1[kt][2] = ra < n ? X[ra * 24 + kt * 8 + 4 + t] : 0u;
-      a1[kt][3] = rb < n ? X[rb * 24 + kt * 8 + 4 + t] : 0u;
+  for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void mbar_init_tc(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait_tc(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for an mbarrier phase for at most ~1 s of wall time; on expiry record
+// ERR_TIMEOUT and return false.
+__device__ __noinline__ bool mbar_wait_bounded_tc(uint64_t* bar, uint32_t parity, int32_t* err) {
+  if (mbar_try_wait_tc(bar, parity)) return true;
+  uint64_t t0, t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  while (true) {
+    if (mbar_try_wait_tc(bar, parity)) return true;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 > 1000000000ull) {
+      atomicOr(err, ERR_TIMEOUT);
+      return false;
     }
-    float z1[8][4], z2[8][4], y[4];
-    uint32_t a2[4][4], a3[4][4];
-    mlp_tile_forward<false>(s, a1, z1, z2, a2, a3, y);
-    if (ra < n) *reinterpret_cast<float2*>(Y + ra * 8 + 2 * t) = make_float2(y[0], y[1]);
-    if (rb < n) *reinterpret_cast<float2*>(Y + rb * 8 + 2 * t) = make_float2(y[2], y[3]);
+  }
+}
+
+constexpr int TC_TILE = 128;             // rows per tile (MMA M), one per thread
+constexpr uint32_t SBO_K48 = 768;        // 16 bytes x K = 48
+constexpr uint32_t SBO_K64 = 1024;       // 16 bytes x K = 64
+constexpr int TC_TMEM_COLS = 64;         // one FP32 accumulator of N = 64 (reused by all three layers)
+struct TcSmem {
+  alignas(128) uint8_t x[TC_TILE * 96];  // X tile, K = 48
+  alignas(128) uint8_t h[TC_TILE * 128]; // hidden activations, K = 64 (H1, then H2)
+  alignas(128) uint8_t w1[64 * 96];      // B of layer 1: N = 64, K = 48
+  alignas(128) uint8_t w2[64 * 128];     // B of layer 2: N = 64, K = 64
+  alignas(128) uint8_t w3[16 * 128];     // B of layer 3: N = 16 (8 outputs, 8 zero rows), K = 64
+  float b1[64], b2[64], b3[8];
+  uint64_t bar;
+  uint32_t tmem;
+};
+
+// Bias, GELU and BF16 rounding of this thread's accumulator row (64 columns
+// at taddr) into row `row` of the canonical K = 64 tile h.
+__device__ __forceinline__ void tc_hidden_row(uint32_t taddr, const float* bias, uint8_t* h, int row) {
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    float v[16];
+    tmem_ld16(taddr + 16 * q, v);
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+      uint4 o;
+      const float* b = bias + 16 * q + 8 * c;
+      const float* z = v + 8 * c;
+      o.x = pack_bf16(gelu_f(z[0] + b[0]), gelu_f(z[1] + b[1]));
+      o.y = pack_bf16(gelu_f(z[2] + b[2]), gelu_f(z[3] + b[3]));
+      o.z = pack_bf16(gelu_f(z[4] + b[4]), gelu_f(z[5] + b[5]));
+      o.w = pack_bf16(gelu_f(z[6] + b[6]), gelu_f(z[7] + b[7]));
+      *reinterpret_cast<uint4*>(h + cm_off(row, 2 * q + c, SBO_K64)) = o;
+    }
+  }
+}
+
+// Y[n][8] = MLP(X[n][48] BF16), 128 threads per CTA, persistent over tiles.
+// Thread 0 issues the MMAs; every wait is bounded (ERR_TIMEOUT in err), after
+// which the CTA waits once more for its MMAs, frees its tensor memory and
+// returns.
+__global__ void __launch_bounds__(128) k_mlp_infer(const uint32_t* __restrict__ X, float* __restrict__ Y,
+                                                   int64_t n, MlpDev m, int32_t* err) {
+  extern __shared__ __align__(128) unsigned char tc_smem_raw[];
+  TcSmem& s = *reinterpret_cast<TcSmem*>(tc_smem_raw);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  // weights into the canonical layouts (16-byte chunks), biases
+  for (int e = tid; e < 64 * 6; e += 128) {
+    const int r = e / 6, kc = e % 6;
+    *reinterpret_cast<uint4*>(s.w1 + cm_off(r, kc, SBO_K48)) = *reinterpret_cast<const uint4*>(m.w1 + r * 24 + kc * 4);
+  }
+  for (int e = tid; e < 64 * 8; e += 128) {
+    const int r = e / 8, kc = e % 8;
+    *reinterpret_cast<uint4*>(s.w2 + cm_off(r, kc, SBO_K64)) = *reinterpret_cast<const uint4*>(m.w2 + r * 32 + kc * 4);
+  }
+  for (int e = tid; e < 16 * 8; e += 128) {
+    const int r = e / 8, kc = e % 8;
+    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+    *reinterpret_cast<uint4*>(s.w3 + cm_off(r, kc, SBO_K64)) =
+        r < 8 ? *reinterpret_cast<const uint4*>(m.w3 + r * 32 + kc * 4) : z;
+  }
+  if (tid < 64) {
+    s.b1[tid] = m.b1[tid];
+    s.b2[tid] = m.b2[tid];
+  }
+  if (tid < 8) s.b3[tid] = m.b3[tid];
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s.tmem)),
+                 "r"(TC_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) mbar_init_tc(&s.bar);
+  proxy_fence_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s.tmem;
+  const uint32_t trow = tmem + (static_cast<uint32_t>(warp * 32) << 16);  // this warp's 32 lanes
+  const uint32_t xs = smem_u32(s.x), hs = smem_u32(s.h);
+  const uint32_t w1s = smem_u32(s.w1), w2s = smem_u32(s.w2), w3s = smem_u32(s.w3);
+  constexpr uint32_t ID64 = umma_idesc_bf16(TC_TILE, 64), ID16 = umma_idesc_bf16(TC_TILE, 16);
+  uint32_t phase = 0;
+  bool failed = false;
+  const int64_t ntiles = (n + TC_TILE - 1) / TC_TILE;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t row = tile * TC_TILE + tid;
+    // this thread's input row into the canonical K = 48 tile (zeros past n)
+    uint4 xv[6];
+#pragma unroll
+    for (int k = 0; k < 6; k++) xv[k] = make_uint4(0u, 0u, 0u, 0u);
+    if (row < n) {
+      const uint4* src = reinterpret_cast<const uint4*>(X + row * 24);
+#pragma unroll
+      for (int k = 0; k < 6; k++) xv[k] = src[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 6; k++) *reinterpret_cast<uint4*>(s.x + cm_off(tid, k, SBO_K48)) = xv[k];
+#pragma unroll 1
+    for (int layer = 0; layer < 3; layer++) {
+      // operands written by the threads -> visible to the tensor cores
+      proxy_fence_smem();
+      tc_fence_before();
+      __syncthreads();
+      if (tid == 0) {
+        tc_fence_after();
+        if (layer == 0) {
+#pragma unroll
+          for (int k = 0; k < 3; k++)
+            umma_bf16(tmem, umma_sdesc(xs + 256 * k, 128, SBO_K48), umma_sdesc(w1s + 256 * k, 128, SBO_K48), ID64,
+                      k > 0);
+        } else {
+          const uint32_t ws = layer == 1 ? w2s : w3s;
+#pragma unroll
+          for (int k = 0; k < 4; k++)
+            umma_bf16(tmem, umma_sdesc(hs + 256 * k, 128, SBO_K64), umma_sdesc(ws + 256 * k, 128, SBO_K64),
+                      layer == 1 ? ID64 : ID16, k > 0);
+        }
+        umma_commit(&s.bar);
+      }
+      const bool got = mbar_wait_bounded_tc(&s.bar, phase, err);
+      if (__syncthreads_or(!got)) {
+        failed = true;
+        break;
+      }
+      phase ^= 1u;
+      tc_fence_after();
+      if (layer < 2) {
+        tc_hidden_row(trow, layer == 0 ? s.b1 : s.b2, s.h, tid);
+      } else {
+        float v[16];
+        tmem_ld16(trow, v);
+        if (row < n) {
+          float4* dst = reinterpret_cast<float4*>(Y + row * 8);
+          dst[0] = make_float4(v[0] + s.b3[0], v[1] + s.b3[1], v[2] + s.b3[2], v[3] + s.b3[3]);
+          dst[1] = make_float4(v[4] + s.b3[4], v[5] + s.b3[5], v[6] + s.b3[6], v[7] + s.b3[7]);
+        }
+      }
+    }
+    if (failed) break;
+  }
+  // an MMA may still run after a timed-out wait: wait for it once more
+  if (failed && tid == 0) mbar_wait_bounded_tc(&s.bar, phase, err);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
   }
 }
 
@@ -383,11 +599,16 @@ cudaError_t launch_mlp_pack(const float* P, const MlpDev& m, cudaStream_t st) {
   k_mlp_pack<<<8, 256, 0, st>>>(P, m);
   return cudaGetLastError();
 }
-cudaError_t launch_mlp_infer(const uint32_t* X, float* Y, int64_t n, const MlpDev& m, int nsm, cudaStream_t st) {
+// X: n rows of 24 words (16-byte aligned), Y: n rows of 8 floats (16-byte
+// aligned); 4 CTAs per SM at most (shared memory 45 KB, tensor memory 64 of
+// the SM's 512 columns each).
+cudaError_t launch_mlp_infer(const uint32_t* X, float* Y, int64_t n, const MlpDev& m, int nsm, int32_t* err,
+                             cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  int64_t tiles = (n + 15) / 16;
-  int grid = static_cast<int>(std::min<int64_t>((tiles + 3) / 4, static_cast<int64_t>(nsm) * 8));
-  k_mlp_infer<<<grid, 128, 0, st>>>(X, Y, n, m);
+  if ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Y)) & 15u) return cudaErrorInvalidValue;
+  const int64_t tiles = (n + TC_TILE - 1) / TC_TILE;
+  const int grid = static_cast<int>(std::min<int64_t>(tiles, static_cast<int64_t>(nsm) * 4));
+  k_mlp_infer<<<grid, 128, sizeof(TcSmem), st>>>(X, Y, n, m, err);
   return cudaGetLastError();
 }
 cudaError_t launch_mlp_train(const float* X, const float* T, int64_t n, const MlpDev& m, float* grad, double* loss,
@@ -462,6 +683,7 @@ struct bats_mlp {
   float *X = nullptr, *T = nullptr, *Y = nullptr;
   uint32_t* Xb = nullptr;
   int64_t cap = 0;
+  int32_t* errw = nullptr;  // device error bits of the inference kernel (ERR_TIMEOUT)
 };
 
 namespace {
@@ -533,6 +755,8 @@ int bats_mlp_create(const float* params, uint64_t seed, void* cuda_stream, bats_
   if (e == cudaSuccess) e = mlp_setup();
   if (e == cudaSuccess) e = cudaMalloc(&m->P, sizeof(float) * MLP_NPARAM * 4);
   if (e == cudaSuccess) e = cudaMalloc(&m->loss, sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&m->errw, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemset(m->errw, 0, sizeof(int32_t));
   if (e == cudaSuccess) e = mlp_alloc(&m->w);
   if (e != cudaSuccess) {
     bats_mlp_destroy(m);
@@ -562,6 +786,7 @@ void bats_mlp_destroy(bats_mlp_t* m) {
   if (m->stream) cudaStreamSynchronize(m->stream);
   cudaFree(m->P);
   cudaFree(m->loss);
+  cudaFree(m->errw);
   cudaFree(m->X);
   cudaFree(m->T);
   cudaFree(m->Y);
@@ -594,12 +819,19 @@ int bats_mlp_forward(bats_mlp_t* m, const float* X, int64_t n, float* Y) {
   if (rc) return rc;
   if ((rc = copy_in(m, m->X, X, static_cast<size_t>(n) * 40))) return rc;
   cudaError_t e = launch_rows_to_bf16(m->X, m->Xb, n, m->stream);
-  if (e == cudaSuccess) e = launch_mlp_infer(m->Xb, m->Y, n, m->w, m->nsm, m->stream);
+  if (e == cudaSuccess) e = launch_mlp_infer(m->Xb, m->Y, n, m->w, m->nsm, m->errw, m->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(Y, m->Y, sizeof(float) * n * 8, dev_ptr(Y) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                         m->stream);
+  int32_t eb = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&eb, m->errw, sizeof(int32_t), cudaMemcpyDeviceToHost, m->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
-  return e == cudaSuccess ? BATS_OK : BATS_ERR_CUDA;
+  if (e != cudaSuccess) return BATS_ERR_CUDA;
+  if (eb) {
+    cudaMemsetAsync(m->errw, 0, sizeof(int32_t), m->stream);
+    return BATS_ERR_TIMEOUT;
+  }
+  return BATS_OK;
 }
 
 int bats_mlp_loss_grad(bats_mlp_t* m, const float* X, const float* T, int64_t n, float* grad, double* loss) {
