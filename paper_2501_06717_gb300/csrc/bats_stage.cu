@@ -1097,6 +1097,13 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1) k_sta
             for (int v = 0; v < NV; v++) bulk_g2s(sT + v * NTILE + NCELL + f * 128, g + v * 128, 128 * sizeof(float), &bar);
           }
         }
+        // this CTA's next block: its interior on its way to L2 while this
+        // block is computed, so that its bulk copies read L2, not HBM
+        const int nblk = blk + 1 < b_end ? blk + 1 : (item + static_cast<int>(gridDim.x)) * a.blocks_per_item;
+        if (nblk < a.nblocks) {
+          const R* nsrc = MIXED ? reinterpret_cast<const R*>(a.Win) : reinterpret_cast<const R*>(a.Uin);
+          prefetch_l2(nsrc + static_cast<int64_t>(nblk) * (NV * NCELL), NV * NCELL * sizeof(R));
+        }
         // the FP64 states the cell phase reads, on their way to L2 meanwhile
         const int64_t boff = static_cast<int64_t>(blk) * (NV * NCELL);
         const bool reads_ubase = a.kind < 3 && !(MIXED && a.kind == 0 && !a.last && !a.write_u_all);
