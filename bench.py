@@ -174,7 +174,8 @@ def learned_form_summary(stream, steps=32):
     scheme at 1x and 2x (960 blocks), fixed dt, FP64 and mixed forms; times
     from CUDA events around graph replays of `steps` coarse steps (2 * steps
     fine).  Errors are against the plain 2x run of the same precision,
-    restricted to 1x."""
+    restricted to 1x, and (FP64) against a plain 4x run restricted to 1x, which
+    also scores the plain 2x run."""
     import torch
     from paper_2501_06717_gb300 import bats, learn
     t0 = time.perf_counter()
@@ -183,6 +184,7 @@ def learned_form_summary(stream, steps=32):
     t_train = time.perf_counter() - t0
     e_plain, e_learn = learn.evaluate(P, nsteps=16)
     e_plain_m, e_learn_m = learn.evaluate(P, nsteps=16, precision=bats.BATS_MIXED)
+    e4 = learn.evaluate_4x(P, nsteps=16)
     coarse, fine = W.blast(), W.blast(resolution=2)
 
     def timed(prob, params, nsteps, dt, precision):
@@ -213,6 +215,7 @@ def learned_form_summary(stream, steps=32):
             "pairs": int(X.shape[0]), "train_s": t_train, "loss_first_last_epoch": [hist[0], hist[-1]],
             "error_vs_restricted_2x": {"plain_1x": e_plain, "learned_1x": e_learn,
                                        "plain_1x_mixed": e_plain_m, "learned_1x_mixed": e_learn_m},
+            "error_vs_restricted_4x_fp64": e4,
             "ms_per_coarse_step": ms,
             "cell_updates_per_s_learned_1x": {k: coarse.ncells / (v["learned_1x"] * 1e-3) for k, v in ms.items()}}
 

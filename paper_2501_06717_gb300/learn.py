@@ -17,7 +17,10 @@ sqrt(rho_ref) c_ref^2, rho_ref c_ref^3).
 Training: Adam on the GPU (bats_mlp_train_step), minibatches of face samples.
 
 Evaluation: the coarse grid with and without the network against the fine run
-restricted to the coarse grid, at the same time and fixed dt.
+restricted to the coarse grid, at the same time and fixed dt; and (evaluate_4x)
+the coarse runs and the plain fine run against a run at 4x restricted to the
+coarse grid, which places the learned coarse run between the plain coarse and
+the plain fine resolution.
 """
 import math
 
@@ -193,3 +196,41 @@ def evaluate(params, nsteps=16, cfl=0.8, precision=B.BATS_FP64, dt_safety=0.5):
         return float(np.mean(e[keep] / d[keep]))
 
     return err(U_plain), err(U_learn)
+
+
+def evaluate_4x(params, nsteps=16, cfl=0.8, precision=B.BATS_FP64, dt_safety=0.5):
+    """Errors against the plain run at 4x (every coarse leaf refined twice,
+    7,680 blocks) restricted to the coarse grid, on the exact blast from the 4x
+    initial state restricted to each resolution, fixed dt (dt_c, dt_c / 2,
+    dt_c / 4).  Returns {"plain_1x", "learned_1x", "plain_2x"}, each the mean
+    over the 8 variables of ||U - U_ref||_1 / ||U_ref - U_0||_1."""
+    coarse, fine, fine4 = W.blast(), W.blast(resolution=2), W.blast(resolution=4)
+    C12, C24 = children_map(coarse, fine), children_map(fine, fine4)
+    U2_0 = restrict_state(fine4.U0, C24)
+    U1_0 = restrict_state(U2_0, C12)
+    with B.Solver(coarse, precision=precision) as s:
+        s.set_state(0, U1_0)
+        dtc = dt_safety * s.dt(0, cfl)
+        s.step_dt(nsteps, dtc)
+        U_plain = s.get_state(0)
+    with B.Solver(coarse, precision=precision) as s:
+        s.set_mlp(params)
+        s.set_state(0, U1_0)
+        s.step_dt(nsteps, dtc)
+        U_learn = s.get_state(0)
+    with B.Solver(fine, precision=precision) as s:
+        s.set_state(0, U2_0)
+        s.step_dt(2 * nsteps, 0.5 * dtc)
+        U_2x = restrict_state(s.get_state(0), C12)
+    with B.Solver(fine4, precision=precision) as s:
+        s.set_state(0, fine4.U0)
+        s.step_dt(4 * nsteps, 0.25 * dtc)
+        U_ref = restrict_state(restrict_state(s.get_state(0), C24), C12)
+
+    def err(U):
+        e = np.abs(U - U_ref).reshape(8, -1).sum(1)
+        d = np.abs(U_ref - U1_0).reshape(8, -1).sum(1)
+        keep = d > 1e-12 * np.abs(U_ref).reshape(8, -1).sum(1)
+        return float(np.mean(e[keep] / d[keep]))
+
+    return {"plain_1x": err(U_plain), "learned_1x": err(U_learn), "plain_2x": err(U_2x)}

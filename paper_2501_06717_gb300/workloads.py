@@ -251,7 +251,8 @@ def orszag_tang(nsteps=10):
 def blast(resolution=1, nsteps=100, limiter=LIM_MC, pin=10.0, centre=(0.0, 0.0, 0.0), bdir=(1.0, 1.0, 0.0),
           roots_per_axis=4):
     """Spherical MHD blast on [-1,1]^3: root blocks refined once where the
-    block intersects r < 0.4; resolution=2 refines every leaf once more."""
+    block intersects r < 0.4; resolution=2 (4) refines every leaf once (twice)
+    more."""
     root = (roots_per_axis,) * 3
     lo, hi = (-1.0,) * 3, (1.0,) * 3
     leaves = uniform_leaves(root)
@@ -261,11 +262,13 @@ def blast(resolution=1, nsteps=100, limiter=LIM_MC, pin=10.0, centre=(0.0, 0.0, 
         return float(np.sqrt(np.sum(q * q))) < 0.4
 
     leaves = refine_where(leaves, hits, lo, hi, root, 1)
-    if resolution == 2:
+    if resolution not in (1, 2, 4):
+        raise ValueError("blast: resolution must be 1, 2 or 4")
+    for _ in range({1: 0, 2: 1, 4: 2}[resolution]):
         leaves = [c for lf in leaves for c in _children(lf)]
     leaves = balance(leaves, root, (False,) * 3)
     leaves = as_leaf_array(morton_sort(leaves))
-    prob = Problem("blast" if resolution == 1 else "blast_x2", lo, hi, root, leaves, (BC_OUTFLOW,) * 6,
+    prob = Problem("blast" if resolution == 1 else "blast_x%d" % resolution, lo, hi, root, leaves, (BC_OUTFLOW,) * 6,
                    gamma=5.0 / 3.0, limiter=limiter, cfl=0.8, nsteps=nsteps)
     x, y, z = cell_centres(lo, hi, root, leaves)
     r = np.sqrt((x - centre[0]) ** 2 + (y - centre[1]) ** 2 + (z - centre[2]) ** 2)
