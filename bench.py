@@ -43,7 +43,7 @@ BYTES_PER_CELL_UPDATE = 320  # FP64 state: stage 1 reads U^n, writes U*; stage 2
 # in profiles/ (None until a capture of the current kernel source exists).
 NCU_TRAFFIC = {
     # precision: (DRAM bytes per cell per launch, mean of the two stages, sha256 of bats_stage.cu at capture)
-    "mixed": (121.6, "d807c01b7461a089c18fc75ba6f3340a2aa15a751730d37a6b7f612f7be4515b"),
+    "mixed": (122.2, "4dbb1fc86d9fd9a88193b1d17ad547531c655a48e3ac634c04e9608d3aaefb21"),
 }
 
 
