@@ -315,19 +315,25 @@ __global__ void __launch_bounds__(128) k_mlp_infer(const uint32_t* __restrict__ 
   uint32_t phase = 0;
   bool failed = false;
   const int64_t ntiles = (n + TC_TILE - 1) / TC_TILE;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t row = tile * TC_TILE + tid;
-    // this thread's input row into the canonical K = 48 tile (zeros past n)
-    uint4 xv[6];
+  // this thread's input row, loaded one tile ahead (zeros past n)
+  auto load_row = [&](int64_t r, uint4 xv[6]) {
 #pragma unroll
     for (int k = 0; k < 6; k++) xv[k] = make_uint4(0u, 0u, 0u, 0u);
-    if (row < n) {
-      const uint4* src = reinterpret_cast<const uint4*>(X + row * 24);
+    if (r < n) {
+      const uint4* src = reinterpret_cast<const uint4*>(X + r * 24);
 #pragma unroll
       for (int k = 0; k < 6; k++) xv[k] = src[k];
     }
+  };
+  uint4 xn[6];
+  load_row(static_cast<int64_t>(blockIdx.x) * TC_TILE + tid, xn);
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t row = tile * TC_TILE + tid;
+    // the row into the canonical K = 48 tile; the next tile's row on its way
+    // while this tile runs through the three layers
 #pragma unroll
-    for (int k = 0; k < 6; k++) *reinterpret_cast<uint4*>(s.x + cm_off(tid, k, SBO_K48)) = xv[k];
+    for (int k = 0; k < 6; k++) *reinterpret_cast<uint4*>(s.x + cm_off(tid, k, SBO_K48)) = xn[k];
+    load_row(row + static_cast<int64_t>(gridDim.x) * TC_TILE, xn);
 #pragma unroll 1
     for (int layer = 0; layer < 3; layer++) {
       // operands written by the threads -> visible to the tensor cores

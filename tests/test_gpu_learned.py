@@ -57,6 +57,41 @@ def test_network_forward_matches_oracle(B):
     assert _relnorm(Y, Yo) <= 2e-2
 
 
+def _forward_bf16_reference(P, X):
+    """The network in numpy as the kernels evaluate it: BF16 weights and
+    inputs, sums in FP64, bias, tanh-form GELU, hidden activations rounded
+    to BF16 before the next layer."""
+    W1, b1 = P[:2560].reshape(64, 40).astype(float), P[2560:2624].astype(float)
+    W2, b2 = P[2624:6720].reshape(64, 64).astype(float), P[6720:6784].astype(float)
+    W3, b3 = P[6784:7296].reshape(8, 64).astype(float), P[7296:7304].astype(float)
+
+    def gelu(z):
+        return 0.5 * z * (1.0 + np.tanh(0.7978845608028654 * (z + 0.044715 * z ** 3)))
+
+    h1 = bf16(gelu(X.astype(float) @ W1.T + b1)).astype(float)
+    h2 = bf16(gelu(h1 @ W2.T + b2)).astype(float)
+    return h2 @ W3.T + b3
+
+
+@pytest.mark.parametrize("n", [1, 127, 128, 129, 200003])
+def test_network_forward_ragged_sizes(B, n):
+    """The tensor-core forward runs 128-row tiles (persistent CTAs take several
+    tiles at the largest size): every row, the ragged last tile included,
+    matches the numpy evaluation of the same BF16 network."""
+    P = _net(11)
+    rng = np.random.default_rng(n)
+    X = bf16(rng.normal(size=(n, 40)))
+    m = B.Mlp(P)
+    Y = m.forward(X)
+    m.close()
+    Yr = _forward_bf16_reference(P, X)
+    assert Y.shape == (n, 8) and np.isfinite(Y).all()
+    # a hidden activation may round to the other BF16 neighbour when the two
+    # FP32/FP64 sums straddle a rounding boundary: a few 2^-8 per row at most
+    assert (np.abs(Y - Yr).max(axis=1) / np.abs(Yr).max()).max() <= 2e-2
+    assert _relnorm(Y, Yr) <= 2e-3
+
+
 def test_network_gradient_matches_oracle(B):
     P = _net(3)
     rng = np.random.default_rng(4)
