@@ -434,14 +434,18 @@ StageArgs base_args(bats_t* h) {
   return a;
 }
 
-int launch_stage_one(bats_t* h, const StageArgs& a0) {
+// make_ghosts = false: the ghost slabs in gbuf already hold this stage input's
+// values (the learned form's second launch of a stage reads the same input).
+int launch_stage_one(bats_t* h, const StageArgs& a0, bool make_ghosts = true) {
   bool mixed = h->ph.precision == BATS_MIXED;
   StageArgs a = a0;
   if (mixed && h->gbuf) {
     // the ghost slabs of faces at resolution changes, from this stage's input
     a.gbuf = h->gbuf;
-    h->launches++;
-    CK(h, launch_amr_ghosts(a, h->gtasks_d, static_cast<int>(h->gtasks_h.size()), h->stream));
+    if (make_ghosts) {
+      h->launches++;
+      CK(h, launch_amr_ghosts(a, h->gtasks_d, static_cast<int>(h->gtasks_h.size()), h->stream));
+    }
   }
   int nitems = (a.nblocks + a.blocks_per_item - 1) / a.blocks_per_item;
   int grid = nitems;
@@ -465,8 +469,9 @@ int launch_reflux(bats_t* h, const StageArgs& a) {
   return BATS_OK;
 }
 
-// One stage; with the learned form, three launches: the network inputs of
-// every face, the network, and the stage with the correction.
+// One stage; with the learned form, three launches (after the mixed form's
+// ghost pre-pass, made once): the network inputs of every face, the network,
+// and the stage with the correction.
 int launch_stage(bats_t* h, const StageArgs& a) {
   if (!h->learned || a.kind >= 3) {
     int rc = launch_stage_one(h, a);
@@ -484,7 +489,7 @@ int launch_stage(bats_t* h, const StageArgs& a) {
   StageArgs u = a;
   u.learned = 1;
   u.Y = h->Yb;
-  return launch_stage_one(h, u);
+  return launch_stage_one(h, u, false);  // same stage input: the ghost slabs are in place
 }
 
 // CFL bound of grid g's current state into smax[g]; with dtc, also every

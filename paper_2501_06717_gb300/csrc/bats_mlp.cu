@@ -165,7 +165,7 @@ __device__ __forceinline__ uint64_t umma_sdesc(uint32_t saddr, uint32_t lbo, uin
 // Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16
 // A and B (bits 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 in
 // bits 17-22, M >> 4 in bits 24-28.
-constexpr uint32_t umma_idesc_bf16(int M, int N) {
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
          (static_cast<uint32_t>(M >> 4) << 24);
 }
@@ -231,7 +231,7 @@ __device__ __noinline__ bool mbar_wait_bounded_tc(uint64_t* bar, uint32_t parity
   }
 }
 
-constexpr int TC_TILE = 128;             // rows per tile (MMA M), one per thread
+constexpr int TC_TILE = 128;             // rows per tile (MMA M = tensor-memory lanes)
 constexpr uint32_t SBO_K48 = 768;        // 16 bytes x K = 48
 constexpr uint32_t SBO_K64 = 1024;       // 16 bytes x K = 64
 constexpr int TC_TMEM_COLS = 64;         // one FP32 accumulator of N = 64 (reused by all three layers)
@@ -246,46 +246,51 @@ struct TcSmem {
   uint32_t tmem;
 };
 
-// Bias, GELU and BF16 rounding of this thread's accumulator row (64 columns
-// at taddr) into row `row` of the canonical K = 64 tile h.
-__device__ __forceinline__ void tc_hidden_row(uint32_t taddr, const float* bias, uint8_t* h, int row) {
+// Bias, GELU and BF16 rounding of 32 accumulator columns c0..c0+31 of this
+// thread's lane (at taddr) into row `row` of the canonical K = 64 tile h.
+__device__ __forceinline__ void tc_hidden_cols(uint32_t taddr, const float* bias, uint8_t* h, int row, int c0) {
 #pragma unroll
-  for (int q = 0; q < 4; q++) {
+  for (int q = 0; q < 2; q++) {
     float v[16];
     tmem_ld16(taddr + 16 * q, v);
 #pragma unroll
     for (int c = 0; c < 2; c++) {
       uint4 o;
-      const float* b = bias + 16 * q + 8 * c;
+      const float* b = bias + c0 + 16 * q + 8 * c;
       const float* z = v + 8 * c;
       o.x = pack_bf16(gelu_f(z[0] + b[0]), gelu_f(z[1] + b[1]));
       o.y = pack_bf16(gelu_f(z[2] + b[2]), gelu_f(z[3] + b[3]));
       o.z = pack_bf16(gelu_f(z[4] + b[4]), gelu_f(z[5] + b[5]));
       o.w = pack_bf16(gelu_f(z[6] + b[6]), gelu_f(z[7] + b[7]));
-      *reinterpret_cast<uint4*>(h + cm_off(row, 2 * q + c, SBO_K64)) = o;
+      *reinterpret_cast<uint4*>(h + cm_off(row, c0 / 8 + 2 * q + c, SBO_K64)) = o;
     }
   }
 }
 
-// Y[n][8] = MLP(X[n][48] BF16), 128 threads per CTA, persistent over tiles.
-// Thread 0 issues the MMAs; every wait is bounded (ERR_TIMEOUT in err), after
-// which the CTA waits once more for its MMAs, frees its tensor memory and
-// returns.
-__global__ void __launch_bounds__(128) k_mlp_infer(const uint32_t* __restrict__ X, float* __restrict__ Y,
-                                                   int64_t n, MlpDev m, int32_t* err) {
+// Y[n][8] = MLP(X[n][48] BF16), 256 threads per CTA, persistent over tiles.
+// Warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (the tile rows it may
+// access) and accumulator columns 32 (w / 4) .. + 31, so two warps share each
+// row's epilogue.  Thread 0 issues the MMAs; every wait is bounded
+// (ERR_TIMEOUT in err), after which the CTA waits once more for its MMAs,
+// frees its tensor memory and returns.
+constexpr int TC_THREADS = 256;
+__global__ void __launch_bounds__(TC_THREADS, 4) k_mlp_infer(const uint32_t* __restrict__ X, float* __restrict__ Y,
+                                                             int64_t n, MlpDev m, int32_t* err) {
   extern __shared__ __align__(128) unsigned char tc_smem_raw[];
   TcSmem& s = *reinterpret_cast<TcSmem*>(tc_smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5;
+  const int lg = warp & 3, ch = warp >> 2;   // lane group, column half
+  const int trow = 32 * lg + (tid & 31);     // the tile row of this thread's lane
   // weights into the canonical layouts (16-byte chunks), biases
-  for (int e = tid; e < 64 * 6; e += 128) {
+  for (int e = tid; e < 64 * 6; e += TC_THREADS) {
     const int r = e / 6, kc = e % 6;
     *reinterpret_cast<uint4*>(s.w1 + cm_off(r, kc, SBO_K48)) = *reinterpret_cast<const uint4*>(m.w1 + r * 24 + kc * 4);
   }
-  for (int e = tid; e < 64 * 8; e += 128) {
+  for (int e = tid; e < 64 * 8; e += TC_THREADS) {
     const int r = e / 8, kc = e % 8;
     *reinterpret_cast<uint4*>(s.w2 + cm_off(r, kc, SBO_K64)) = *reinterpret_cast<const uint4*>(m.w2 + r * 32 + kc * 4);
   }
-  for (int e = tid; e < 16 * 8; e += 128) {
+  for (int e = tid; e < 16 * 8; e += TC_THREADS) {
     const int r = e / 8, kc = e % 8;
     const uint4 z = make_uint4(0u, 0u, 0u, 0u);
     *reinterpret_cast<uint4*>(s.w3 + cm_off(r, kc, SBO_K64)) =
@@ -308,32 +313,33 @@ __global__ void __launch_bounds__(128) k_mlp_infer(const uint32_t* __restrict__ 
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = s.tmem;
-  const uint32_t trow = tmem + (static_cast<uint32_t>(warp * 32) << 16);  // this warp's 32 lanes
+  const uint32_t tlanes = tmem + (static_cast<uint32_t>(32 * lg) << 16);  // this warp's 32 lanes
   const uint32_t xs = smem_u32(s.x), hs = smem_u32(s.h);
   const uint32_t w1s = smem_u32(s.w1), w2s = smem_u32(s.w2), w3s = smem_u32(s.w3);
   constexpr uint32_t ID64 = umma_idesc_bf16(TC_TILE, 64), ID16 = umma_idesc_bf16(TC_TILE, 16);
   uint32_t phase = 0;
   bool failed = false;
   const int64_t ntiles = (n + TC_TILE - 1) / TC_TILE;
-  // this thread's input row, loaded one tile ahead (zeros past n)
-  auto load_row = [&](int64_t r, uint4 xv[6]) {
+  // input: thread tid carries half (three 16-byte chunks) of row tid % 128,
+  // loaded one tile ahead (zeros past n)
+  const int xr = tid & (TC_TILE - 1), xk0 = 3 * (tid / TC_TILE);
+  auto load_part = [&](int64_t r, uint4 xv[3]) {
 #pragma unroll
-    for (int k = 0; k < 6; k++) xv[k] = make_uint4(0u, 0u, 0u, 0u);
+    for (int k = 0; k < 3; k++) xv[k] = make_uint4(0u, 0u, 0u, 0u);
     if (r < n) {
-      const uint4* src = reinterpret_cast<const uint4*>(X + r * 24);
+      const uint4* src = reinterpret_cast<const uint4*>(X + r * 24) + xk0;
 #pragma unroll
-      for (int k = 0; k < 6; k++) xv[k] = src[k];
+      for (int k = 0; k < 3; k++) xv[k] = src[k];
     }
   };
-  uint4 xn[6];
-  load_row(static_cast<int64_t>(blockIdx.x) * TC_TILE + tid, xn);
+  uint4 xn[3];
+  load_part(static_cast<int64_t>(blockIdx.x) * TC_TILE + xr, xn);
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t row = tile * TC_TILE + tid;
-    // the row into the canonical K = 48 tile; the next tile's row on its way
-    // while this tile runs through the three layers
+    // the input chunks into the canonical K = 48 tile; the next tile's on
+    // their way while this tile runs through the three layers
 #pragma unroll
-    for (int k = 0; k < 6; k++) *reinterpret_cast<uint4*>(s.x + cm_off(tid, k, SBO_K48)) = xn[k];
-    load_row(row + static_cast<int64_t>(gridDim.x) * TC_TILE, xn);
+    for (int k = 0; k < 3; k++) *reinterpret_cast<uint4*>(s.x + cm_off(xr, xk0 + k, SBO_K48)) = xn[k];
+    load_part(tile * TC_TILE + xr + static_cast<int64_t>(gridDim.x) * TC_TILE, xn);
 #pragma unroll 1
     for (int layer = 0; layer < 3; layer++) {
       // operands written by the threads -> visible to the tensor cores
@@ -364,10 +370,11 @@ __global__ void __launch_bounds__(128) k_mlp_infer(const uint32_t* __restrict__ 
       phase ^= 1u;
       tc_fence_after();
       if (layer < 2) {
-        tc_hidden_row(trow, layer == 0 ? s.b1 : s.b2, s.h, tid);
-      } else {
+        tc_hidden_cols(tlanes + 32 * ch, layer == 0 ? s.b1 : s.b2, s.h, trow, 32 * ch);
+      } else if (ch == 0) {
         float v[16];
-        tmem_ld16(trow, v);
+        tmem_ld16(tlanes, v);
+        const int64_t row = tile * TC_TILE + trow;
         if (row < n) {
           float4* dst = reinterpret_cast<float4*>(Y + row * 8);
           dst[0] = make_float4(v[0] + s.b3[0], v[1] + s.b3[1], v[2] + s.b3[2], v[3] + s.b3[3]);
@@ -614,7 +621,7 @@ cudaError_t launch_mlp_infer(const uint32_t* X, float* Y, int64_t n, const MlpDe
   if ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Y)) & 15u) return cudaErrorInvalidValue;
   const int64_t tiles = (n + TC_TILE - 1) / TC_TILE;
   const int grid = static_cast<int>(std::min<int64_t>(tiles, static_cast<int64_t>(nsm) * 4));
-  k_mlp_infer<<<grid, 128, sizeof(TcSmem), st>>>(X, Y, n, m, err);
+  k_mlp_infer<<<grid, TC_THREADS, sizeof(TcSmem), st>>>(X, Y, n, m, err);
   return cudaGetLastError();
 }
 cudaError_t launch_mlp_train(const float* X, const float* T, int64_t n, const MlpDev& m, float* grad, double* loss,
