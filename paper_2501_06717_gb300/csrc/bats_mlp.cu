@@ -6,9 +6,9 @@
 //    40 features and 8 zeros) on the 5th-generation tensor cores: per CTA a
 //    persistent loop over 128-row tiles; each layer is a tcgen05.mma chain
 //    (M = 128, K = 16 per instruction) from shared-memory operands into a
-//    tensor-memory accumulator, whose rows the four warps read back
-//    (tcgen05.ld), add the bias to, pass through GELU and store as the next
-//    layer's BF16 operand.
+//    tensor-memory accumulator, which eight warps read back (tcgen05.ld;
+//    two warps per row, 32 columns each), add the bias to, pass through GELU
+//    and store as the next layer's BF16 operand.
 //  * k_mlp_train: the mean-squared-error loss and its gradient for a batch;
 //    forward and the backward data products on tensor cores (warp-level
 //    mma.sync m16n8k16 BF16, activations kept in registers), the weight
