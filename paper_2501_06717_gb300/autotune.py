@@ -14,6 +14,8 @@ from . import bats as B
 DEFAULT_CANDIDATES = [
     (0, 1, 0),
     (0, 2, 0),
+    (0, 4, 0),
+    (0, 8, 0),
     (1, 1, 0),
     (1, 2, 0),
     (1, 4, 0),
