@@ -1,8 +1,10 @@
 """The benchmark's workload at full size (64 grids, 60,194 blocks, 30.8 M
-cells) in the launch form the benchmark times (one non-persistent launch per
-stage, whole steps replayed from a CUDA graph): one step of the whole batch on
-the GPU, checked grid by grid against the oracle on a sample of the grids (the
-largest, the smallest and two others), in both precisions."""
+cells) in the launch forms the benchmark's autotuner chooses between (one
+block or four consecutive blocks per non-persistent CTA, four per persistent
+CTA; whole steps replayed from a CUDA graph), and in the form the autotuner
+itself picks on this GPU: one step of the whole batch, checked grid by grid
+against the oracle on a sample of the grids (the largest, the smallest and
+two others), in both precisions."""
 import os
 
 import numpy as np
@@ -29,20 +31,44 @@ def _scaled(g, o):
     return np.abs(g - o).max(1) / s
 
 
-@pytest.mark.parametrize("prec,tol", [(1, 1e-5), (0, 1e-12)])
-def test_full_batched_workload_sampled_against_the_oracle(grids, prec, tol):
-    from paper_2501_06717_gb300 import bats as B
-    assert sum(p.nb for p in grids) == 60194
+def _sample(grids):
     sizes = np.array([p.nb for p in grids])
-    sample = sorted({int(np.argmax(sizes)), int(np.argmin(sizes)), 17, 41})
+    return sorted({int(np.argmax(sizes)), int(np.argmin(sizes)), 17, 41})
+
+
+@pytest.fixture(scope="module")
+def oracle_steps(grids):
+    out = {}
+    for g in _sample(grids):
+        p = grids[g]
+        out[g] = O.run(p, p.U0, 1, cfl=p.cfl)
+    return out
+
+
+@pytest.mark.parametrize("form", [(0, 1, 0), (0, 4, 0), (1, 4, 0), "autotuned"])
+@pytest.mark.parametrize("prec,tol", [(1, 1e-5), (0, 1e-12)])
+def test_full_batched_workload_sampled_against_the_oracle(grids, oracle_steps, prec, tol, form):
+    from paper_2501_06717_gb300 import bats as B
+    from paper_2501_06717_gb300 import autotune
+    assert sum(p.nb for p in grids) == 60194
+    sample = _sample(grids)
     with B.Solver(grids, precision=prec) as s:
+        if form == "autotuned":
+            # the autotuner advances the state while it times the candidates;
+            # tune, then start again from the initial state (set_states also
+            # resets the elapsed times) in its pick
+            cands = autotune.DEFAULT_CANDIDATES if prec == 1 else [(0, 1, 0), (0, 4, 0)]
+            best, _ = autotune.autotune(s, 0.8, steps=1, candidates=cands)
+            print("autotuner pick", best)
+            s.set_launch(best[0], best[1], best[2], 1)
+        else:
+            s.set_launch(form[0], form[1], form[2], 1)
         s.set_states()
-        s.set_launch(0, 1, 0, 1)
         s.step(1, 0.8)
         got = {g: (s.get_state(g), s.time(g)) for g in sample}
     for g in sample:
         p = grids[g]
-        Uo, dto, to = O.run(p, p.U0, 1, cfl=p.cfl)
+        Uo, dto, to = oracle_steps[g]
         err = _scaled(got[g][0], Uo)
         print("grid", g, "blocks", p.nb, "scaled error per variable", err)
         assert err.max() <= tol, (g, err)
