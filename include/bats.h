@@ -313,8 +313,13 @@ int bats_mlp_train_step(bats_mlp_t* m, const float* X, const float* T, int64_t n
  * maps (sum over levels 0..max of the number of block positions,
  * root[0]*root[1]*root[2]*8^level) at most BATS_NOALLOC_MAX_MAP_ENTRIES;
  * larger grids are rejected with BATS_ERR_INVALID_ARG and a message.  FP64
- * form only (phys->precision must be BATS_FP64, learned 0); the launch fields
- * of phys are ignored.
+ * form only (phys->precision must be BATS_FP64, learned 0).  The refluxing
+ * and local-time-step options need buffers this entry point does not keep:
+ * phys->reflux or phys->local_dt set is rejected with BATS_ERR_INVALID_ARG
+ * (never silently ignored).  All three schemes (midpoint, SSP-RK2 and the
+ * one-stage BATS_RK_EULER) and all limiters are supported.  The launch
+ * fields of phys (persistent, blocks_per_cta, ctas_per_sm, use_graph) are
+ * ignored: one CTA per block, eager launches.
  *
  * Arguments: grid, phys as for bats_create (one grid); U the state, host or
  * device, n = 8 * 512 * n_leaves doubles in the layout above, read and then
@@ -326,7 +331,8 @@ int bats_mlp_train_step(bats_mlp_t* m, const float* X, const float* T, int64_t n
  *
  * The first call on a device (per process) looks up the device address of
  * the array and sets the stage kernel's shared-memory limit; make that first
- * call before any CUDA stream capture.  All calls share the one array, which
+ * call before any CUDA stream capture.  If that set-up fails, the call
+ * returns BATS_ERR_CUDA and the next call tries the set-up again.  All calls share the one array, which
  * keeps the previous call's contents (each call rewrites what it reads first
  * and clears its counters), so calls whose GPU work overlaps -- from two
  * threads, or on two streams without ordering -- race and corrupt each

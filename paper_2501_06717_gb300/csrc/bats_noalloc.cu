@@ -33,6 +33,7 @@ cudaError_t launch_cfl(bool mixed, const double* U, const float* Wt, const GridD
                        const PhysDev& ph, int b0, int nb, unsigned long long* smax, cudaStream_t st);
 cudaError_t launch_dt(int ngrids, int mode, double cfl, double fixed_dt, double* dt, double* t,
                       unsigned long long* smax, unsigned long long* smax_next, cudaStream_t st);
+cudaError_t read_index_flag(int32_t* out);
 }  // namespace batsk
 
 using namespace batsk;
@@ -52,30 +53,35 @@ constexpr size_t kOffBlocks = align256(kOffU1 + kStateBytes);
 constexpr size_t kOffGrid = align256(kOffBlocks + sizeof(BlockDev) * kMaxBlocks);
 constexpr size_t kOffMap = align256(kOffGrid + sizeof(GridDev));
 constexpr size_t kOffWords = align256(kOffMap + sizeof(int32_t) * kMaxMap);
-// words: dt, t (double), smax, smax_next (u64), err[2] (int32)
-constexpr size_t kScratchBytes = align256(kOffWords + 4 * sizeof(double) + 2 * sizeof(int32_t));
+// words: dt, t (double), smax, smax_next (u64), err[3] (int32: error bits,
+// first bad block, learned-fallback count -- the stage kernel's error block)
+constexpr size_t kScratchBytes = align256(kOffWords + 4 * sizeof(double) + 3 * sizeof(int32_t));
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 unsigned char* g_scratch_dev[kMaxDevices] = {};
-std::once_flag g_setup_once[kMaxDevices];
-cudaError_t g_setup_err[kMaxDevices] = {};
+std::mutex g_setup_mutex;
 
 // Once per device, with that device current: the device address of the
 // scratch array (in host code its name is only a host-side stand-in) and the
-// stage kernel's shared-memory attribute.
+// stage kernel's shared-memory attribute.  The address is kept only when the
+// set-up succeeded; a failed set-up (for example one attempted during a
+// stream capture) is tried again by the next call.
 cudaError_t setup_device(int dev) {
-  std::call_once(g_setup_once[dev], [dev]() {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e == cudaSuccess) {
-      int occ[2];
-      e = stage_setup(occ);
-    }
-    if (e == cudaSuccess) g_scratch_dev[dev] = static_cast<unsigned char*>(p);
-    g_setup_err[dev] = e;
-  });
-  return g_setup_err[dev];
+  std::lock_guard<std::mutex> lock(g_setup_mutex);
+  if (g_scratch_dev[dev]) return cudaSuccess;
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e == cudaSuccess) {
+    int occ[2];
+    e = stage_setup(occ);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // do not leave the failure pending for unrelated code
+    return e;
+  }
+  g_scratch_dev[dev] = static_cast<unsigned char*>(p);
+  return cudaSuccess;
 }
 
 int report(char* err, size_t len, int code, const char* msg) {
@@ -271,9 +277,16 @@ extern "C" int bats_step_noalloc(const bats_grid_desc* grid, const bats_physics*
   if (!(phys->gamma > 1.0)) return report(err, err_len, BATS_ERR_INVALID_ARG, "gamma must exceed 1");
   if (phys->precision != BATS_FP64 || phys->learned)
     return report(err, err_len, BATS_ERR_INVALID_ARG, "bats_step_noalloc runs the FP64 form only");
-  if (phys->limiter < 0 || phys->limiter > 1 || phys->rk < 0 || phys->rk > 1 || phys->b0 < 0 || phys->b0 > 3 ||
+  if (phys->limiter < 0 || phys->limiter > 2 || phys->rk < 0 || phys->rk > 2 || phys->b0 < 0 || phys->b0 > 3 ||
       phys->flux < BATS_FLUX_RUSANOV || phys->flux > BATS_FLUX_HLL)
     return report(err, err_len, BATS_ERR_INVALID_ARG, "bad physics enumeration");
+  // options that change the physics and need buffers this entry point does
+  // not keep (the flux register, the per-cell time steps): refused, never
+  // silently dropped
+  if (phys->reflux)
+    return report(err, err_len, BATS_ERR_INVALID_ARG, "bats_step_noalloc does not support reflux (use bats_step)");
+  if (phys->local_dt)
+    return report(err, err_len, BATS_ERR_INVALID_ARG, "bats_step_noalloc does not support local_dt (use bats_step)");
   if (grid->n_leaves > kMaxBlocks)
     return report(err, err_len, BATS_ERR_INVALID_ARG,
                   "grid has more blocks than bats_step_noalloc supports (BATS_NOALLOC_MAX_BLOCKS)");
@@ -284,6 +297,8 @@ extern "C" int bats_step_noalloc(const bats_grid_desc* grid, const bats_physics*
   int rc = build_tables(*grid, T, err, err_len);
   if (rc) return rc;
 
+  // an error left pending by unrelated code is not this call's failure
+  cudaGetLastError();
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return report(err, err_len, BATS_ERR_CUDA, cudaGetErrorString(e));
@@ -300,7 +315,7 @@ extern "C" int bats_step_noalloc(const bats_grid_desc* grid, const bats_physics*
   double* tw = dtw + 1;
   unsigned long long* smax = reinterpret_cast<unsigned long long*>(dtw + 2);
   unsigned long long* smax_next = smax + 1;
-  int32_t* errw = reinterpret_cast<int32_t*>(smax + 2);
+  int32_t* errw = reinterpret_cast<int32_t*>(smax + 2);  // [3]
 
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   PhysDev ph{};
@@ -335,7 +350,7 @@ extern "C" int bats_step_noalloc(const bats_grid_desc* grid, const bats_physics*
   NA_CK(cudaMemcpyAsync(blocks, T.blocks, sizeof(BlockDev) * nb, cudaMemcpyHostToDevice, st));
   NA_CK(cudaMemcpyAsync(levmap, T.map, sizeof(int32_t) * map_entries, cudaMemcpyHostToDevice, st));
   NA_CK(cudaMemsetAsync(dtw, 0, 4 * sizeof(double), st));
-  int32_t init[2] = {0, INT_MAX};
+  int32_t init[3] = {0, INT_MAX, 0};
   NA_CK(cudaMemcpyAsync(errw, init, sizeof(init), cudaMemcpyHostToDevice, st));
   NA_CK(launch_init_grid_states(G, 1, ph.inv_gm1, ph.gm1, st));
   // caller state -> block-major copy (host states are staged through U1)
@@ -346,6 +361,7 @@ extern "C" int bats_step_noalloc(const bats_grid_desc* grid, const bats_physics*
   NA_CK(launch_cfl(false, Ui, nullptr, G, blocks, ph, 0, nb, smax, st));
 
   const bool ssp = ph.rk == BATS_RK_SSP2;
+  const bool euler = ph.rk == BATS_RK_EULER;
   StageArgs a{};
   a.grids = G;
   a.blocks = blocks;
@@ -358,8 +374,26 @@ extern "C" int bats_step_noalloc(const bats_grid_desc* grid, const bats_physics*
   a.ph = ph;
   a.write_u_all = 1;
   const double c = cfl > 0.0 ? cfl : -1.0;
+  // the one-stage scheme cannot update in place (other blocks read this
+  // block's cells as ghosts): it alternates between Ui and U1
+  double* Ucur = Ui;
+  double* Uoth = U1;
   for (int s = 0; s < steps; s++) {
     NA_CK(launch_dt(1, 0, c, dt, dtw, tw, smax, smax_next, st));
+    if (euler) {
+      a.Uin = Ucur;
+      a.Ubase = Ucur;
+      a.Uout = Uoth;
+      a.kind = 0;
+      a.last = 1;
+      a.beta = 1.0;
+      NA_CK(launch_stage_kernel(false, nb, st, a));
+      NA_CK(launch_dt(1, 1, c, dt, dtw, tw, smax, smax_next, st));
+      double* tmp = Ucur;
+      Ucur = Uoth;
+      Uoth = tmp;
+      continue;
+    }
     a.Uin = Ui;
     a.Ubase = Ui;
     a.Uout = U1;
@@ -376,16 +410,22 @@ extern "C" int bats_step_noalloc(const bats_grid_desc* grid, const bats_physics*
     NA_CK(launch_stage_kernel(false, nb, st, a));
     NA_CK(launch_dt(1, 1, c, dt, dtw, tw, smax, smax_next, st));
   }
+  if (Ucur != Ui) NA_CK(cudaMemcpyAsync(Ui, Ucur, bytes, cudaMemcpyDeviceToDevice, st));
   // block-major -> caller layout (host destinations staged through U1)
   NA_CK(launch_to_external(Ui, dev_ptr ? U : U1, 0, nb, st));
   if (!dev_ptr) NA_CK(cudaMemcpyAsync(U, U1, bytes, cudaMemcpyDeviceToHost, st));
-  int32_t ew[2];
+  int32_t ew[3];
   double tt = 0.0;
   NA_CK(cudaMemcpyAsync(ew, errw, sizeof(ew), cudaMemcpyDeviceToHost, st));
   NA_CK(cudaMemcpyAsync(&tt, tw, sizeof(double), cudaMemcpyDeviceToHost, st));
   NA_CK(cudaStreamSynchronize(st));
+  // checked build: an index that left its range in these launches (always
+  // clear in the normal build)
+  int32_t bad_index = 0;
+  NA_CK(read_index_flag(&bad_index));
 #undef NA_CK
   if (t_out) *t_out = tt;
+  if (bad_index) return report(err, err_len, BATS_ERR_CUDA, "index check failed (checked build): an index left its range");
   if (ew[0] & ERR_TIMEOUT) return report(err, err_len, BATS_ERR_TIMEOUT, "a bounded device wait ran out");
   if (ew[0] & ERR_BOUNDS) return report(err, err_len, BATS_ERR_CUDA, "ghost fill met a source two levels away");
   if (ew[0] & ERR_NONPHYSICAL) return report(err, err_len, BATS_ERR_NONPHYSICAL, "non-physical state after an update");

@@ -77,3 +77,53 @@ def test_noalloc_rejects_grids_beyond_its_limit(B):
     with pytest.raises(B.BatsError) as e:
         B.bats_step_noalloc(q, B.physics_from(q), q.U0.copy(), 1, cfl=0.8)
     assert e.value.code == B.BATS_ERR_INVALID_ARG and "BATS_NOALLOC_MAX_BLOCKS" in str(e.value)
+
+
+@pytest.mark.parametrize("option", ["reflux", "local_dt"])
+def test_noalloc_refuses_options_it_cannot_honour(B, option):
+    """Refluxing and local time steps change the physics and need buffers the
+    entry point does not keep: they are refused with a message, not ignored."""
+    q = _problem()
+    setattr(q, option, 1)
+    U = q.U0.copy()
+    with pytest.raises(B.BatsError) as e:
+        B.bats_step_noalloc(q, B.physics_from(q), U, 1, cfl=0.8)
+    assert e.value.code == B.BATS_ERR_INVALID_ARG and option in str(e.value)
+    assert np.array_equal(U, q.U0)  # the caller's state is untouched
+
+
+@pytest.mark.parametrize("nsteps", [3, 4])
+def test_noalloc_one_stage_scheme_matches_allocating_path(B, nsteps):
+    """The one-stage first-order scheme (alternating buffers; an odd step
+    count ends in the other buffer) gives the allocating path's result."""
+    q = _problem()
+    q.rk = W.RK_EULER
+    q.limiter = W.LIM_NONE
+    ph = B.physics_from(q)
+    with B.Solver(q) as s:
+        s.set_state(0, q.U0)
+        s.step(nsteps, 0.8)
+        ref = s.get_state(0)
+    U = q.U0.copy()
+    B.bats_step_noalloc(q, ph, U, nsteps, cfl=0.8)
+    assert _scaled(U, ref) <= 1e-12
+
+
+def test_noalloc_allocates_no_device_memory(B):
+    """After a first call (which loads the kernels), further calls on host and
+    device buffers leave the device's free memory unchanged."""
+    torch = pytest.importorskip("torch")
+    q = _problem()
+    ph = B.physics_from(q)
+    Uh = q.U0.copy()
+    Ud = torch.from_numpy(q.U0.copy()).cuda()
+    B.bats_step_noalloc(q, ph, Uh, 1, cfl=0.8)
+    B.bats_step_noalloc(q, ph, Ud, 1, cfl=0.8)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        B.bats_step_noalloc(q, ph, Uh, 2, cfl=0.8)
+        B.bats_step_noalloc(q, ph, Ud, 2, dt=1e-3)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
