@@ -1014,6 +1014,216 @@ __device__ __forceinline__ void b0_face(const PhysDev& ph, int d, int i, int j, 
   b0_at<R>(ph, x, B0);
 }
 
+// ---------------------------------------------------------------------------
+// Mixed form, plain faces (no learned correction): packed FP32.  GB300 issues
+// FADD2 / FMUL2 / FFMA2 on float2 pairs (two FP32 lanes per instruction);
+// every quantity of a face's two sides -- its left and right reconstructed
+// states -- is such a pair, so the physical fluxes, the fast speeds and the
+// flux combination of both sides take one instruction each.  One direction D
+// per thread group, fixed at compile time, so every shared-memory offset of
+// the rotated variables and of the face stores is an immediate.  The face
+// values are stored doubled (2 F, and the sum of the two sides' normal B1);
+// the cell phase scales its flux differences by 1/2.
+
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 p_bc(float s) { return make_float2(s, s); }
+__device__ __forceinline__ float p_sum(float2 a) { return a.x + a.y; }
+
+// minmod as the median of (0, a, b): the smaller magnitude when a and b share
+// a sign, else 0 (four min/max operations)
+__device__ __forceinline__ float minmod_med(float a, float b) {
+  return fminf(fmaxf(a, b), fmaxf(fminf(a, b), 0.f));
+}
+template <int LIM>
+__device__ __forceinline__ float limit_f(float a, float b) {
+  if constexpr (LIM == 2) return 0.f;
+  else if constexpr (LIM == 1) return mc_<float>(a, b);
+  else return minmod_med(a, b);
+}
+
+// Twice the numerical flux (Rusanov or HLL) of one face in the face frame from
+// the pairs W2[v] = (left, right) of reconstructed primitives and the face's
+// B0 (components in the frame).  The same physics as phys_flux + the flux
+// combination of the generic path: split-field flux, fast speed with the
+// total field, F = (F_L + F_R)/2 - cmax (U_R - U_L)/2 with cmax the larger
+// |u_n| + c_f (Rusanov), or the two-state HLL flux.
+template <bool HAS_B0, int FLX>
+__device__ __forceinline__ void face_flux2(const float2 W2[8], const float B0r[3], float gamma, float inv_gm1,
+                                           float Fr2[8]) {
+  const float2 rho = W2[0], u0 = W2[1], u1 = W2[2], u2 = W2[3];
+  const float2 b0 = W2[4], b1 = W2[5], b2 = W2[6], p = W2[7];
+  float2 Bt0 = b0, Bt1 = b1, Bt2 = b2;
+  if constexpr (HAS_B0) {
+    Bt0 = p_add(b0, p_bc(B0r[0]));
+    Bt1 = p_add(b1, p_bc(B0r[1]));
+    Bt2 = p_add(b2, p_bc(B0r[2]));
+  }
+  // fast speeds of both sides (total field, along the normal)
+  const float2 rinv = make_float2(rcp_approx(rho.x), rcp_approx(rho.y));
+  const float2 b1sq = p_fma(b2, b2, p_fma(b1, b1, p_mul(b0, b0)));
+  const float2 bsq = HAS_B0 ? p_fma(Bt2, Bt2, p_fma(Bt1, Bt1, p_mul(Bt0, Bt0))) : b1sq;
+  const float2 a2 = p_mul(p_mul(p_bc(gamma), p), rinv);
+  const float2 bb = p_mul(bsq, rinv);
+  const float2 bn2 = p_mul(p_mul(Bt0, Bt0), rinv);
+  const float2 s = p_add(a2, bb);
+  const float2 disc = p_fma(p_mul(a2, bn2), p_bc(-4.f), p_mul(s, s));
+  const float2 sq = make_float2(sqrt_approx(fmaxf(disc.x, 0.f)), sqrt_approx(fmaxf(disc.y, 0.f)));
+  const float2 t = p_mul(p_add(s, sq), p_bc(0.5f));
+  const float2 cf = make_float2(sqrt_approx(t.x), sqrt_approx(t.y));
+  // coefficients of the combination 2F = sum over the two sides of (cF F + cU U)
+  float2 cF = p_bc(1.f), cU;
+  if constexpr (FLX == FLUX_HLL) {
+    // S_L = min(unL - cfL, unR - cfR, 0), S_R = max(unL + cfL, unR + cfR, 0),
+    // F = F_L - k ((F_R - F_L) - S_R (U_R - U_L)), k = S_L / (S_R - S_L)
+    const float2 lo = p_fma(cf, p_bc(-1.f), u0), hi = p_add(u0, cf);
+    const float sl = fminf(fminf(lo.x, lo.y), 0.f), sr = fmaxf(fmaxf(hi.x, hi.y), 0.f);
+    const float den = sr - sl;
+    const float k2 = den > 0.f ? 2.f * (sl * rcp_approx(den)) : 0.f;
+    cF = make_float2(2.f + k2, -k2);
+    cU = make_float2(-k2 * sr, k2 * sr);
+  } else {
+    const float cmax = fmaxf(fabsf(u0.x) + cf.x, fabsf(u0.y) + cf.y);
+    cU = make_float2(cmax, -cmax);
+  }
+  auto comb = [&](float2 F, float2 U) -> float {
+    if constexpr (FLX == FLUX_HLL) return p_sum(p_fma(F, cF, p_mul(U, cU)));
+    else return p_sum(p_fma(U, cU, F));
+  };
+  // split-field physical fluxes of both sides
+  const float2 usq = p_fma(u2, u2, p_fma(u1, u1, p_mul(u0, u0)));
+  float2 pt = p_fma(b1sq, p_bc(0.5f), p);
+  if constexpr (HAS_B0)
+    pt = p_add(pt, p_fma(p_bc(B0r[2]), b2, p_fma(p_bc(B0r[1]), b1, p_mul(p_bc(B0r[0]), b0))));
+  const float2 e1 = p_fma(p, p_bc(inv_gm1), p_mul(p_bc(0.5f), p_fma(rho, usq, b1sq)));
+  const float2 ub1 = p_fma(u2, b2, p_fma(u1, b1, p_mul(u0, b0)));
+  const float2 m0 = p_mul(rho, u0), m1 = p_mul(rho, u1), m2 = p_mul(rho, u2);
+  const float2 nB0 = p_mul(Bt0, p_bc(-1.f));
+  float2 F1 = p_fma(b0, nB0, p_fma(m0, u0, pt));
+  float2 F2 = p_fma(b1, nB0, p_mul(m1, u0));
+  float2 F3 = p_fma(b2, nB0, p_mul(m2, u0));
+  if constexpr (HAS_B0) {
+    F1 = p_fma(b0, p_bc(-B0r[0]), F1);
+    F2 = p_fma(b0, p_bc(-B0r[1]), F2);
+    F3 = p_fma(b0, p_bc(-B0r[2]), F3);
+  }
+  const float2 F5 = p_fma(nB0, u1, p_mul(u0, Bt1));
+  const float2 F6 = p_fma(nB0, u2, p_mul(u0, Bt2));
+  const float2 F7 = p_fma(nB0, ub1, p_mul(u0, p_add(e1, pt)));
+  Fr2[0] = comb(m0, rho);
+  Fr2[1] = comb(F1, m0);
+  Fr2[2] = comb(F2, m1);
+  Fr2[3] = comb(F3, m2);
+  if constexpr (FLX == FLUX_HLL) Fr2[4] = p_sum(p_mul(b0, cU));
+  else Fr2[4] = p_sum(p_mul(b0, cU));
+  Fr2[5] = comb(F5, b1);
+  Fr2[6] = comb(F6, b2);
+  Fr2[7] = comb(F7, e1);
+}
+
+// The faces of one direction D on this thread's grid line: lane half 0 takes
+// faces 0-4, half 1 faces 5-8 (its fifth step is computed and not stored),
+// sliding a window along the line so that every cell is loaded and every
+// limited slope formed once.  Writes twice the fluxes (un-rotated components)
+// and the sum of the two sides' normal B1 into sF[D][9][576].
+template <int D, int LIM, bool HAS_B0, int FLX>
+__device__ __forceinline__ void faces_mixed(const StageArgs& a, const BlockDev& B, const float* sT, float* sF,
+                                            int fline, int fhalf, float gamma, float inv_gm1, int gb0, int gb1,
+                                            int gb2, float lor0, float lor1, float lor2, float dxr0, float dxr1,
+                                            float dxr2) {
+  constexpr int D1 = D == 2 ? 0 : D + 1, D2 = D == 0 ? 2 : D - 1;
+  constexpr int S = D == 0 ? 1 : (D == 1 ? NC : NC * NC);
+  constexpr int R1 = (1 + D) * NTILE, R2 = (1 + D1) * NTILE, R3 = (1 + D2) * NTILE;
+  constexpr int R4 = (4 + D) * NTILE, R5 = (4 + D1) * NTILE, R6 = (4 + D2) * NTILE, R7 = 7 * NTILE;
+  const int fta = fline & 7, ftb = fline >> 3;
+  const int ibase = D == 0 ? (ftb * NC + fta) * NC : (D == 1 ? ftb * NC * NC + fta : ftb * NC + fta);
+  const int glo = NCELL + 2 * D * 128 + 2 * (fta + NC * ftb), ghi = glo + 128;
+  const bool h1 = fhalf != 0;
+  // tile index of window cell j (after unrolling, j is a constant): half 0
+  // reads cells -2..5, half 1 cells 3..9 (j = 7 repeats cell 9)
+  auto cell = [&](int j) -> int {
+    const int c0 = j - 2, c1 = j + 3;
+    const int i0 = c0 < 0 ? glo + (c0 + 2) : ibase + c0 * S;
+    const int i1 = c1 < NC ? ibase + c1 * S : ghi + (c1 - NC > 1 ? 1 : c1 - NC);
+    return chki(h1 ? i1 : i0, 0, NTILE);
+  };
+  auto load = [&](int idx, float w[8]) {
+    const float* q = sT + idx;
+    w[0] = q[0]; w[1] = q[R1]; w[2] = q[R2]; w[3] = q[R3];
+    w[4] = q[R4]; w[5] = q[R5]; w[6] = q[R6]; w[7] = q[R7];
+  };
+  float W0[8], d[8], WL[8];
+  {
+    float Wm2[8], Wm1[8];
+    load(cell(0), Wm2);
+    load(cell(1), Wm1);
+    load(cell(2), W0);
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      d[v] = W0[v] - Wm1[v];
+      WL[v] = fmaf(0.5f, limit_f<LIM>(Wm1[v] - Wm2[v], d[v]), Wm1[v]);
+    }
+  }
+  const int f0 = h1 ? 5 : 0;
+  float* const fo = sF + D * (9 * NFACE) + chki(fline * 9 + f0, 0, NFACE - 3);  // + k, k <= 4 - f0 / 5
+#pragma unroll
+  for (int k = 0; k < 5; k++) {
+    float Wp[8];
+    load(cell(k + 3), Wp);
+    // the face's two sides, then the window moves on (the next face's left
+    // state, cell and difference), so that only the pairs stay live
+    float2 W2[8];
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      const float dn = Wp[v] - W0[v];
+      const float s0 = limit_f<LIM>(d[v], dn);
+      W2[v] = make_float2(WL[v], fmaf(-0.5f, s0, W0[v]));
+      WL[v] = fmaf(0.5f, s0, W0[v]);
+      W0[v] = Wp[v];
+      d[v] = dn;
+    }
+    float B0r[3] = {0.f, 0.f, 0.f};
+    if constexpr (HAS_B0) {
+      const int f = f0 + k;
+      const int ci_ = D == 0 ? f : fta, cj_ = D == 1 ? f : (D == 0 ? fta : ftb), ck_ = D == 2 ? f : ftb;
+      float B0f[3];
+      b0_face<float>(a.ph, D, ci_, cj_, ck_, gb0, gb1, gb2, lor0, lor1, lor2, dxr0, dxr1, dxr2, B0f);
+      B0r[0] = B0f[D];
+      B0r[1] = B0f[D1];
+      B0r[2] = B0f[D2];
+    }
+    float Fr2[8];
+    face_flux2<HAS_B0, FLX>(W2, B0r, gamma, inv_gm1, Fr2);
+    const float bn2 = W2[4].x + W2[4].y;
+    if (k == 4 && h1) continue;  // half 1 has four faces
+    fo[k] = Fr2[0];
+    fo[(1 + D) * NFACE + k] = Fr2[1];
+    fo[(1 + D1) * NFACE + k] = Fr2[2];
+    fo[(1 + D2) * NFACE + k] = Fr2[3];
+    fo[(4 + D) * NFACE + k] = Fr2[4];
+    fo[(4 + D1) * NFACE + k] = Fr2[5];
+    fo[(4 + D2) * NFACE + k] = Fr2[6];
+    fo[7 * NFACE + k] = Fr2[7];
+    fo[8 * NFACE + k] = bn2;
+    // refluxing: the block-face fluxes (face 0 of half 0, face 8 of half 1)
+    if ((k == 0 || k == 3) && a.freg && (k == 0) == !h1) {
+      const int sl = chki(B.rslot[2 * D + (k == 3 ? 1 : 0)], -1, a.nslots);
+      if (sl >= 0) {
+        double* o = a.freg + (static_cast<int64_t>(sl) * 64 + fta * NC + ftb) * NV;
+        o[0] = f2d_int(0.5f * Fr2[0]);
+        o[1 + D] = f2d_int(0.5f * Fr2[1]);
+        o[1 + D1] = f2d_int(0.5f * Fr2[2]);
+        o[1 + D2] = f2d_int(0.5f * Fr2[3]);
+        o[4 + D] = f2d_int(0.5f * Fr2[4]);
+        o[4 + D1] = f2d_int(0.5f * Fr2[5]);
+        o[4 + D2] = f2d_int(0.5f * Fr2[6]);
+        o[7] = f2d_int(0.5f * Fr2[7]);
+      }
+    }
+  }
+}
+
 // The fused stage (StageCfg::THREADS threads).  Per block: (1) interior by TMA, face-slab
 // ghosts by threads; (2) FP64 form: primitives in place; (3) faces of all
 // three directions at once on the first FACE_THREADS threads, two per grid
@@ -1335,6 +1545,9 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1) k_sta
         const int kind = FAST ? 0 : a.kind;
         double* const dtc = FAST ? nullptr : a.dtc;
         const bool blk_body = FAST ? false : B.body != 0;
+        // the packed mixed face phase stores doubled face values
+        constexpr R FS = (MIXED && !LRN) ? R(0.5) : R(1);
+        const R fidx0 = FS * idx0, fidx1 = FS * idx1, fidx2 = FS * idx2;
         bool any_bad = false;
         R smax_loc = R(0);
         const double cdt_blk = a.beta * a.dt[B.grid];
@@ -1358,14 +1571,14 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1) k_sta
           R res[8];
 #pragma unroll
           for (int v = 0; v < NV; v++) {
-            R r = -((Fx[v * NFACE + tx + 1] - Fx[v * NFACE + tx]) * idx0);
-            r = r - (Fy[v * NFACE + ty + 1] - Fy[v * NFACE + ty]) * idx1;
-            r = r - (Fz[v * NFACE + tz + 1] - Fz[v * NFACE + tz]) * idx2;
+            R r = -((Fx[v * NFACE + tx + 1] - Fx[v * NFACE + tx]) * fidx0);
+            r = r - (Fy[v * NFACE + ty + 1] - Fy[v * NFACE + ty]) * fidx1;
+            r = r - (Fz[v * NFACE + tz + 1] - Fz[v * NFACE + tz]) * fidx2;
             res[v] = r;
           }
-          const R divb = ((Fx[8 * NFACE + tx + 1] - Fx[8 * NFACE + tx]) * idx0 +
-                          (Fy[8 * NFACE + ty + 1] - Fy[8 * NFACE + ty]) * idx1) +
-                         (Fz[8 * NFACE + tz + 1] - Fz[8 * NFACE + tz]) * idx2;
+          const R divb = ((Fx[8 * NFACE + tx + 1] - Fx[8 * NFACE + tx]) * fidx0 +
+                          (Fy[8 * NFACE + ty + 1] - Fy[8 * NFACE + ty]) * fidx1) +
+                         (Fz[8 * NFACE + tz + 1] - Fz[8 * NFACE + tz]) * fidx2;
           bool in_body = false;
           if (blk_body) {  // FP64, the same centre formula as the host and the oracle
             double x = G.lo[0] + ((static_cast<double>(gb0) + ci) + 0.5) * G.dx[lev][0];
@@ -1536,7 +1749,22 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1) k_sta
         return any_bad;
       };
 
-      if (tid < FACE_THREADS) faces(true);
+      if constexpr (MIXED && !LRN) {
+        // direction fixed at compile time per warp group (fd is warp-uniform)
+        if (tid < FACE_THREADS) {
+          if (fd == 0)
+            faces_mixed<0, LIM, HAS_B0, FLX>(a, B, sT, sF, fline, fhalf, gamma, inv_gm1, gb0, gb1, gb2, lor0, lor1,
+                                             lor2, dxr0, dxr1, dxr2);
+          else if (fd == 1)
+            faces_mixed<1, LIM, HAS_B0, FLX>(a, B, sT, sF, fline, fhalf, gamma, inv_gm1, gb0, gb1, gb2, lor0, lor1,
+                                             lor2, dxr0, dxr1, dxr2);
+          else
+            faces_mixed<2, LIM, HAS_B0, FLX>(a, B, sT, sF, fline, fhalf, gamma, inv_gm1, gb0, gb1, gb2, lor0, lor1,
+                                             lor2, dxr0, dxr1, dxr2);
+        }
+      } else {
+        if (tid < FACE_THREADS) faces(true);
+      }
       __syncthreads();
       if (a.kind >= 3) continue;  // features / dumps only
       const bool fast = a.kind == 0 && !a.dtc && !B.body;

@@ -54,9 +54,10 @@ def test_full_batched_workload_sampled_against_the_oracle(grids, oracle_steps, p
     sample = _sample(grids)
     with B.Solver(grids, precision=prec) as s:
         if form == "autotuned":
-            # the autotuner advances the state while it times the candidates;
-            # tune, then start again from the initial state (set_states also
-            # resets the elapsed times) in its pick
+            # the autotuner advances the state while it times the candidates:
+            # tune from the initial state, then start again from it (set_states
+            # also resets the elapsed times) in the autotuner's pick
+            s.set_states()
             cands = autotune.DEFAULT_CANDIDATES if prec == 1 else [(0, 1, 0), (0, 4, 0)]
             best, _ = autotune.autotune(s, 0.8, steps=1, candidates=cands)
             print("autotuner pick", best)
