@@ -389,7 +389,7 @@ def main():
     # mean stage-kernel launch duration: the same K steps launched eagerly, with
     # CUDA events around each step's two stage launches (graph replay carries
     # no per-kernel events)
-    solver.set_launch(*(tune[0] if tune else (1, 1, 0)), 0)
+    solver.set_launch(*(tune[0][:3] if tune else (1, 1, 0)), 0)
     solver.step(args.steps, cfl)
     stage_ms = solver.timings()[bats.BATS_PHASE_STAGE]
     stage_total_ms = solver.timings()[bats.BATS_PHASE_TOTAL]
@@ -459,7 +459,9 @@ def main():
             "dtype": "f32+f64" if prec == bats.BATS_MIXED else "f64", "data": "synthetic",
             "config": {"workload": desc, "blocks": sum(p.nb for p in problems), "cells_per_gpu": cells,
                        "precision": args.precision,
-                       "launch": {"persistent_blocks_per_cta_ctas_per_sm": list(tune[0]) if tune else [1, 1, 0],
+                       "launch": {"persistent_blocks_per_cta_ctas_per_sm": list(tune[0][:3]) if tune else [1, 1, 0],
+                                  "staging": (None if not tune or tune[0][3] is None
+                                              else ("tma" if tune[0][3] else "gather")),
                                   "cuda_graph": True},
                        "l2": "inputs larger than L2 (state %.2f GB per GPU, L2 129 MB); no flush" %
                              (2 * state_bytes / 1e9),
@@ -480,7 +482,9 @@ def main():
             "stage_share": stage_ms / stage_total_ms if stage_total_ms > 0 else None,
         }
         if tune:
-            line["autotune_ms_per_stage"] = {"%d/%d/%d" % c: m for c, m in tune[1]}
+            line["autotune_ms_per_stage"] = {
+                "%d/%d/%d%s" % (c[:3] + ("" if c[3] is None else "/" + ("tma" if c[3] else "gather"),)): m
+                for c, m in tune[1]}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -218,6 +218,18 @@ int bats_debug_wait_timeout(bats_t* h);
  * blocks per work item, CTAs per SM, CUDA-graph replay of whole steps. */
 int bats_set_launch(bats_t* h, int persistent, int blocks_per_cta, int ctas_per_sm, int use_graph);
 
+/* Staging layout of the mixed form's plain stage kernel (an autotuner knob;
+ * the result is the same either way, bit for bit).  The kernel stages each
+ * block's padded stencil (Section 4.1's ghost cells around the block's own
+ * cells) in shared memory: the block's 512 cells by one tensor copy (TMA),
+ * the face slabs at resolution changes from their precomputed buffer by bulk
+ * copies, and the same-level face slabs, with tma = 1 (the default), by one
+ * tensor copy each of the neighbour's cells nearest the face, or with
+ * tma = 0 gathered by the kernel's threads.  BATS_ERR_INVALID_ARG for other
+ * values.  bats_get_staging returns the current value (-1 for NULL). */
+int bats_set_staging(bats_t* h, int tma);
+int bats_get_staging(const bats_t* h);
+
 /* Number of kernels launched by the last bats_step call. */
 int bats_get_launch_count(bats_t* h, long long* n);
 

@@ -106,6 +106,9 @@ def lib():
     L.bats_debug_residual.argtypes = [vp, ctypes.c_int, dp, ctypes.c_size_t]
     L.bats_debug_wait_timeout.argtypes = [vp]
     L.bats_set_launch.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.bats_set_staging.argtypes = [vp, ctypes.c_int]
+    L.bats_get_staging.argtypes = [vp]
+    L.bats_get_staging.restype = ctypes.c_int
     L.bats_get_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     L.bats_get_fallbacks.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     L.bats_debug_check_conversions.argtypes = [vp, vp, ctypes.c_int, vp, vp]
@@ -293,6 +296,14 @@ def bats_set_launch(h, persistent, blocks_per_cta, ctas_per_sm, use_graph):
     _check(h, lib().bats_set_launch(h, int(persistent), int(blocks_per_cta), int(ctas_per_sm), int(use_graph)))
 
 
+def bats_set_staging(h, tma):
+    _check(h, lib().bats_set_staging(h, int(tma)))
+
+
+def bats_get_staging(h):
+    return lib().bats_get_staging(h)
+
+
 def bats_get_launch_count(h):
     n = ctypes.c_longlong(0)
     _check(h, lib().bats_get_launch_count(h, ctypes.byref(n)))
@@ -449,6 +460,7 @@ class Solver:
         if not isinstance(problems, (list, tuple)):
             problems = [problems]
         self.problems = list(problems)
+        self.precision = int(precision)
         self.phys = physics_from(self.problems[0], precision, persistent, blocks_per_cta, ctas_per_sm, use_graph)
         self.h = bats_create(self.problems, self.phys, stream)
 
@@ -515,6 +527,12 @@ class Solver:
 
     def face_data(self, grid=0, stage_input=0, dt=0.0, with_inputs=True):
         return bats_debug_face_data(self.h, grid, self.problems[grid].nb, stage_input, dt, with_inputs=with_inputs)
+
+    def set_staging(self, tma):
+        bats_set_staging(self.h, tma)
+
+    def staging(self):
+        return bats_get_staging(self.h)
 
     def set_launch(self, persistent=0, blocks_per_cta=1, ctas_per_sm=0, use_graph=0):
         bats_set_launch(self.h, persistent, blocks_per_cta, ctas_per_sm, use_graph)

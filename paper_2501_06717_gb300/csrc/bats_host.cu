@@ -39,6 +39,7 @@ cudaError_t launch_dt(int ngrids, int mode, double cfl, double fixed_dt, double*
                       unsigned long long* smax, unsigned long long* smax_next, cudaStream_t st);
 cudaError_t launch_debug_fill(const StageArgs& a, int b0, int nb, double* T, cudaStream_t st);
 cudaError_t launch_debug_fill_w(const StageArgs& a, int b0, int nb, double* T, cudaStream_t st);
+cudaError_t launch_debug_fill_mx(const StageArgs& a, int b0, int nb, double* T, cudaStream_t st);
 cudaError_t launch_check_conversions(const float* f, const double* d, int n, double* f2d_out, float* d2f_out);
 cudaError_t read_index_flag(int32_t* out);
 cudaError_t launch_debug_wait_timeout(int32_t* err, cudaStream_t st);
@@ -85,6 +86,10 @@ struct bats {
   std::vector<GhostTask> gtasks_h;
   GhostTask* gtasks_d = nullptr;
   float* gbuf = nullptr;
+  // mixed form: tensor maps of W and W1 for the plain stage kernel's tile
+  // staging (interior, x, y, z slab boxes), and the staging layout
+  CUtensorMap tmW[4], tmW1[4];
+  int stage_tma = 1;
   int occ[2] = {1, 1};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<cudaEvent_t> stage_ev;   // pairs around the two stage launches of each step
@@ -439,6 +444,14 @@ StageArgs base_args(bats_t* h) {
 int launch_stage_one(bats_t* h, const StageArgs& a0, bool make_ghosts = true) {
   bool mixed = h->ph.precision == BATS_MIXED;
   StageArgs a = a0;
+  if (mixed) {
+    // the plain kernel stages its tile with tensor copies of the stage input
+    const bool lrn = a.learned || a.kind >= 3;
+    a.gbuf_mx = lrn ? 0 : 1;
+    a.stage_tma = h->stage_tma;
+    const CUtensorMap* m = a.Win == h->W1 ? h->tmW1 : h->tmW;
+    for (int k = 0; k < 4; k++) a.tm[k] = m[k];
+  }
   if (mixed && h->gbuf) {
     // the ghost slabs of faces at resolution changes, from this stage's input
     a.gbuf = h->gbuf;
@@ -682,6 +695,40 @@ int run_steps(bats_t* h, int n, double cfl, double fixed_dt, double* t_out) {
 
 extern "C" {
 
+// cuTensorMapEncodeTiled, looked up through the runtime (no link against the
+// driver library).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The four tensor maps of an FP32 state buffer W (block-major [block][8][512])
+// viewed as the 4-D tensor (i, j, k, 8 * block + v): the interior box
+// 8 x 8 x 8 x 8 with the 32-byte swizzle, and the face-slab boxes of the
+// neighbour's cells nearest a face, 4 x 8 x 8 x 8 (x; a TMA box row is at
+// least 16 bytes), 8 x 2 x 8 x 8 (y) and 8 x 8 x 2 x 8 (z).
+static int encode_tile_maps(bats_t* h, float* W, CUtensorMap tm[4]) {
+  static EncodeTiledFn encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+      return fail(h, BATS_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    encode = reinterpret_cast<EncodeTiledFn>(fn);
+  }
+  const cuuint64_t dims[4] = {NC, NC, NC, static_cast<cuuint64_t>(h->nbt) * NV};
+  const cuuint64_t strides[3] = {NC * sizeof(float), NC * NC * sizeof(float), NCELL * sizeof(float)};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  const cuuint32_t boxes[4][4] = {{NC, NC, NC, NV}, {4, NC, NC, NV}, {NC, 2, NC, NV}, {NC, NC, 2, NV}};
+  for (int m = 0; m < 4; m++) {
+    CUresult r = encode(&tm[m], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, W, dims, strides, boxes[m], estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, m == 0 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(h, BATS_ERR_CUDA, "cuTensorMapEncodeTiled failed for a state buffer");
+  }
+  return BATS_OK;
+}
+
 int bats_create(const bats_grid_desc* grids, int n_grids, const bats_physics* phys, void* cuda_stream,
                 bats_t** out) {
   if (!out) return fail(nullptr, BATS_ERR_INVALID_ARG, "out is NULL");
@@ -776,7 +823,7 @@ int bats_create(const bats_grid_desc* grids, int n_grids, const bats_physics* ph
     return rc;
   }
   if (h->ph.precision == BATS_MIXED && !h->gtasks_h.empty() &&
-      ((rc = dev_alloc(h, &h->gbuf, static_cast<size_t>(h->nslots) * NV * 128)) ||
+      ((rc = dev_alloc(h, &h->gbuf, static_cast<size_t>(h->nslots) * GSLOT)) ||
        (rc = dev_alloc(h, &h->gtasks_d, h->gtasks_h.size())))) {
     free_all(h);
     g_create_error = h->err;
@@ -790,7 +837,8 @@ int bats_create(const bats_grid_desc* grids, int n_grids, const bats_physics* ph
     return rc;
   }
   if (h->ph.precision == BATS_MIXED) {
-    if ((rc = dev_alloc(h, &h->W, nstate)) || (rc = dev_alloc(h, &h->W1, nstate))) {
+    if ((rc = dev_alloc(h, &h->W, nstate)) || (rc = dev_alloc(h, &h->W1, nstate)) ||
+        (rc = encode_tile_maps(h, h->W, h->tmW)) || (rc = encode_tile_maps(h, h->W1, h->tmW1))) {
       free_all(h);
       g_create_error = h->err;
       delete h;
@@ -994,10 +1042,17 @@ int bats_debug_fill_ghosts_w(bats_t* h, int grid, double* T, size_t n) {
   a.Uin = h->U;
   a.Win = h->W;
   a.gbuf = h->gbuf;
+  // the tile as the stage kernel stages it: the plain kernel's staged layout,
+  // the learned kernel's generic one
+  const bool staged = !h->learned;
+  a.gbuf_mx = staged ? 1 : 0;
+  a.stage_tma = h->stage_tma;
+  for (int k = 0; k < 4; k++) a.tm[k] = h->tmW[k];
   int32_t init[3] = {0, INT_MAX, 0};
   CK(h, cudaMemcpyAsync(h->errw, init, sizeof(init), cudaMemcpyHostToDevice, h->stream));
   if (h->gbuf) CK(h, launch_amr_ghosts(a, h->gtasks_d, static_cast<int>(h->gtasks_h.size()), h->stream));
-  CK(h, launch_debug_fill_w(a, G.block0, G.nb, dst, h->stream));
+  if (staged) CK(h, launch_debug_fill_mx(a, G.block0, G.nb, dst, h->stream));
+  else CK(h, launch_debug_fill_w(a, G.block0, G.nb, dst, h->stream));
   if (!dev) CK(h, cudaMemcpyAsync(T, h->staging, need * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
   return index_check(h);
@@ -1055,6 +1110,19 @@ int bats_set_launch(bats_t* h, int persistent, int blocks_per_cta, int ctas_per_
   }
   return BATS_OK;
 }
+
+int bats_set_staging(bats_t* h, int tma) {
+  if (!h) return BATS_ERR_INVALID_ARG;
+  if (tma != 0 && tma != 1) return fail(h, BATS_ERR_INVALID_ARG, "staging layout must be 0 or 1");
+  h->stage_tma = tma;
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  return BATS_OK;
+}
+
+int bats_get_staging(const bats_t* h) { return h ? h->stage_tma : -1; }
 
 int bats_set_mlp(bats_t* h, const float* params) {
   if (!h) return BATS_ERR_INVALID_ARG;

@@ -5,6 +5,7 @@
 // single bulk copy per variable stages into shared memory.
 #pragma once
 #include <cstdint>
+#include <cuda.h>  // CUtensorMap (the type only; maps are encoded through the runtime's driver entry point)
 #include <cuda_runtime.h>
 
 namespace batsk {
@@ -21,6 +22,21 @@ constexpr int FACE_THREADS = 384;   // face phase: two threads per grid line, th
 // mixed form, 1 at 168 in FP64).  512 threads (one per cell in the cell phase)
 // measured slower in the mixed form: 64 registers spill in the face phase.
 constexpr int STAGE_THREADS_MIXED = 384, STAGE_THREADS_FP64 = 384;
+
+// Mixed-form tile of the plain stage kernel (FP32 primitives, floats):
+//  * interior [8 v][8 k][8 j][8 i] in the 32-byte TMA swizzle: the two
+//    16-byte halves of each 8-cell row are exchanged in rows with j >= 4, so
+//    that cell (i, j, k) of variable v sits at
+//    v * 512 + 64 k + 8 j + (i ^ (4 * ((j >> 2) & 1)));
+//  * the six face slabs in the layouts that tensor copies of the neighbour's
+//    cells nearest the face produce, in the neighbour's own cell order:
+//    -x / +x [8 v][8 k][8 j][4 i] (the neighbour's cells 4-7 / 0-3 along x:
+//    ghost cells -2, -1 at positions 2, 3, ghost cells 8, 9 at 0, 1), -y / +y
+//    [8 v][8 k][2 j][8 i] and -z / +z [8 v][2 k][8 j][8 i] (the neighbour's
+//    cells 6, 7 / 0, 1: ghost cells -2, -1 and 8, 9 at positions 0, 1).
+constexpr int MX_GX0 = 4096, MX_GX1 = 6144, MX_GY0 = 8192, MX_GY1 = 9216, MX_GZ0 = 10240, MX_GZ1 = 11264;
+constexpr int MX_TILE = 12288;
+constexpr int GSLOT = 2048;    // floats per ghost-slab buffer slot (either layout)
 
 enum FaceType : int32_t { FACE_SAME = 0, FACE_COARSER = 1, FACE_FINER = 2, FACE_OUTFLOW = 3, FACE_INFLOW = 4 };
 enum B0Mode : int32_t { B0_NONE = 0, B0_UNIFORM = 1, B0_DIPOLE = 2, B0_LINEAR = 3 };
@@ -119,6 +135,13 @@ struct StageArgs {
   float* Xf;              // kind 4: FP32 features, 40 per face
   double* Fd;             // kind 4: plain Rusanov flux (8, x/y/z components), rho_ref, c_ref per face
   const float* Y;         // normalised correction in the face frame, 8 per face
+  // mixed form, plain stage kernel: tensor maps of Win (interior box
+  // 8x8x8x8 with the 32-byte swizzle; face-slab boxes 4x8x8x8, 8x2x8x8,
+  // 8x8x2x8 over the dims (i, j, k, 8 * block + v)), and the staging layout:
+  // 1 = same-level face slabs by tensor copies, 0 = gathered by the threads
+  int32_t stage_tma;
+  int32_t gbuf_mx;        // ghost-slab buffer in the mixed tile's slab layouts (1) or the generic one (0)
+  CUtensorMap tm[4];
 };
 
 }  // namespace batsk

@@ -813,6 +813,22 @@ __device__ __forceinline__ int tile_index(int d, int c, int a, int b) {
   return (c < 0 || c >= NC) ? ghost : inner;
 }
 
+// Staged tile of the mixed plain kernel (layouts: MX_* in bats_internal.h).
+// Interior cell (i, j, k) of one variable in the swizzled tile.
+__device__ __forceinline__ int mx_int(int i, int j, int k) { return 64 * k + 8 * j + (i ^ (4 * ((j >> 2) & 1))); }
+// Start of face s's slab, the variable stride in it, and the element of
+// ghost cell c (-2, -1 or 8, 9 along the face's axis) at transverse
+// coordinates (ta, tb) (increasing axis order).
+__device__ __forceinline__ int mx_slab_base(int s) {
+  return s == 0 ? MX_GX0 : s == 1 ? MX_GX1 : s == 2 ? MX_GY0 : s == 3 ? MX_GY1 : s == 4 ? MX_GZ0 : MX_GZ1;
+}
+__device__ __forceinline__ int mx_slab_vstride(int d) { return d == 0 ? 256 : 128; }
+__device__ __forceinline__ int mx_slab_elem(int d, int side, int c, int ta, int tb) {
+  const int p = side ? c - NC : (d == 0 ? c + 4 : c + 2);
+  return d == 0 ? (tb * NC + ta) * 4 + p : (d == 1 ? (tb * 2 + p) * NC + ta : (p * NC + tb) * NC + ta);
+}
+__device__ __forceinline__ uint32_t mx_slab_bytes(int d) { return d == 0 ? NV * 256 * 4 : NV * 128 * 4; }
+
 // Fill face-slab ghost q (0..767) of block blk into the tile.
 template <bool MIXED, class R>
 __device__ __forceinline__ void fill_ghost(const StageArgs& a, const GhostCtx& cx, const BlockDev& B, int blk, int q,
@@ -932,7 +948,7 @@ __device__ __forceinline__ void fill_ghosts_block_mixed(const StageArgs& a, cons
     if (!((amask >> (q >> 7)) & 1u)) fill_ghost<true, float>(a, cx, B, blk, q, sT);
     else if (copy_amr) {
       const int s = q >> 7, local = q & 127;
-      const float* src = a.gbuf + chk(B.rslot[s], 0, a.nslots) * (NV * 128) + local;
+      const float* src = a.gbuf + chk(B.rslot[s], 0, a.nslots) * GSLOT + local;
 #pragma unroll
       for (int v = 0; v < NV; v++) sT[v * NTILE + NCELL + q] = src[v * 128];
     }
@@ -977,9 +993,15 @@ __global__ void __launch_bounds__(128) k_amr_ghosts(const StageArgs a, const Gho
     int g[3] = {B.bi * NC + i, B.bj * NC + j, B.bk * NC + k};
     sample_w(a.Win, G, a.blocks, a.levmap, B.level, g, a.ph.gm1f, w, a.err);
   }
-  float* o = a.gbuf + chk(T.slot, 0, a.nslots) * (NV * 128) + tid;
+  // slot layout: the generic tile's slab order [8][128] (layer fastest), or
+  // the staged tile's slab layout of this face's axis
+  const int d = T.s >> 1, side = T.s & 1;
+  const int layer = tid & 1, ta = (tid >> 1) & 7, tb = tid >> 4;
+  const int e = a.gbuf_mx ? mx_slab_elem(d, side, side ? NC + layer : layer - 2, ta, tb) : tid;
+  const int vs = a.gbuf_mx ? mx_slab_vstride(d) : 128;
+  float* o = a.gbuf + chk(T.slot, 0, a.nslots) * GSLOT + chki(e, 0, vs);
 #pragma unroll
-  for (int v = 0; v < NV; v++) o[v * 128] = w[v];
+  for (int v = 0; v < NV; v++) o[v * vs] = w[v];
 }
 
 // ---------------------------------------------------------------------------
@@ -991,6 +1013,9 @@ struct StageCfg {
   static constexpr int THREADS = MIXED ? STAGE_THREADS_MIXED : STAGE_THREADS_FP64;
   static constexpr int NFC = 9;  // per face: 8 fluxes and the face-averaged normal B1
   static constexpr size_t SMEM = sizeof(R) * (NV * NTILE + 3 * NFC * NFACE);
+  // the mixed plain kernel's staged tile (MX_TILE floats, 1024-byte aligned
+  // for the swizzled tensor copy) and its face values
+  static constexpr size_t SMEM_MX = sizeof(float) * (MX_TILE + 3 * NFC * NFACE) + 1024;
 };
 
 // Load the 8 primitives of tile cell `idx` in the face frame (normal, t1, t2):
@@ -1049,9 +1074,10 @@ __device__ __forceinline__ float limit_f(float a, float b) {
 // combination of the generic path: split-field flux, fast speed with the
 // total field, F = (F_L + F_R)/2 - cmax (U_R - U_L)/2 with cmax the larger
 // |u_n| + c_f (Rusanov), or the two-state HLL flux.
+// dsgn = 1: W2 = (left, right); dsgn = -1: W2 = (right, left).
 template <bool HAS_B0, int FLX>
 __device__ __forceinline__ void face_flux2(const float2 W2[8], const float B0r[3], float gamma, float inv_gm1,
-                                           float Fr2[8]) {
+                                           float dsgn, float Fr2[8]) {
   const float2 rho = W2[0], u0 = W2[1], u1 = W2[2], u2 = W2[3];
   const float2 b0 = W2[4], b1 = W2[5], b2 = W2[6], p = W2[7];
   float2 Bt0 = b0, Bt1 = b1, Bt2 = b2;
@@ -1081,10 +1107,11 @@ __device__ __forceinline__ void face_flux2(const float2 W2[8], const float B0r[3
     const float sl = fminf(fminf(lo.x, lo.y), 0.f), sr = fmaxf(fmaxf(hi.x, hi.y), 0.f);
     const float den = sr - sl;
     const float k2 = den > 0.f ? 2.f * (sl * rcp_approx(den)) : 0.f;
-    cF = make_float2(2.f + k2, -k2);
-    cU = make_float2(-k2 * sr, k2 * sr);
+    cF = dsgn > 0.f ? make_float2(2.f + k2, -k2) : make_float2(-k2, 2.f + k2);
+    const float ks = dsgn * (k2 * sr);
+    cU = make_float2(-ks, ks);
   } else {
-    const float cmax = fmaxf(fabsf(u0.x) + cf.x, fabsf(u0.y) + cf.y);
+    const float cmax = dsgn * fmaxf(fabsf(u0.x) + cf.x, fabsf(u0.y) + cf.y);
     cU = make_float2(cmax, -cmax);
   }
   auto comb = [&](float2 F, float2 U) -> float {
@@ -1122,57 +1149,157 @@ __device__ __forceinline__ void face_flux2(const float2 W2[8], const float B0r[3
   Fr2[7] = comb(F7, e1);
 }
 
-// The faces of one direction D on this thread's grid line: lane half 0 takes
-// faces 0-4, half 1 faces 5-8 (its fifth step is computed and not stored),
-// sliding a window along the line so that every cell is loaded and every
-// limited slope formed once.  Writes twice the fluxes (un-rotated components)
-// and the sum of the two sides' normal B1 into sF[D][9][576].
+// ---------------------------------------------------------------------------
+// Mixed form, plain stage kernel: tile staging.  Per block one thread issues
+// the copies that complete on the block's mbarrier: the interior by one
+// tensor copy (box 8 x 8 x 8 cells x 8 variables, 32-byte swizzle), each
+// same-level face slab by one tensor copy of the neighbour's cells nearest
+// the face (stage_tma = 1), and each precomputed slab of a face at a
+// resolution change by a bulk copy from the ghost-slab buffer.  The threads
+// fill the rest: outflow and inflow faces, and the same-level slabs when
+// stage_tma = 0.  Layouts: see MX_* in bats_internal.h.
+
+// 4-D tensor copy global -> shared (coordinates innermost first), completing
+// on bar with the copied bytes.
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* tm, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
+
+
+// Primitives of face-slab ghost (s, layer, ta, tb) of block blk for a
+// same-level, outflow or inflow face: the neighbour's (or, outflow, the
+// block's own boundary) cell from Win, or the inflow state.
+__device__ __forceinline__ void mx_ghost_value(const StageArgs& a, const GridDev& G, const BlockDev& B, int blk,
+                                               int s, int layer, int ta, int tb, float w[8]) {
+  const int d = s >> 1, side = s & 1;
+  const int ft = B.ftype[s];
+  if (ft == FACE_INFLOW) {
+#pragma unroll
+    for (int v = 0; v < NV; v++) w[v] = G.Winflow32[v];
+    return;
+  }
+  const int c = side ? NC + layer : layer - 2;
+  const int src = chki(ft == FACE_SAME ? B.fnb[s] : blk, 0, a.nblocks);
+  const int cn = ft == FACE_SAME ? (side ? c - NC : c + NC) : (side ? NC - 1 : 0);
+  const int i = d == 0 ? cn : ta, j = d == 1 ? cn : (d == 0 ? ta : tb), k = d == 2 ? cn : tb;
+  const float* p = a.Win + static_cast<int64_t>(src) * (NV * NCELL) + chki((k * NC + j) * NC + i, 0, NCELL);
+#pragma unroll
+  for (int v = 0; v < NV; v++) w[v] = p[v * NCELL];
+}
+
+// Stage block blk into the tile sT: copies issued by thread 0 on bar, the
+// remaining slabs filled by the calling threads.  Returns after the fill;
+// the caller waits on bar and synchronises.
+__device__ __forceinline__ void mx_stage_tile(const StageArgs& a, const BlockDev& B, int blk, float* sT,
+                                              uint64_t* bar, int tid, int nthr) {
+  unsigned tmask = 0, amask = 0;  // faces by tensor copy / by bulk copy from the ghost-slab buffer
+#pragma unroll
+  for (int f = 0; f < 6; f++) {
+    const int ft = B.ftype[f];
+    tmask |= (ft == FACE_SAME && a.stage_tma ? 1u : 0u) << f;
+    amask |= (ft == FACE_COARSER || ft == FACE_FINER ? 1u : 0u) << f;
+  }
+  if (tid == 0) {
+    fence_proxy_async();
+    uint32_t bytes = NV * NCELL * 4;
+#pragma unroll
+    for (int f = 0; f < 6; f++)
+      if (((tmask | amask) >> f) & 1u) bytes += mx_slab_bytes(f >> 1);
+    mbar_expect_tx(bar, bytes);
+    tma_load_4d(sT, &a.tm[0], 0, 0, 0, blk * NV, bar);
+#pragma unroll
+    for (int f = 0; f < 6; f++) {
+      if ((tmask >> f) & 1u) {
+        const int nb = chki(B.fnb[f], 0, a.nblocks), d = f >> 1, side = f & 1;
+        // the neighbour's cells nearest the face: 4-7 / 0-3 along x, 6-7 / 0-1 along y and z
+        const int o = side ? 0 : (d == 0 ? 4 : 6);
+        tma_load_4d(sT + mx_slab_base(f), &a.tm[1 + d], d == 0 ? o : 0, d == 1 ? o : 0, d == 2 ? o : 0, nb * NV,
+                    bar);
+      } else if ((amask >> f) & 1u) {
+        const float* g = a.gbuf + chk(B.rslot[f], 0, a.nslots) * GSLOT;
+        bulk_g2s(sT + mx_slab_base(f), g, mx_slab_bytes(f >> 1), bar);
+      }
+    }
+  }
+  const unsigned fill = 0x3fu & ~(tmask | amask);
+  const int nfill = __popc(fill) * 128;
+  for (int q = tid; q < nfill; q += nthr) {
+    const int slot = q >> 7, loc = q & 127;
+    unsigned m = fill;
+    for (int k = 0; k < slot; k++) m &= m - 1;
+    const int s = __ffs(m) - 1, d = s >> 1, side = s & 1;
+    const int layer = loc & 1, ta = (loc >> 1) & 7, tb = loc >> 4;
+    float w[8];
+    mx_ghost_value(a, a.grids[B.grid], B, blk, s, layer, ta, tb, w);
+    const int c = side ? NC + layer : layer - 2;
+    float* o = sT + mx_slab_base(s) + chki(mx_slab_elem(d, side, c, ta, tb), 0, mx_slab_vstride(d));
+    const int vs = mx_slab_vstride(d);
+#pragma unroll
+    for (int v = 0; v < NV; v++) o[v * vs] = w[v];
+  }
+}
+
+// The faces of one direction D on this thread's grid line for the staged
+// tile: lane half 0 walks up from cell -2 (faces 0-4), half 1 walks down from
+// cell 9 (faces 8-5; its fifth step is face 4, computed by half 0, and not
+// stored), so that at every step both halves read the same kind of cell (two
+// ghost cells, then interior cells) with the same variable stride.  Walking
+// down, a face's two sides come as (right, left): the dissipation's sign
+// flips with the lane's direction.  Writes twice the fluxes (un-rotated
+// components) and the sum of the two sides' normal B1 into sF[D][9][576].
 template <int D, int LIM, bool HAS_B0, int FLX>
-__device__ __forceinline__ void faces_mixed(const StageArgs& a, const BlockDev& B, const float* sT, float* sF,
-                                            int fline, int fhalf, float gamma, float inv_gm1, int gb0, int gb1,
-                                            int gb2, float lor0, float lor1, float lor2, float dxr0, float dxr1,
-                                            float dxr2) {
+__device__ __forceinline__ void faces_mx(const StageArgs& a, const BlockDev& B, const float* sT, float* sF,
+                                         int fline, int fhalf, float gamma, float inv_gm1, int gb0, int gb1, int gb2,
+                                         float lor0, float lor1, float lor2, float dxr0, float dxr1, float dxr2) {
   constexpr int D1 = D == 2 ? 0 : D + 1, D2 = D == 0 ? 2 : D - 1;
-  constexpr int S = D == 0 ? 1 : (D == 1 ? NC : NC * NC);
-  constexpr int R1 = (1 + D) * NTILE, R2 = (1 + D1) * NTILE, R3 = (1 + D2) * NTILE;
-  constexpr int R4 = (4 + D) * NTILE, R5 = (4 + D1) * NTILE, R6 = (4 + D2) * NTILE, R7 = 7 * NTILE;
+  constexpr int VI = NCELL;                 // variable stride, interior
+  constexpr int VG = D == 0 ? 256 : 128;    // variable stride, this direction's slabs
   const int fta = fline & 7, ftb = fline >> 3;
-  const int ibase = D == 0 ? (ftb * NC + fta) * NC : (D == 1 ? ftb * NC * NC + fta : ftb * NC + fta);
-  const int glo = NCELL + 2 * D * 128 + 2 * (fta + NC * ftb), ghi = glo + 128;
   const bool h1 = fhalf != 0;
-  // tile index of window cell j (after unrolling, j is a constant): half 0
-  // reads cells -2..5, half 1 cells 3..9 (j = 7 repeats cell 9)
-  auto cell = [&](int j) -> int {
-    const int c0 = j - 2, c1 = j + 3;
-    const int i0 = c0 < 0 ? glo + (c0 + 2) : ibase + c0 * S;
-    const int i1 = c1 < NC ? ibase + c1 * S : ghi + (c1 - NC > 1 ? 1 : c1 - NC);
-    return chki(h1 ? i1 : i0, 0, NTILE);
+  // interior index of cell c along the line
+  auto cint = [&](int c) -> int {
+    if constexpr (D == 0) return mx_int(c, fta, ftb);
+    else if constexpr (D == 1) return mx_int(fta, c, ftb);
+    else return mx_int(fta, ftb, c);
   };
-  auto load = [&](int idx, float w[8]) {
-    const float* q = sT + idx;
-    w[0] = q[0]; w[1] = q[R1]; w[2] = q[R2]; w[3] = q[R3];
-    w[4] = q[R4]; w[5] = q[R5]; w[6] = q[R6]; w[7] = q[R7];
+  // window step j: half 0 cell j - 2, half 1 cell 9 - j
+  auto cell_of = [&](int j) -> int { return h1 ? 9 - j : j - 2; };
+  const int gbase = (h1 ? (D == 0 ? MX_GX1 : D == 1 ? MX_GY1 : MX_GZ1) : (D == 0 ? MX_GX0 : D == 1 ? MX_GY0 : MX_GZ0));
+  auto load_g = [&](int j, float w[8]) {  // j = 0, 1: ghost cells
+    const float* q = sT + gbase + chki(mx_slab_elem(D, h1 ? 1 : 0, cell_of(j), fta, ftb), 0, VG);
+    w[0] = q[0]; w[1] = q[(1 + D) * VG]; w[2] = q[(1 + D1) * VG]; w[3] = q[(1 + D2) * VG];
+    w[4] = q[(4 + D) * VG]; w[5] = q[(4 + D1) * VG]; w[6] = q[(4 + D2) * VG]; w[7] = q[7 * VG];
+  };
+  auto load_i = [&](int j, float w[8]) {  // j >= 2: interior cells
+    const float* q = sT + chki(cint(cell_of(j)), 0, NCELL);
+    w[0] = q[0]; w[1] = q[(1 + D) * VI]; w[2] = q[(1 + D1) * VI]; w[3] = q[(1 + D2) * VI];
+    w[4] = q[(4 + D) * VI]; w[5] = q[(4 + D1) * VI]; w[6] = q[(4 + D2) * VI]; w[7] = q[7 * VI];
   };
   float W0[8], d[8], WL[8];
   {
     float Wm2[8], Wm1[8];
-    load(cell(0), Wm2);
-    load(cell(1), Wm1);
-    load(cell(2), W0);
+    load_g(0, Wm2);
+    load_g(1, Wm1);
+    load_i(2, W0);
 #pragma unroll
     for (int v = 0; v < NV; v++) {
       d[v] = W0[v] - Wm1[v];
       WL[v] = fmaf(0.5f, limit_f<LIM>(Wm1[v] - Wm2[v], d[v]), Wm1[v]);
     }
   }
-  const int f0 = h1 ? 5 : 0;
-  float* const fo = sF + D * (9 * NFACE) + chki(fline * 9 + f0, 0, NFACE - 3);  // + k, k <= 4 - f0 / 5
+  // face of step k: half 0 face k, half 1 face 8 - k
+  const int fstep = h1 ? -1 : 1;
+  float* const fo = sF + D * (9 * NFACE) + chki(fline * 9 + (h1 ? 8 : 0), 0, NFACE);
+  const float dsgn = h1 ? -1.f : 1.f;
 #pragma unroll
   for (int k = 0; k < 5; k++) {
     float Wp[8];
-    load(cell(k + 3), Wp);
-    // the face's two sides, then the window moves on (the next face's left
-    // state, cell and difference), so that only the pairs stay live
+    load_i(k + 3, Wp);
     float2 W2[8];
 #pragma unroll
     for (int v = 0; v < NV; v++) {
@@ -1185,7 +1312,7 @@ __device__ __forceinline__ void faces_mixed(const StageArgs& a, const BlockDev& 
     }
     float B0r[3] = {0.f, 0.f, 0.f};
     if constexpr (HAS_B0) {
-      const int f = f0 + k;
+      const int f = h1 ? 8 - k : k;
       const int ci_ = D == 0 ? f : fta, cj_ = D == 1 ? f : (D == 0 ? fta : ftb), ck_ = D == 2 ? f : ftb;
       float B0f[3];
       b0_face<float>(a.ph, D, ci_, cj_, ck_, gb0, gb1, gb2, lor0, lor1, lor2, dxr0, dxr1, dxr2, B0f);
@@ -1194,31 +1321,32 @@ __device__ __forceinline__ void faces_mixed(const StageArgs& a, const BlockDev& 
       B0r[2] = B0f[D2];
     }
     float Fr2[8];
-    face_flux2<HAS_B0, FLX>(W2, B0r, gamma, inv_gm1, Fr2);
+    face_flux2<HAS_B0, FLX>(W2, B0r, gamma, inv_gm1, dsgn, Fr2);
     const float bn2 = W2[4].x + W2[4].y;
-    if (k == 4 && h1) continue;  // half 1 has four faces
-    fo[k] = Fr2[0];
-    fo[(1 + D) * NFACE + k] = Fr2[1];
-    fo[(1 + D1) * NFACE + k] = Fr2[2];
-    fo[(1 + D2) * NFACE + k] = Fr2[3];
-    fo[(4 + D) * NFACE + k] = Fr2[4];
-    fo[(4 + D1) * NFACE + k] = Fr2[5];
-    fo[(4 + D2) * NFACE + k] = Fr2[6];
-    fo[7 * NFACE + k] = Fr2[7];
-    fo[8 * NFACE + k] = bn2;
-    // refluxing: the block-face fluxes (face 0 of half 0, face 8 of half 1)
-    if ((k == 0 || k == 3) && a.freg && (k == 0) == !h1) {
-      const int sl = chki(B.rslot[2 * D + (k == 3 ? 1 : 0)], -1, a.nslots);
+    if (k == 4 && h1) continue;  // face 4 is half 0's
+    float* const o = fo + k * fstep;
+    o[0] = Fr2[0];
+    o[(1 + D) * NFACE] = Fr2[1];
+    o[(1 + D1) * NFACE] = Fr2[2];
+    o[(1 + D2) * NFACE] = Fr2[3];
+    o[(4 + D) * NFACE] = Fr2[4];
+    o[(4 + D1) * NFACE] = Fr2[5];
+    o[(4 + D2) * NFACE] = Fr2[6];
+    o[7 * NFACE] = Fr2[7];
+    o[8 * NFACE] = bn2;
+    // refluxing: the block-face fluxes (face 0: half 0 step 0; face 8: half 1 step 0)
+    if (k == 0 && a.freg) {
+      const int sl = chki(B.rslot[2 * D + (h1 ? 1 : 0)], -1, a.nslots);
       if (sl >= 0) {
-        double* o = a.freg + (static_cast<int64_t>(sl) * 64 + fta * NC + ftb) * NV;
-        o[0] = f2d_int(0.5f * Fr2[0]);
-        o[1 + D] = f2d_int(0.5f * Fr2[1]);
-        o[1 + D1] = f2d_int(0.5f * Fr2[2]);
-        o[1 + D2] = f2d_int(0.5f * Fr2[3]);
-        o[4 + D] = f2d_int(0.5f * Fr2[4]);
-        o[4 + D1] = f2d_int(0.5f * Fr2[5]);
-        o[4 + D2] = f2d_int(0.5f * Fr2[6]);
-        o[7] = f2d_int(0.5f * Fr2[7]);
+        double* r = a.freg + (static_cast<int64_t>(sl) * 64 + fta * NC + ftb) * NV;
+        r[0] = f2d_int(0.5f * Fr2[0]);
+        r[1 + D] = f2d_int(0.5f * Fr2[1]);
+        r[1 + D1] = f2d_int(0.5f * Fr2[2]);
+        r[1 + D2] = f2d_int(0.5f * Fr2[3]);
+        r[4 + D] = f2d_int(0.5f * Fr2[4]);
+        r[4 + D1] = f2d_int(0.5f * Fr2[5]);
+        r[4 + D2] = f2d_int(0.5f * Fr2[6]);
+        r[7] = f2d_int(0.5f * Fr2[7]);
       }
     }
   }
@@ -1232,13 +1360,22 @@ __device__ __forceinline__ void faces_mixed(const StageArgs& a, const BlockDev& 
 // flux differences x, y, z, the sources, the update and (last stage) the CFL
 // bound.
 template <bool MIXED, int LIM, bool HAS_B0, bool LRN, int FLX>
-__global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1) k_stage(const StageArgs a) {
+__global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1)
+    k_stage(const __grid_constant__ StageArgs a) {
   using R = typename StageCfg<MIXED>::R;
   constexpr int STAGE_THREADS = StageCfg<MIXED>::THREADS;
   constexpr int NFC = StageCfg<MIXED>::NFC;
+  // mixed form without the learned correction: the staged tile (tensor copies)
+  constexpr bool MX = MIXED && !LRN;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  R* sT = reinterpret_cast<R*>(smem_raw);       // [8][1280] tile
-  R* sF = sT + NV * NTILE;                       // [3][9][576] face values
+  R* sT;                                         // tile: [8][1280] (generic) or the staged layout (MX)
+  if constexpr (MX) {
+    const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
+    sT = reinterpret_cast<R*>(smem_raw + pad);
+  } else {
+    sT = reinterpret_cast<R*>(smem_raw);
+  }
+  R* sF = sT + (MX ? MX_TILE : NV * NTILE);      // [3][9][576] face values
   __shared__ uint64_t bar;
   __shared__ R sred[STAGE_THREADS / 32];
 
@@ -1281,8 +1418,10 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1) k_sta
       const GridDev& G = a.grids[B.grid];
       GhostCtx cx{&G, a.blocks, a.levmap, a.Uin, a.err};
 
-      // 1. interior by TMA bulk copies (one per variable), ghosts by threads
-      if (tid == 0) {
+      // 1. interior by TMA bulk copies (one per variable), ghosts by threads;
+      //    the mixed plain kernel: the staged tile (tensor copies)
+      if constexpr (MX) mx_stage_tile(a, B, blk, reinterpret_cast<float*>(sT), &bar, tid, STAGE_THREADS);
+      if (tid == 0 && !MX) {
         fence_proxy_async();
         // mixed form: the ghost slabs of faces at resolution changes come
         // precomputed, by bulk copies on the same barrier
@@ -1302,11 +1441,13 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1) k_sta
         if constexpr (MIXED) {
           for (int f = 0; f < 6; f++) {
             if (!((amask >> f) & 1u)) continue;
-            const float* g = a.gbuf + chk(B.rslot[f], 0, a.nslots) * (NV * 128);
+            const float* g = a.gbuf + chk(B.rslot[f], 0, a.nslots) * GSLOT;
 #pragma unroll
             for (int v = 0; v < NV; v++) bulk_g2s(sT + v * NTILE + NCELL + f * 128, g + v * 128, 128 * sizeof(float), &bar);
           }
         }
+      }
+      if (tid == 0) {
         // this CTA's next block: its interior on its way to L2 while this
         // block is computed, so that its bulk copies read L2, not HBM
         const int nblk = blk + 1 < b_end ? blk + 1 : (item + static_cast<int>(gridDim.x)) * a.blocks_per_item;
@@ -1320,8 +1461,12 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1) k_sta
         if (reads_ubase) prefetch_l2(a.Ubase + boff, NV * NCELL * sizeof(double));
         if (MIXED && a.kind == 1) prefetch_l2(a.Uin + boff, NV * NCELL * sizeof(double));
       }
-      if constexpr (MIXED) fill_ghosts_block_mixed(a, cx, B, blk, sT, tid, STAGE_THREADS, false);
-      else fill_ghosts_block<false, double>(a, cx, B, blk, sT, sF, tid, STAGE_THREADS);
+      if constexpr (MX) {
+      } else if constexpr (MIXED) {
+        fill_ghosts_block_mixed(a, cx, B, blk, sT, tid, STAGE_THREADS, false);
+      } else {
+        fill_ghosts_block<false, double>(a, cx, B, blk, sT, sF, tid, STAGE_THREADS);
+      }
       if (!mbar_wait_bounded(&bar, parity, a.err)) mbar_wait_bounded(&bar, parity, a.err);
       parity ^= 1u;
       __syncthreads();
@@ -1587,8 +1732,14 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1) k_sta
             in_body = (x * x + y * y + z * z) < G.body_r * G.body_r;
           }
           R Wc[8];
+          if constexpr (MX) {
+            const int cs = c ^ (((c >> 5) & 1) << 2);  // the interior's swizzle (j >= 4: halves exchanged)
 #pragma unroll
-          for (int v = 0; v < NV; v++) Wc[v] = sT[v * NTILE + c];
+            for (int v = 0; v < NV; v++) Wc[v] = sT[v * NCELL + cs];
+          } else {
+#pragma unroll
+            for (int v = 0; v < NV; v++) Wc[v] = sT[v * NTILE + c];
+          }
           R B0c[3] = {R(0), R(0), R(0)};
           R S[8] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
           if constexpr (HAS_B0) b0_face<R>(ph, -1, ci, cj, ck, gb0, gb1, gb2, lor0, lor1, lor2, dxr0, dxr1, dxr2, B0c);
@@ -1749,18 +1900,18 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1) k_sta
         return any_bad;
       };
 
-      if constexpr (MIXED && !LRN) {
+      if constexpr (MX) {
         // direction fixed at compile time per warp group (fd is warp-uniform)
         if (tid < FACE_THREADS) {
           if (fd == 0)
-            faces_mixed<0, LIM, HAS_B0, FLX>(a, B, sT, sF, fline, fhalf, gamma, inv_gm1, gb0, gb1, gb2, lor0, lor1,
-                                             lor2, dxr0, dxr1, dxr2);
+            faces_mx<0, LIM, HAS_B0, FLX>(a, B, sT, sF, fline, fhalf, gamma, inv_gm1, gb0, gb1, gb2, lor0, lor1, lor2,
+                                          dxr0, dxr1, dxr2);
           else if (fd == 1)
-            faces_mixed<1, LIM, HAS_B0, FLX>(a, B, sT, sF, fline, fhalf, gamma, inv_gm1, gb0, gb1, gb2, lor0, lor1,
-                                             lor2, dxr0, dxr1, dxr2);
+            faces_mx<1, LIM, HAS_B0, FLX>(a, B, sT, sF, fline, fhalf, gamma, inv_gm1, gb0, gb1, gb2, lor0, lor1, lor2,
+                                          dxr0, dxr1, dxr2);
           else
-            faces_mixed<2, LIM, HAS_B0, FLX>(a, B, sT, sF, fline, fhalf, gamma, inv_gm1, gb0, gb1, gb2, lor0, lor1,
-                                             lor2, dxr0, dxr1, dxr2);
+            faces_mx<2, LIM, HAS_B0, FLX>(a, B, sT, sF, fline, fhalf, gamma, inv_gm1, gb0, gb1, gb2, lor0, lor1, lor2,
+                                          dxr0, dxr1, dxr2);
         }
       } else {
         if (tid < FACE_THREADS) faces(true);
@@ -2123,6 +2274,43 @@ __global__ void k_debug_fill_w(const StageArgs a, int b0, int nb, double* T) {
   write_debug_tile(sT, nb, T);
 }
 
+// The same for the mixed plain kernel's staged tile: block blockIdx.x staged
+// exactly as the stage kernel stages it (tensor copies or thread gathers, as
+// stage_tma says, and the precomputed slabs of faces at resolution changes),
+// then written out through the tile's layout.
+constexpr size_t kDebugFillMxSmem = sizeof(float) * MX_TILE + 1024;
+__global__ void k_debug_fill_mx(const __grid_constant__ StageArgs a, int b0, int nb, double* T) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ uint64_t bar;
+  const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
+  float* sT = reinterpret_cast<float*>(smem_raw + pad);
+  const int blk = b0 + blockIdx.x;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  mx_stage_tile(a, a.blocks[blk], blk, sT, &bar, threadIdx.x, blockDim.x);
+  if (!mbar_wait_bounded(&bar, 0, a.err)) mbar_wait_bounded(&bar, 0, a.err);
+  __syncthreads();
+  const int tile = 12 * 12 * 12;
+  for (int e = threadIdx.x; e < tile; e += blockDim.x) {
+    const int i = e % 12 - 2, j = (e / 12) % 12 - 2, k = e / 144 - 2;
+    const int oi = (i < 0 || i >= NC), oj = (j < 0 || j >= NC), ok = (k < 0 || k >= NC);
+    int t = -1, vs = 0;
+    if (oi + oj + ok == 0) {
+      t = mx_int(i, j, k);
+      vs = NCELL;
+    } else if (oi + oj + ok == 1) {
+      const int d = oi ? 0 : (oj ? 1 : 2);
+      const int c = d == 0 ? i : (d == 1 ? j : k);
+      const int ta = d == 0 ? j : i, tb = d == 2 ? j : k;
+      const int side = c >= NC ? 1 : 0;
+      t = mx_slab_base(2 * d + side) + mx_slab_elem(d, side, c, ta, tb);
+      vs = mx_slab_vstride(d);
+    }
+    for (int v = 0; v < NV; v++)
+      T[(static_cast<int64_t>(v) * nb + blockIdx.x) * tile + e] = t >= 0 ? static_cast<double>(sT[t + v * vs]) : 0.0;
+  }
+}
+
 // Conversion self-check against CUDA's own conversions: n float/double pairs.
 __global__ void k_check_conversions(const float* f, const double* d, int n, double* f2d_out, float* d2f_out) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -2136,6 +2324,11 @@ __global__ void k_check_conversions(const float* f, const double* d, int n, doub
 
 size_t stage_smem_bytes(bool mixed) {
   return mixed ? StageCfg<true>::SMEM : StageCfg<false>::SMEM;
+}
+// dynamic shared memory of a stage kernel: the mixed plain kernel stages
+// its own tile layout
+static size_t stage_smem(bool mixed, bool lrn) {
+  return mixed ? (lrn ? StageCfg<true>::SMEM : StageCfg<true>::SMEM_MX) : StageCfg<false>::SMEM;
 }
 
 using StageFn = void (*)(const StageArgs);
@@ -2165,7 +2358,7 @@ cudaError_t stage_setup(int occ[2]) {
                                  static_cast<int>(StageCfg<false>::SMEM));
         if (e == cudaSuccess)
           e = cudaFuncSetAttribute(stage_fn<true>(lim, b0, lrn, flux), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   static_cast<int>(StageCfg<true>::SMEM));
+                                   static_cast<int>(stage_smem(true, lrn)));
       }
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_debug_fill, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2174,11 +2367,14 @@ cudaError_t stage_setup(int occ[2]) {
     e = cudaFuncSetAttribute(k_debug_fill_w, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(kDebugFillWSmem));
   if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_debug_fill_mx, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kDebugFillMxSmem));
+  if (e == cudaSuccess)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], stage_fn<false>(0, false), StageCfg<false>::THREADS,
                                                       StageCfg<false>::SMEM);
   if (e == cudaSuccess)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], stage_fn<true>(0, false), StageCfg<true>::THREADS,
-                                                      StageCfg<true>::SMEM);
+                                                      stage_smem(true, false));
   return e;
 }
 
@@ -2187,7 +2383,7 @@ cudaError_t launch_stage_kernel(bool mixed, int grid, cudaStream_t st, const Sta
   const bool lrn = a.learned || a.kind >= 3;
   const int flux = a.ph.flux;
   if (mixed)
-    stage_fn<true>(a.ph.limiter, b0, lrn, flux)<<<grid, StageCfg<true>::THREADS, StageCfg<true>::SMEM, st>>>(a);
+    stage_fn<true>(a.ph.limiter, b0, lrn, flux)<<<grid, StageCfg<true>::THREADS, stage_smem(true, lrn), st>>>(a);
   else
     stage_fn<false>(a.ph.limiter, b0, lrn, flux)<<<grid, StageCfg<false>::THREADS, StageCfg<false>::SMEM, st>>>(a);
   return cudaGetLastError();
@@ -2245,6 +2441,10 @@ cudaError_t launch_debug_fill(const StageArgs& a, int b0, int nb, double* T, cud
 }
 cudaError_t launch_debug_fill_w(const StageArgs& a, int b0, int nb, double* T, cudaStream_t st) {
   k_debug_fill_w<<<nb, 256, kDebugFillWSmem, st>>>(a, b0, nb, T);
+  return cudaGetLastError();
+}
+cudaError_t launch_debug_fill_mx(const StageArgs& a, int b0, int nb, double* T, cudaStream_t st) {
+  k_debug_fill_mx<<<nb, 256, kDebugFillMxSmem, st>>>(a, b0, nb, T);
   return cudaGetLastError();
 }
 // Checked build: read and clear the index-check flag (always 0 otherwise).

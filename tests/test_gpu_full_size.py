@@ -1,8 +1,8 @@
 """The benchmark's workload at full size (64 grids, 60,194 blocks, 30.8 M
 cells) in the launch forms the benchmark's autotuner chooses between (one
 block or four consecutive blocks per non-persistent CTA, four per persistent
-CTA; whole steps replayed from a CUDA graph), and in the form the autotuner
-itself picks on this GPU: one step of the whole batch, checked grid by grid
+CTA, the mixed form's two staging layouts; whole steps replayed from a CUDA
+graph), and in the form the autotuner itself picks on this GPU: one step of the whole batch, checked grid by grid
 against the oracle on a sample of the grids (the largest, the smallest and
 two others), in both precisions."""
 import os
@@ -45,7 +45,7 @@ def oracle_steps(grids):
     return out
 
 
-@pytest.mark.parametrize("form", [(0, 1, 0), (0, 4, 0), (1, 4, 0), "autotuned"])
+@pytest.mark.parametrize("form", [(0, 1, 0, 1), (0, 4, 0, 1), (1, 4, 0, 1), (0, 2, 0, 0), "autotuned"])
 @pytest.mark.parametrize("prec,tol", [(1, 1e-5), (0, 1e-12)])
 def test_full_batched_workload_sampled_against_the_oracle(grids, oracle_steps, prec, tol, form):
     from paper_2501_06717_gb300 import bats as B
@@ -63,6 +63,8 @@ def test_full_batched_workload_sampled_against_the_oracle(grids, oracle_steps, p
             print("autotuner pick", best)
             s.set_launch(best[0], best[1], best[2], 1)
         else:
+            if prec == 1:
+                s.set_staging(form[3])   # same-level face slabs by tensor copies (1) or thread gathers (0)
             s.set_launch(form[0], form[1], form[2], 1)
         s.set_states()
         s.step(1, 0.8)

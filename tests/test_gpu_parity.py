@@ -95,13 +95,17 @@ def test_ghost_fill_bitwise(B, case):
     assert np.array_equal(Tg[:, :, m], To[:, :, m])
 
 
+@pytest.mark.parametrize("staging", [1, 0])
 @pytest.mark.parametrize("case", ["amr_periodic", "amr_inflow", "magnetosphere", "blast"])
-def test_mixed_ghost_fill_matches_oracle(B, case):
+def test_mixed_ghost_fill_matches_oracle(B, case, staging):
     """The mixed form fills ghosts from the FP32 primitives alone: at
     resolution changes the restriction and prolongation are the oracle's
     conservative ones written in primitive form.  Against the oracle's FP64
     fill turned into primitives, face slabs and interior, per variable scaled
-    by its largest magnitude: FP32 rounding of a few operations, bound 4e-6."""
+    by its largest magnitude: FP32 rounding of a few operations, bound 4e-6.
+    The view is the stage kernel's own staged tile (swizzled interior, face
+    slabs by tensor copies or by thread gathers) read back through its
+    layout, in both staging layouts."""
     if case == "amr_periodic":
         q = _amr_problem(3, True)
     elif case == "amr_inflow":
@@ -115,6 +119,8 @@ def test_mixed_ghost_fill_matches_oracle(B, case):
                              0.2 * np.cos(2 * X[2]), 0.1 * X[0], 0.5 + 0.2 * X[2], 0.3 * np.cos(X[0]),
                              -0.2 + 0 * X[0], 1 + 0.5 * np.exp(-3 * (X[1] ** 2 + X[2] ** 2))])
     with B.Solver(q, precision=B.BATS_MIXED) as s:
+        s.set_staging(staging)
+        assert s.staging() == staging
         s.set_state(0, q.U0)
         Tg = s.fill_ghosts_w(0)
     To, _ = O.fill_ghosts(q, q.U0)
@@ -254,6 +260,41 @@ def test_batched_grids_equal_single_runs_bitwise(B):
             s.step(4, 0.8)
             assert np.array_equal(s.get_state(0), batched[g])
             assert s.time(0) == times[g]
+
+
+@pytest.mark.parametrize("case", ["blast", "magnetosphere", "periodic_amr"])
+def test_staging_layouts_bitwise_equal(B, case):
+    """The mixed form's two staging layouts (same-level face slabs by tensor
+    copies or gathered by the threads) give the same state bit for bit, on
+    a grid with resolution changes and outflow faces, one with inflow faces,
+    a dipole B0 and the inner body, and a periodic one, in every launch form
+    the autotuner tries (persistent or not, one to eight blocks per CTA)."""
+    if case == "blast":
+        q = W.blast()
+    elif case == "magnetosphere":
+        q = W.magnetosphere()
+    else:
+        q = _amr_problem(3, True)
+    ref = None
+    for staging in (1, 0):
+        for persistent, bpc in [(0, 1), (0, 4), (1, 2), (1, 8)]:
+            with B.Solver(q, precision=B.BATS_MIXED, persistent=persistent, blocks_per_cta=bpc) as s:
+                s.set_staging(staging)
+                s.set_state(0, q.U0)
+                s.step(3, 0.8)
+                U = s.get_state(0)
+            if ref is None:
+                ref = U
+            else:
+                assert np.array_equal(U, ref), (staging, persistent, bpc)
+
+
+def test_staging_layout_is_validated(B):
+    q = W.orszag_tang()
+    with B.Solver(q, precision=B.BATS_MIXED) as s:
+        with pytest.raises(B.BatsError):
+            s.set_staging(2)
+        assert s.staging() == 1
 
 
 @pytest.mark.parametrize("prec", [0, 1])
