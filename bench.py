@@ -38,6 +38,10 @@ from paper_2501_06717_gb300 import workloads as W  # noqa: E402
 METRIC = "cell-updates/s/GB300"
 UNIT = "cell-updates/s"
 BYTES_PER_CELL_UPDATE = 320  # FP64 state: stage 1 reads U^n, writes U*; stage 2 reads U*, U^n, writes U^{n+1}
+# FP64 form: executed FP64 flops per cell-update (DADD + DMUL + 2 DFMA, both
+# stages: 1,539 + 1,865), ncu counters of k_stage<0,...> on the first 8 grids
+# of the batched workload (profiles/k_stage_fp64_batched8_ncu.md)
+FP64_FLOPS_PER_CELL_UPDATE = 3404
 
 # DRAM traffic of one k_stage launch per cell, from the ncu capture summarised
 # in profiles/ (None until a capture of the current kernel source exists).
@@ -429,6 +433,7 @@ def main():
 
     # the plain FP64 path on the same workload, for the mixed-vs-FP64 comparison
     fp64 = None
+    fp64_roofline = None
     if prec == bats.BATS_MIXED and args.fp64_steps > 0:
         solver.close()
         s64 = bats.Solver(problems, precision=bats.BATS_FP64, stream=stream, persistent=1, blocks_per_cta=1)
@@ -443,6 +448,15 @@ def main():
         torch.cuda.synchronize()
         fp64 = cells * args.fp64_steps / (e0.elapsed_time(e1) * 1e-3)
         s64.close()
+        # its roofline: the FP64 pipe.  Executed FP64 flops per cell-update
+        # (DADD + DMUL + 2 DFMA, both stages) from the ncu counters of the
+        # FP64 stage kernel; the peak is this GPU's FP64 FMA rate, measured now
+        peak64 = bats.bats_fp64_fma_rate(stream)
+        achieved64 = FP64_FLOPS_PER_CELL_UPDATE * fp64 / 1e9
+        fp64_roofline = {"bound": "fp64", "achieved": achieved64, "peak": peak64, "unit": "GFLOP/s",
+                         "frac": achieved64 / peak64 if peak64 > 0 else None,
+                         "flops_per_cell_update": FP64_FLOPS_PER_CELL_UPDATE,
+                         "peak_source": "measured (bats_fp64_fma_rate: independent FMA chains)"}
 
     learned = None
     if rank == 0 and world == 1 and not args.no_learned and args.workload == "batched":
@@ -477,6 +491,7 @@ def main():
             "gpu_launches": launches,
             "clocks": clk,
             "fp64_value": fp64,
+            "fp64_roofline": fp64_roofline,
             "learned_form": learned,
             "other_workloads_cell_updates_per_s": others,
             "stage_share": stage_ms / stage_total_ms if stage_total_ms > 0 else None,

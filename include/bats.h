@@ -230,6 +230,16 @@ int bats_set_launch(bats_t* h, int persistent, int blocks_per_cta, int ctas_per_
 int bats_set_staging(bats_t* h, int tma);
 int bats_get_staging(const bats_t* h);
 
+/* Measurement helper, no counterpart in the paper: the FP64 FMA throughput of
+ * the current device in GFLOP/s (2 flops per FMA), the ceiling of the FP64
+ * form's stage kernel, whose FP64 pipe is its bound.  Runs a kernel of
+ * independent FMA chains (eight per thread, 8 CTAs of 256 threads per SM)
+ * four times on cuda_stream (NULL: the legacy default stream) and returns the
+ * best of the last three (CUDA events).  Allocates and frees 8 bytes of
+ * device memory.  BATS_ERR_CUDA on a CUDA failure (message: bats_last_error
+ * with NULL). */
+int bats_fp64_fma_rate(void* cuda_stream, double* gflops);
+
 /* Number of kernels launched by the last bats_step call. */
 int bats_get_launch_count(bats_t* h, long long* n);
 

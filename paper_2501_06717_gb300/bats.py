@@ -107,6 +107,7 @@ def lib():
     L.bats_debug_wait_timeout.argtypes = [vp]
     L.bats_set_launch.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     L.bats_set_staging.argtypes = [vp, ctypes.c_int]
+    L.bats_fp64_fma_rate.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
     L.bats_get_staging.argtypes = [vp]
     L.bats_get_staging.restype = ctypes.c_int
     L.bats_get_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
@@ -302,6 +303,16 @@ def bats_set_staging(h, tma):
 
 def bats_get_staging(h):
     return lib().bats_get_staging(h)
+
+
+def bats_fp64_fma_rate(stream=None):
+    """FP64 FMA throughput of the current device in GFLOP/s (2 flops per FMA)."""
+    g = ctypes.c_double(0.0)
+    s = None
+    if stream is not None:
+        s = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(None, lib().bats_fp64_fma_rate(s, ctypes.byref(g)))
+    return g.value
 
 
 def bats_get_launch_count(h):

@@ -41,6 +41,7 @@ cudaError_t launch_debug_fill(const StageArgs& a, int b0, int nb, double* T, cud
 cudaError_t launch_debug_fill_w(const StageArgs& a, int b0, int nb, double* T, cudaStream_t st);
 cudaError_t launch_debug_fill_mx(const StageArgs& a, int b0, int nb, double* T, cudaStream_t st);
 cudaError_t launch_check_conversions(const float* f, const double* d, int n, double* f2d_out, float* d2f_out);
+cudaError_t launch_fp64_fma_rate(double* out, int ctas, int iters, cudaStream_t st);
 cudaError_t read_index_flag(int32_t* out);
 cudaError_t launch_debug_wait_timeout(int32_t* err, cudaStream_t st);
 cudaError_t mlp_alloc(MlpDev* w);
@@ -1108,6 +1109,38 @@ int bats_set_launch(bats_t* h, int persistent, int blocks_per_cta, int ctas_per_
     cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
   }
+  return BATS_OK;
+}
+
+int bats_fp64_fma_rate(void* cuda_stream, double* gflops) {
+  if (!gflops) return fail(nullptr, BATS_ERR_INVALID_ARG, "gflops is required");
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  int dev = 0, nsm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return fail(nullptr, BATS_ERR_CUDA, cudaGetErrorString(e));
+  const int ctas = nsm * 8, iters = 4096;
+  double* out = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  e = cudaMalloc(&out, sizeof(double));
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  double best = 0.0;
+  for (int r = 0; r < 4 && e == cudaSuccess; r++) {  // the first launch warms up
+    e = cudaEventRecord(e0, st);
+    if (e == cudaSuccess) e = launch_fp64_fma_rate(out, ctas, iters, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    const double flops = 2.0 * 8.0 * iters * 256.0 * ctas;
+    if (e == cudaSuccess && r > 0 && ms > 0.f) best = std::max(best, flops / (ms * 1e-3) / 1e9);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (out) cudaFree(out);
+  if (e != cudaSuccess) return fail(nullptr, BATS_ERR_CUDA, cudaGetErrorString(e));
+  *gflops = best;
   return BATS_OK;
 }
 

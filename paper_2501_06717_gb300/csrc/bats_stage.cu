@@ -1192,19 +1192,29 @@ __device__ __forceinline__ void mx_ghost_value(const StageArgs& a, const GridDev
   for (int v = 0; v < NV; v++) w[v] = p[v * NCELL];
 }
 
-// Stage block blk into the tile sT: copies issued by thread 0 on bar, the
-// remaining slabs filled by the calling threads.  Returns after the fill;
-// the caller waits on bar and synchronises.
-__device__ __forceinline__ void mx_stage_tile(const StageArgs& a, const BlockDev& B, int blk, float* sT,
-                                              uint64_t* bar, int tid, int nthr) {
-  unsigned tmask = 0, amask = 0;  // faces by tensor copy / by bulk copy from the ghost-slab buffer
+// Faces of block B whose slabs come by copies: tensor copies (same level,
+// stage_tma = 1) and bulk copies from the ghost-slab buffer (resolution
+// changes).
+__device__ __forceinline__ void mx_copy_masks(const StageArgs& a, const BlockDev& B, unsigned& tmask,
+                                              unsigned& amask) {
+  tmask = 0;
+  amask = 0;
 #pragma unroll
   for (int f = 0; f < 6; f++) {
     const int ft = B.ftype[f];
     tmask |= (ft == FACE_SAME && a.stage_tma ? 1u : 0u) << f;
     amask |= (ft == FACE_COARSER || ft == FACE_FINER ? 1u : 0u) << f;
   }
-  if (tid == 0) {
+}
+
+// Issue (one thread) the copies of block blk's tile on bar: the interior,
+// the copied face slabs.  Any generic-proxy access to sT that they overwrite
+// must be ordered before (the caller's barrier); this fences the proxies.
+__device__ __forceinline__ void mx_issue_copies(const StageArgs& a, const BlockDev& B, int blk, float* sT,
+                                                uint64_t* bar) {
+  unsigned tmask, amask;
+  mx_copy_masks(a, B, tmask, amask);
+  {
     fence_proxy_async();
     uint32_t bytes = NV * NCELL * 4;
 #pragma unroll
@@ -1226,6 +1236,14 @@ __device__ __forceinline__ void mx_stage_tile(const StageArgs& a, const BlockDev
       }
     }
   }
+}
+
+// The calling threads fill the face slabs of block blk that no copy brings:
+// outflow and inflow faces, and same-level faces when stage_tma = 0.
+__device__ __forceinline__ void mx_fill_slabs(const StageArgs& a, const BlockDev& B, int blk, float* sT, int tid,
+                                              int nthr) {
+  unsigned tmask, amask;
+  mx_copy_masks(a, B, tmask, amask);
   const unsigned fill = 0x3fu & ~(tmask | amask);
   const int nfill = __popc(fill) * 128;
   for (int q = tid; q < nfill; q += nthr) {
@@ -1242,6 +1260,15 @@ __device__ __forceinline__ void mx_stage_tile(const StageArgs& a, const BlockDev
 #pragma unroll
     for (int v = 0; v < NV; v++) o[v * vs] = w[v];
   }
+}
+
+// Stage block blk into the tile sT: copies issued by thread 0 on bar, the
+// remaining slabs filled by the calling threads.  Returns after the fill;
+// the caller waits on bar and synchronises.
+__device__ __forceinline__ void mx_stage_tile(const StageArgs& a, const BlockDev& B, int blk, float* sT,
+                                              uint64_t* bar, int tid, int nthr) {
+  if (tid == 0) mx_issue_copies(a, B, blk, sT, bar);
+  mx_fill_slabs(a, B, blk, sT, tid, nthr);
 }
 
 // The faces of one direction D on this thread's grid line for the staged
@@ -1352,6 +1379,194 @@ __device__ __forceinline__ void faces_mx(const StageArgs& a, const BlockDev& B, 
   }
 }
 
+// Mixed plain kernel, common case (first or second midpoint stage with the
+// global dt, no body cell in the block, no B0): the cell phase on the first
+// 256 threads, two cells each -- cell c and cell c + 256 (the same (i, j),
+// four layers apart in k) -- with the FP32 work packed over the pair and the
+// FP64 accumulation per cell.  The same arithmetic, value for value, as the
+// general cell phase (which runs the other cases, one cell per thread).
+// Returns this thread's largest CFL bound (last stage), 0 otherwise.
+// The pair's primitives Wc (the stage input) come from the tile, read by the
+// caller before the next block's copies overwrite it (first stage only: the
+// last stage reads them, for the Powell term, from memory).
+__device__ __forceinline__ void cells_mx_pair_w(const float* sT, int tid, float2 Wc[8]) {
+  if (tid >= NCELL / 2) return;
+  const int cs = tid ^ (((tid >> 5) & 1) << 2);  // the interior's swizzle (the pair shares it)
+#pragma unroll
+  for (int v = 0; v < NV; v++) Wc[v] = make_float2(sT[v * NCELL + cs], sT[v * NCELL + cs + NCELL / 2]);
+}
+__device__ __forceinline__ float cells_mx_pair(const StageArgs& a, const GridDev& G, const BlockDev& B, int blk,
+                                               const float2 Wc[8], const float* sF, int tid, float fx, float fy,
+                                               float fz, float idx0, float idx1, float idx2, float gamma) {
+  if (tid >= NCELL / 2) return 0.f;
+  const PhysDev& ph = a.ph;
+  const int c = tid, ci = c & 7, cj = (c >> 3) & 7, ck = c >> 6;  // ck 0..3; the pair's second cell: ck + 4
+  const int tx = (ck * NC + cj) * 9 + ci, ty = (ck * NC + ci) * 9 + cj, tz = (cj * NC + ci) * 9 + ck;
+  constexpr int DX = 4 * NC * 9, DZ = 4;   // face-index offsets of the second cell (x, y: +288; z: +4)
+  const float* Fx = sF;
+  const float* Fy = sF + 9 * NFACE;
+  const float* Fz = sF + 2 * 9 * NFACE;
+  const bool light = !a.last && !a.write_u_all;
+  const int64_t base = static_cast<int64_t>(blk) * (NV * NCELL) + c;
+  constexpr int H = NCELL / 2;  // the pair's second cell
+  const float2 fx2 = p_bc(fx), fy2 = p_bc(fy), fz2 = p_bc(fz);
+  // t[v] = sum_d (F_d,i+1/2 - F_d,i-1/2) / dx_d (v = 8: the face-averaged
+  // normal B1, i.e. div B); the residual is -t + S
+  float2 t[9];
+#pragma unroll
+  for (int v = 0; v < 9; v++) {
+    const float* px = Fx + v * NFACE + tx;
+    const float* py = Fy + v * NFACE + ty;
+    const float* pz = Fz + v * NFACE + tz;
+    const float2 x0 = make_float2(px[0], px[DX]), x1 = make_float2(px[1], px[DX + 1]);
+    const float2 y0 = make_float2(py[0], py[DX]), y1 = make_float2(py[1], py[DX + 1]);
+    const float2 z0 = make_float2(pz[0], pz[DZ]), z1 = make_float2(pz[1], pz[DZ + 1]);
+    float2 r = p_mul(p_fma(x0, p_bc(-1.f), x1), fx2);
+    r = p_fma(p_fma(y0, p_bc(-1.f), y1), fy2, r);
+    r = p_fma(p_fma(z0, p_bc(-1.f), z1), fz2, r);
+    t[v] = r;
+  }
+  // residual R = -t + S (Powell: S = -div B (0, B, u, u.B1))
+  float2 R[8];
+#pragma unroll
+  for (int v = 0; v < NV; v++) R[v] = p_mul(t[v], p_bc(-1.f));
+  if (ph.powell) {
+    // the stage input: in registers in the first stage; later stages read it
+    // from memory here (the tile already receives the next block)
+    float2 Wi[8];
+    if (light) {
+#pragma unroll
+      for (int v = 0; v < NV; v++) Wi[v] = Wc[v];
+    } else {
+      const float* wi = a.Win + static_cast<int64_t>(blk) * (NV * NCELL) + c;
+#pragma unroll
+      for (int v = 0; v < NV; v++) Wi[v] = make_float2(wi[v * NCELL], wi[v * NCELL + NCELL / 2]);
+    }
+    const float2 nd = p_mul(t[8], p_bc(-1.f));
+    const float2 ub1 = p_fma(Wi[3], Wi[6], p_fma(Wi[2], Wi[5], p_mul(Wi[1], Wi[4])));
+#pragma unroll
+    for (int e = 0; e < 3; e++) {
+      R[1 + e] = p_fma(nd, Wi[4 + e], R[1 + e]);
+      R[4 + e] = p_fma(nd, Wi[1 + e], R[4 + e]);
+    }
+    R[7] = p_fma(nd, ub1, R[7]);
+  }
+  const double cdt = a.beta * a.dt[B.grid];
+  if (light) {
+    // first midpoint stage: W* = W^n + the increment, in FP32
+    const float c32 = d2f_int(cdt);
+    float2 dU[8];
+#pragma unroll
+    for (int v = 0; v < NV; v++) dU[v] = p_mul(p_bc(c32), R[v]);
+    const float gm1f = ph.gm1f;
+    const float2 rf = p_add(Wc[0], dU[0]);
+    const float2 irf = make_float2(rcp_approx(rf.x), rcp_approx(rf.y));
+    const float2 udm = p_fma(Wc[3], dU[3], p_fma(Wc[2], dU[2], p_mul(Wc[1], dU[1])));
+    const float2 usq = p_fma(Wc[3], Wc[3], p_fma(Wc[2], Wc[2], p_mul(Wc[1], Wc[1])));
+    const float2 dmsq = p_fma(dU[3], dU[3], p_fma(dU[2], dU[2], p_mul(dU[1], dU[1])));
+    // dK = ((2 rho u.dm - rho drho |u|^2) + |dm|^2) / (2 rho')
+    const float2 k1 = p_mul(p_mul(p_bc(2.f), Wc[0]), udm);
+    const float2 k2 = p_mul(p_mul(Wc[0], dU[0]), usq);
+    const float2 dK = p_mul(p_mul(p_bc(0.5f), p_add(p_fma(k2, p_bc(-1.f), k1), dmsq)), irf);
+    const float2 bdb = p_fma(Wc[6], dU[6], p_fma(Wc[5], dU[5], p_mul(Wc[4], dU[4])));
+    const float2 db2 = p_fma(dU[6], dU[6], p_fma(dU[5], dU[5], p_mul(dU[4], dU[4])));
+    const float2 dM = p_fma(p_bc(0.5f), db2, bdb);
+    float2 Wl[8];
+    Wl[0] = rf;
+#pragma unroll
+    for (int e = 1; e < 4; e++) Wl[e] = p_fma(p_fma(Wc[e], p_mul(dU[0], p_bc(-1.f)), dU[e]), irf, Wc[e]);
+#pragma unroll
+    for (int e = 4; e < 7; e++) Wl[e] = p_add(Wc[e], dU[e]);
+    Wl[7] = p_fma(p_bc(gm1f), p_add(p_fma(dK, p_bc(-1.f), dU[7]), p_mul(dM, p_bc(-1.f))), Wc[7]);
+    bool badA = !(Wl[0].x > 0.f) || !(Wl[7].x > 0.f), badB = !(Wl[0].y > 0.f) || !(Wl[7].y > 0.f);
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      badA |= !finite_f(Wl[v].x);
+      badB |= !finite_f(Wl[v].y);
+    }
+    if (badA || badB) {
+      atomicOr(&a.err[0], ERR_NONPHYSICAL);
+      atomicMin(&a.err[1], blk);
+    }
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      a.Wout[base + v * NCELL] = Wl[v].x;
+      a.Wout[base + v * NCELL + H] = Wl[v].y;
+    }
+    return 0.f;
+  }
+  // last stage (or the FP64 state kept): U^{n+1} = U^n + c R in FP64, then
+  // the FP32 primitives (FP64 pressure where it cancels) and the CFL bound.
+  // Both cells' new states before any store (Uout may alias Ubase, so the
+  // base-state loads of the pair precede every store)
+  double U2[2][8];
+#pragma unroll
+  for (int v = 0; v < NV; v++) {
+    U2[0][v] = fma(cdt, f2d_int(R[v].x), a.Ubase[base + v * NCELL]);
+    U2[1][v] = fma(cdt, f2d_int(R[v].y), a.Ubase[base + H + v * NCELL]);
+  }
+  float2 Wn[8];
+  bool bad = false;
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    const int64_t b = base + h * H;
+    double* const Uo = U2[h];
+#pragma unroll
+    for (int v = 0; v < NV; v++) bad |= !finite_d(Uo[v]);
+    bad |= !positive_d(Uo[0]);
+    float w[8];
+    double p64;
+    prim_mixed(Uo, ph.gm1f, w, &p64);
+    bad |= !positive_d(p64);
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      a.Uout[b + v * NCELL] = Uo[v];
+      a.Wout[b + v * NCELL] = w[v];
+      if (h) Wn[v].y = w[v];
+      else Wn[v].x = w[v];
+    }
+  }
+  if (bad) {
+    atomicOr(&a.err[0], ERR_NONPHYSICAL);
+    atomicMin(&a.err[1], blk);
+  }
+  if (!a.last) return 0.f;
+  // CFL bound sum_d (|u_d| + c_f,d) / dx_d of both cells (fast speeds with
+  // the total field B1, no B0 here); cells that refluxing corrects afterwards
+  // are bounded by the correction kernel
+  const float2 rinv = make_float2(rcp_approx(Wn[0].x), rcp_approx(Wn[0].y));
+  const float2 a2 = p_mul(p_mul(p_bc(gamma), Wn[7]), rinv);
+  const float2 bsq = p_fma(Wn[6], Wn[6], p_fma(Wn[5], Wn[5], p_mul(Wn[4], Wn[4])));
+  const float2 b2 = p_mul(bsq, rinv);
+  const float2 s = p_add(a2, b2);
+  const float2 ss = p_mul(s, s);
+  float2 sacc = p_bc(0.f);
+#pragma unroll
+  for (int e = 0; e < 3; e++) {
+    const float2 bn2 = p_mul(p_mul(Wn[4 + e], Wn[4 + e]), rinv);
+    const float2 disc = p_fma(p_mul(a2, bn2), p_bc(-4.f), ss);
+    const float2 sq = make_float2(sqrt_approx(fmaxf(disc.x, 0.f)), sqrt_approx(fmaxf(disc.y, 0.f)));
+    const float2 q = p_mul(p_add(s, sq), p_bc(0.5f));
+    const float2 cf = make_float2(sqrt_approx(q.x), sqrt_approx(q.y));
+    const float2 au = make_float2(fabsf(Wn[1 + e].x), fabsf(Wn[1 + e].y));
+    sacc = p_fma(p_add(au, cf), p_bc(e == 0 ? idx0 : (e == 1 ? idx1 : idx2)), sacc);
+  }
+  float m = 0.f;
+  if (a.freg) {
+    // reflux-corrected cells (next to a refined face) are left out here
+    const bool rA = (ci == 0 && B.ftype[0] == FACE_FINER) || (ci == NC - 1 && B.ftype[1] == FACE_FINER) ||
+                    (cj == 0 && B.ftype[2] == FACE_FINER) || (cj == NC - 1 && B.ftype[3] == FACE_FINER) ||
+                    (ck == 0 && B.ftype[4] == FACE_FINER);
+    const bool rB = (ci == 0 && B.ftype[0] == FACE_FINER) || (ci == NC - 1 && B.ftype[1] == FACE_FINER) ||
+                    (cj == 0 && B.ftype[2] == FACE_FINER) || (cj == NC - 1 && B.ftype[3] == FACE_FINER) ||
+                    (ck + 4 == NC - 1 && B.ftype[5] == FACE_FINER);
+    m = fmaxf(rA ? 0.f : sacc.x, rB ? 0.f : sacc.y);
+  } else {
+    m = fmaxf(sacc.x, sacc.y);
+  }
+  return m;
+}
+
 // The fused stage (StageCfg::THREADS threads).  Per block: (1) interior by TMA, face-slab
 // ghosts by threads; (2) FP64 form: primitives in place; (3) faces of all
 // three directions at once on the first FACE_THREADS threads, two per grid
@@ -1411,6 +1626,13 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1)
   uint32_t parity = 0;
 
   const int nitems = (a.nblocks + a.blocks_per_item - 1) / a.blocks_per_item;
+  if constexpr (MX) {
+    // the staged tile's copies run one block ahead: those of each block are
+    // issued while the block before it is in its cell phase (which reads the
+    // face values and global memory only); the first block's here
+    const int b0 = blockIdx.x * a.blocks_per_item;
+    if (tid == 0 && b0 < a.nblocks) mx_issue_copies(a, a.blocks[b0], b0, reinterpret_cast<float*>(sT), &bar);
+  }
   for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
     const int b_end = min(a.nblocks, (item + 1) * a.blocks_per_item);
     for (int blk = item * a.blocks_per_item; blk < b_end; blk++) {
@@ -1420,7 +1642,7 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1)
 
       // 1. interior by TMA bulk copies (one per variable), ghosts by threads;
       //    the mixed plain kernel: the staged tile (tensor copies)
-      if constexpr (MX) mx_stage_tile(a, B, blk, reinterpret_cast<float*>(sT), &bar, tid, STAGE_THREADS);
+      if constexpr (MX) mx_fill_slabs(a, B, blk, reinterpret_cast<float*>(sT), tid, STAGE_THREADS);
       if (tid == 0 && !MX) {
         fence_proxy_async();
         // mixed form: the ghost slabs of faces at resolution changes come
@@ -1917,8 +2139,47 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1)
         if (tid < FACE_THREADS) faces(true);
       }
       __syncthreads();
+      // the staged tile's next block (its copies go out once this block's
+      // cell phase has read what it needs from the tile)
+      const int nblk = blk + 1 < b_end ? blk + 1 : (item + static_cast<int>(gridDim.x)) * a.blocks_per_item;
+      // issuer: a thread of a warp with no cell work in the packed cell phase
+      // (threads 256-383), so that its wait for the next block's table entry
+      // delays no cell's update
+      auto issue_next = [&](int issuer) {
+        if constexpr (MX) {
+          if (tid == issuer && nblk < a.nblocks)
+            mx_issue_copies(a, a.blocks[nblk], nblk, reinterpret_cast<float*>(sT), &bar);
+        }
+      };
       if (a.kind >= 3) continue;  // features / dumps only
       const bool fast = a.kind == 0 && !a.dtc && !B.body;
+      if constexpr (MX && !HAS_B0) {
+        if (fast) {
+          // the common case: two cells per thread, packed; the pair's
+          // primitives from the tile, then the tile is free for the next block
+          float2 Wc[8];
+          if (!a.last && !a.write_u_all) cells_mx_pair_w(reinterpret_cast<const float*>(sT), tid, Wc);
+          __syncthreads();
+          issue_next(NCELL / 2);
+          const float m = cells_mx_pair(a, G, B, blk, Wc, sF, tid, 0.5f * idx0, 0.5f * idx1, 0.5f * idx2, idx0,
+                                        idx1, idx2, gamma);
+          if (a.last) {
+            float mm = m;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mm = fmaxf(mm, __shfl_xor_sync(0xffffffffu, mm, o));
+            if ((tid & 31) == 0) sred[tid >> 5] = mm;
+            __syncthreads();
+            if (tid == 0) {
+              float mx = 0.f;
+              for (int w = 0; w < STAGE_THREADS / 32; w++) mx = fmaxf(mx, sred[w]);
+              const double md = f2d_int(mx);
+              if (md > 0.0) atomicMax(&a.smax_next[B.grid], static_cast<unsigned long long>(__double_as_longlong(md)));
+            }
+          }
+          __syncthreads();
+          continue;
+        }
+      }
       auto run_cells = [&](const bool commit) -> bool {
         return fast ? cells(commit, std::true_type{}) : cells(commit, std::false_type{});
       };
@@ -1936,6 +2197,7 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1)
       }
       run_cells(true);
       __syncthreads();
+      issue_next(0);
     }
   }
 }
@@ -2471,6 +2733,27 @@ __global__ void k_debug_wait_timeout(int32_t* err) {
 }
 cudaError_t launch_debug_wait_timeout(int32_t* err, cudaStream_t st) {
   k_debug_wait_timeout<<<1, 32, 0, st>>>(err);
+  return cudaGetLastError();
+}
+
+// FP64 FMA throughput probe (the FP64 form's roofline): every thread runs
+// `iters` rounds of eight independent FMA chains x = x * b + c, so that the
+// FP64 pipe's issue rate, not an FMA's latency, sets the time.  The chains'
+// sum is stored only in the (never taken) case that it equals `never`,
+// which keeps all of them live.
+__global__ void __launch_bounds__(256) k_fp64_fma_rate(double* out, int iters, double b, double c, double never) {
+  double x[8];
+#pragma unroll
+  for (int k = 0; k < 8; k++) x[k] = 1e-3 * threadIdx.x + k;
+  for (int i = 0; i < iters; i++) {
+#pragma unroll
+    for (int k = 0; k < 8; k++) x[k] = fma(x[k], b, c);
+  }
+  double s = ((x[0] + x[1]) + (x[2] + x[3])) + ((x[4] + x[5]) + (x[6] + x[7]));
+  if (s == never) out[0] = s;
+}
+cudaError_t launch_fp64_fma_rate(double* out, int ctas, int iters, cudaStream_t st) {
+  k_fp64_fma_rate<<<ctas, 256, 0, st>>>(out, iters, 0.9999999, 1e-7, -1.0);
   return cudaGetLastError();
 }
 
