@@ -116,7 +116,12 @@ typedef struct {
  *                 flux that Section 5 names; its contact-restoring term is not
  *                 given in the paper and not included).  HLL is not available
  *                 with `learned` (the correction is clipped by the Rusanov
- *                 dissipation): BATS_ERR_INVALID_ARG. */
+ *                 dissipation): BATS_ERR_INVALID_ARG.
+ *  learned_last_only  learned form: 1 = apply the correction in the last
+ *                 stage of each two-stage step only (the stage whose fluxes
+ *                 make U^{n+1}, and the one whose fine fluxes the training
+ *                 target is made of); the first stage then takes the plain
+ *                 Rusanov flux.  0 (the default) = both stages. */
 typedef struct {
   double gamma;
   int32_t limiter, rk, precision, b0;
@@ -126,6 +131,7 @@ typedef struct {
   int32_t local_dt;
   int32_t reflux;
   int32_t flux;
+  int32_t learned_last_only;
 } bats_physics;
 
 /* Create a solver for n_grids independent grids advanced together (batched

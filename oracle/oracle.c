@@ -84,6 +84,8 @@ typedef struct {
   int32_t local_dt;      /* 1 = local time stepping: each cell its own dt (steady-state runs) */
   int32_t reflux;        /* 1 = conservative flux correction at resolution changes */
   int32_t flux;          /* FLUX_RUSANOV, or FLUX_HLL (two-state HLL, Davis wave-speed bounds) */
+  int32_t learned_last_only; /* learned form: 1 = the correction in the last stage of a step only (the
+                              * stage whose fluxes enter U^{n+1}, where the training target is defined) */
 } or_desc;
 
 typedef struct {
@@ -1155,11 +1157,15 @@ int or_run_ex(const or_desc* d, double* U, int nsteps, double cfl, double fixed_
     /* with local time stepping the stage coefficients are beta * dt_i */
     const double f = lts ? 1.0 : dt;
     const int nst = d->rk == RK_EULER ? 1 : 2;
+    /* the first of two stages without the correction when it is applied in the last stage only */
+    or_desc first = *d;
+    if (d->learned_last_only && nst == 2) first.learned = 0;
     for (int st = 0; st < nst && !rc; st++) {
       if (d->rk == RK_EULER) rc = or_stage_ex(d, U, U, U2, 0, f, dtc, fb);
       else if (d->rk == RK_SSP2)
-        rc = st == 0 ? or_stage_ex(d, U, U, U1, 0, f, dtc, fb) : or_stage_ex(d, U1, U, U2, 1, f, dtc, fb);
-      else rc = st == 0 ? or_stage_ex(d, U, U, U1, 0, 0.5 * f, dtc, fb) : or_stage_ex(d, U1, U, U2, 0, f, dtc, fb);
+        rc = st == 0 ? or_stage_ex(&first, U, U, U1, 0, f, dtc, fb) : or_stage_ex(d, U1, U, U2, 1, f, dtc, fb);
+      else
+        rc = st == 0 ? or_stage_ex(&first, U, U, U1, 0, 0.5 * f, dtc, fb) : or_stage_ex(d, U1, U, U2, 0, f, dtc, fb);
       for (int b = 0; b < nb && !rc; b++) nfb += fb[b];
     }
     if (rc) break;

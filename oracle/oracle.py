@@ -65,6 +65,7 @@ class _Desc(ctypes.Structure):
         ("local_dt", ctypes.c_int32),
         ("reflux", ctypes.c_int32),
         ("flux", ctypes.c_int32),
+        ("learned_last_only", ctypes.c_int32),
     ]
 
 
@@ -150,6 +151,7 @@ class _Bound:
         d.local_dt = int(getattr(prob, "local_dt", 0) or 0)
         d.reflux = int(getattr(prob, "reflux", 0) or 0)
         d.flux = int(getattr(prob, "flux", 0) or 0)
+        d.learned_last_only = int(getattr(prob, "learned_last_only", 0) or 0)
         self.desc = d
         self.nb = d.n_leaves
 

@@ -64,6 +64,7 @@ class bats_physics(ctypes.Structure):
         ("local_dt", ctypes.c_int32),
         ("reflux", ctypes.c_int32),
         ("flux", ctypes.c_int32),
+        ("learned_last_only", ctypes.c_int32),
     ]
 
 
@@ -188,6 +189,7 @@ def physics_from(problem, precision=BATS_FP64, persistent=0, blocks_per_cta=1, c
     ph.local_dt = int(getattr(problem, "local_dt", 0) or 0)
     ph.reflux = int(getattr(problem, "reflux", 0) or 0)
     ph.flux = int(getattr(problem, "flux", 0) or 0)
+    ph.learned_last_only = int(getattr(problem, "learned_last_only", 0) or 0)
     return ph
 
 

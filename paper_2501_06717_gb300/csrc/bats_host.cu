@@ -104,6 +104,7 @@ struct bats {
   long long graph_launches = 0;
   // learned form
   bool learned_requested = false, learned = false;
+  bool learned_last_only = false;  // the correction in the last stage of a step only
   MlpDev mlp{};
   float* mlp_params = nullptr;
   uint32_t* Xb = nullptr;   // BF16 network inputs of every face
@@ -487,7 +488,7 @@ int launch_reflux(bats_t* h, const StageArgs& a) {
 // ghost pre-pass, made once): the network inputs of every face, the network,
 // and the stage with the correction.
 int launch_stage(bats_t* h, const StageArgs& a) {
-  if (!h->learned || a.kind >= 3) {
+  if (!h->learned || a.kind >= 3 || (h->learned_last_only && !a.last)) {
     int rc = launch_stage_one(h, a);
     return rc ? rc : launch_reflux(h, a);
   }
@@ -748,6 +749,7 @@ int bats_create(const bats_grid_desc* grids, int n_grids, const bats_physics* ph
     return fail(nullptr, BATS_ERR_INVALID_ARG, "bad physics enumeration");
   bats_t* h = new bats_t();
   h->learned_requested = phys->learned != 0;
+  h->learned_last_only = phys->learned_last_only != 0;
   h->stream = static_cast<cudaStream_t>(cuda_stream);
   h->ngrids = n_grids;
   h->grids_h.resize(n_grids);

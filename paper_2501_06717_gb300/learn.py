@@ -95,53 +95,79 @@ def _rotation(nbc):
     return np.stack([0 * d, 1 + d, 1 + d1, 1 + d2, 4 + d, 4 + d1, 4 + d2, 7 + 0 * d], axis=1)
 
 
-def targets(Fc, Ff1, Ff2, C):
+def fine_face_index(Cs):
+    """For every coarse face, the indices of its fine sub-faces r^2 levels of
+    refinement down (Cs: the children maps of each refinement, coarse first):
+    [nbc * 1728, 4^len(Cs)]."""
+    idx = _fine_face_index(Cs[0])
+    for C in Cs[1:]:
+        nxt = _fine_face_index(C)
+        idx = nxt[idx].reshape(idx.shape[0], -1)
+    return idx
+
+
+def targets(Fc, Ffs, Cs):
     """Normalised face-frame targets from the coarse dump Fc (n x 10) and the
-    two fine stage-2 dumps."""
-    idx = _fine_face_index(C)
-    tgt = 0.5 * (Ff1[idx, :8].mean(axis=1) + Ff2[idx, :8].mean(axis=1))
+    fine stage-2 dumps Ffs of the fine substeps (one per substep, the fine
+    grid len(Cs) refinements down): the mean over the substeps and the fine
+    sub-faces of each coarse face, minus the coarse Rusanov flux."""
+    idx = fine_face_index(Cs)
+    tgt = sum(F[idx, :8].mean(axis=1) for F in Ffs) / len(Ffs)
     dF = tgt - Fc[:, :8]
-    rot = _rotation(C.shape[0])
+    rot = _rotation(Cs[0].shape[0])
     dF = np.take_along_axis(dF, rot, axis=1)
     rho, c = Fc[:, 8], Fc[:, 9]
     sc = np.stack([rho * c] + [rho * c * c] * 3 + [np.sqrt(rho) * c * c] * 3 + [rho * c ** 3], axis=1)
     return dF / sc
 
 
-def make_pairs(variants, snapshots=(6, 14), cfl=0.8, keep=0.3, seed=0, precision=B.BATS_FP64):
-    """Training pairs from the blast variants (list of seeds).  Returns (X, Y),
-    float32, n x 40 and n x 8."""
+def make_pairs(variants, snapshots=(6, 14), cfl=0.8, keep=0.3, seed=0, precision=B.BATS_FP64, factor=2):
+    """Training pairs from the blast variants (list of seeds), with targets
+    from the plain solver at `factor` (2 or 4) times the coarse resolution
+    (snapshots are counted in fine steps of the 2x run and scaled with the
+    factor).  Returns (X, Y), float32, n x 40 and n x 8."""
+    if factor not in (2, 4):
+        raise ValueError("factor must be 2 or 4")
     rng = np.random.default_rng(seed)
     Xs, Ys = [], []
+    nsub = factor
     for vs in variants:
-        coarse, fine = blast_variant(vs, 1), blast_variant(vs, 2)
-        C = children_map(coarse, fine)
+        coarse, fine = blast_variant(vs, 1), blast_variant(vs, factor)
+        if factor == 2:
+            Cs = [children_map(coarse, fine)]
+        else:
+            mid = blast_variant(vs, 2)
+            Cs = [children_map(coarse, mid), children_map(mid, fine)]
         with B.Solver(fine, precision=precision) as sf, B.Solver(coarse, precision=precision) as sc:
             Uf = fine.U0
             sf.set_state(0, Uf)
             done = 0
-            for snap in snapshots:
+            for snap0 in snapshots:
+                snap = snap0 * factor // 2
                 if snap > done:
                     sf.step(snap - done, cfl)
                     done = snap
                 Uf = sf.get_state(0)
-                Uc = restrict_state(Uf, C)
+                Uc = Uf
+                for C in reversed(Cs):
+                    Uc = restrict_state(Uc, C)
                 sc.set_state(0, Uc)
                 dtc = sc.dt(0, cfl)
                 Xc, Fc = sc.face_data(0, stage_input=1, dt=dtc)
-                _, F1 = sf.face_data(0, stage_input=1, dt=0.5 * dtc, with_inputs=False)
-                sf.step_dt(1, 0.5 * dtc)
-                _, F2 = sf.face_data(0, stage_input=1, dt=0.5 * dtc, with_inputs=False)
-                sf.step_dt(1, 0.5 * dtc)
-                Y = targets(Fc, F1, F2, C)
+                Ffs = []
+                for _ in range(nsub):
+                    _, Ff = sf.face_data(0, stage_input=1, dt=dtc / nsub, with_inputs=False)
+                    Ffs.append(Ff)
+                    sf.step_dt(1, dtc / nsub)
+                Y = targets(Fc, Ffs, Cs)
                 sel = rng.uniform(size=Y.shape[0]) < keep
                 ok = np.isfinite(Y).all(axis=1) & np.isfinite(Xc).all(axis=1)
                 Xs.append(Xc[sel & ok])
                 Ys.append(Y[sel & ok].astype(np.float32))
-                # the fine run continues from the end of the two substeps
+                # the fine run continues from the end of the substeps
                 Uf = sf.get_state(0)
                 sf.set_state(0, Uf)
-                done += 2
+                done += nsub
     return np.concatenate(Xs).astype(np.float32), np.concatenate(Ys).astype(np.float32)
 
 
@@ -198,7 +224,7 @@ def evaluate(params, nsteps=16, cfl=0.8, precision=B.BATS_FP64, dt_safety=0.5):
     return err(U_plain), err(U_learn)
 
 
-def evaluate_4x(params, nsteps=16, cfl=0.8, precision=B.BATS_FP64, dt_safety=0.5):
+def evaluate_4x(params, nsteps=16, cfl=0.8, precision=B.BATS_FP64, dt_safety=0.5, last_only=0):
     """Errors against the plain run at 4x (every coarse leaf refined twice,
     7,680 blocks) restricted to the coarse grid, on the exact blast from the 4x
     initial state restricted to each resolution, fixed dt (dt_c, dt_c / 2,
@@ -213,7 +239,8 @@ def evaluate_4x(params, nsteps=16, cfl=0.8, precision=B.BATS_FP64, dt_safety=0.5
         dtc = dt_safety * s.dt(0, cfl)
         s.step_dt(nsteps, dtc)
         U_plain = s.get_state(0)
-    with B.Solver(coarse, precision=precision) as s:
+    coarse_l = W.Problem(**{**coarse.__dict__, "learned_last_only": int(last_only)})
+    with B.Solver(coarse_l, precision=precision) as s:
         s.set_mlp(params)
         s.set_state(0, U1_0)
         s.step_dt(nsteps, dtc)

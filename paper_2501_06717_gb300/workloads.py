@@ -64,6 +64,7 @@ class Problem:
     local_dt: int = 0
     reflux: int = 0
     flux: int = 0               # FLUX_RUSANOV or FLUX_HLL
+    learned_last_only: int = 0  # learned form: the correction in the last stage of a step only
 
     @property
     def nb(self):

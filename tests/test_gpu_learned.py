@@ -237,3 +237,29 @@ def test_learned_fallback_matches_oracle(B, precision, graph):
     print("fallback: max scaled error", err, "effect of the network", effect)
     assert effect > 1e-3
     assert err <= 3e-2 * effect
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_learned_last_stage_only_matches_oracle(B, precision):
+    """The correction applied in the last stage of each step only (the stage
+    whose fluxes make U^{n+1}): GPU against the oracle with the same option,
+    to BF16 accuracy of the network's effect, in both precisions."""
+    q = W.blast()
+    P = _net(8, scale=0.15)
+    prec = B.BATS_FP64 if precision == "fp64" else B.BATS_MIXED
+    q.learned_last_only = 1
+    with B.Solver(q, precision=prec) as s:
+        s.set_mlp(P)
+        s.set_state(0, q.U0)
+        s.step_dt(2, 2e-3)
+        Ug = s.get_state(0)
+    ql = W.Problem(**{**q.__dict__, "learned": 1, "mlp": P.astype(np.float64)})
+    Uo, _, _ = O.run(ql, q.U0, 2, dt=2e-3)
+    q.learned_last_only = 0
+    U0, _, _ = O.run(q, q.U0, 2, dt=2e-3)
+    scale = np.abs(Uo).reshape(8, -1).max(1)
+    err = (np.abs(Ug - Uo).reshape(8, -1).max(1) / scale).max()
+    effect = (np.abs(Uo - U0).reshape(8, -1).max(1) / scale).max()
+    print("learned, last stage only:", precision, "max scaled error", err, "effect", effect)
+    assert effect > 1e-4
+    assert err <= (3e-2 if precision == "fp64" else 5e-2) * effect

@@ -191,3 +191,26 @@ def test_learned_fallback_rescues_a_stage_the_plain_flux_keeps_physical():
     qn.no_fallback = 1
     Un, _, _ = O.run(qn, q.U0, 1, cfl=0.8)
     assert (~physical_per_block(q.gamma, Un)).sum() == 8
+
+
+def test_learned_last_stage_only_composes_a_plain_first_stage():
+    """With the correction in the last stage only, a midpoint step is the
+    plain first stage followed by the learned second stage (bitwise), and it
+    differs from the step with the correction in both stages."""
+    q = W.blast()
+    rng = np.random.default_rng(5)
+    P = rng.normal(0, 0.1, size=O.MLP_NPARAM)
+    both = W.Problem(**{**q.__dict__, "learned": 1, "mlp": P})
+    last = W.Problem(**{**q.__dict__, "learned": 1, "mlp": P, "learned_last_only": 1})
+    U = q.U0.reshape(8, q.nb, 8, 8, 8)
+    dt = 2e-3
+    Us = O.stage(q, U, U, 0, 0.5 * dt)          # plain stage 1
+    U1 = O.stage(both, Us, U, 0, dt)            # learned stage 2
+    Ul, _, _ = O.run(last, U, 1, dt=dt)
+    assert np.array_equal(Ul, U1)
+    Ub, _, _ = O.run(both, U, 1, dt=dt)
+    assert np.abs(Ub - Ul).max() > 1e-10
+    # one-stage scheme: the only stage is the last, so the option changes nothing
+    qe = W.Problem(**{**q.__dict__, "rk": W.RK_EULER, "limiter": W.LIM_NONE, "learned": 1, "mlp": P})
+    qel = W.Problem(**{**qe.__dict__, "learned_last_only": 1})
+    assert np.array_equal(O.run(qe, U, 1, dt=dt)[0], O.run(qel, U, 1, dt=dt)[0])
