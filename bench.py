@@ -219,6 +219,26 @@ def learned_form_summary(stream, steps=32):
                     "learned_1x_both_stages": timed(coarse, P, steps, dtc, prec),
                     "plain_1x": timed(coarse, None, steps, dtc, prec),
                     "plain_2x_two_fine_steps": timed(fine, None, 2 * steps, 0.5 * dtc, prec)}
+    # the same network on a GPU-filling grid: the blast on 16^3 roots (6,056
+    # blocks at 1x, 48,448 at 2x); timing only (the network was trained on the
+    # 4^3-root blast; its inputs are scale-free)
+    big1 = W.blast(roots_per_axis=16)
+    big2 = W.blast(roots_per_axis=16, resolution=2)
+    big1_last = W.Problem(**{**big1.__dict__, "learned_last_only": 1})
+    with bats.Solver(big1) as s:
+        s.set_state(0, big1.U0)
+        dtb = 0.5 * s.dt(0, 0.8)
+    nb = max(4, steps // 4)
+    big = {"blocks_1x": big1.nb, "blocks_2x": big2.nb}
+    for name, prec in (("fp64", bats.BATS_FP64), ("mixed", bats.BATS_MIXED)):
+        r = {"learned_1x": timed(big1_last, P, nb, dtb, prec) * steps / nb,
+             "learned_1x_both_stages": timed(big1, P, nb, dtb, prec) * steps / nb,
+             "plain_1x": timed(big1, None, nb, dtb, prec) * steps / nb,
+             "plain_2x_two_fine_steps": timed(big2, None, 2 * nb, 0.5 * dtb, prec) * steps / nb}
+        big[name] = {"ms_per_coarse_step": r,
+                     "cell_updates_per_s": {"learned_1x": big1.ncells / (r["learned_1x"] * 1e-3),
+                                            "plain_1x": big1.ncells / (r["plain_1x"] * 1e-3),
+                                            "plain_2x": 2 * big2.ncells / (r["plain_2x_two_fine_steps"] * 1e-3)}}
     return {"workload": "spherical blast: 120 blocks (1x) with the trained network vs plain 1x and plain 2x "
                         "(960 blocks), fixed dt, CUDA graph",
             "pairs": int(X.shape[0]), "train_s": t_train, "loss_first_last_epoch": [hist[0], hist[-1]],
@@ -228,6 +248,7 @@ def learned_form_summary(stream, steps=32):
                                             "learned_1x": e4_last["learned_1x"]},
             "learned_form": "correction in the last stage of each step (learned_last_only)",
             "ms_per_coarse_step": ms,
+            "gpu_filling_blast_16cube_roots": big,
             "cell_updates_per_s_learned_1x": {k: coarse.ncells / (v["learned_1x"] * 1e-3) for k, v in ms.items()}}
 
 

@@ -264,6 +264,13 @@ int bats_get_fallbacks(bats_t* h, long long* n);
  * the compiler's conversions.  Allocates and frees its own device buffers. */
 int bats_debug_check_conversions(const float* f, const double* d, int n, double* f2d_out, float* d2f_out);
 
+/* Self-check of the network's activation (the learned correction's GELU,
+ * tanh form, Hendrycks & Gimpel): y[i] = the kernels' GELU of x[i] as they
+ * compute it for the hidden activations -- two values at a time, the tanh by
+ * one tanh.approx.bf16x2, the result rounded to BF16.  n host values;
+ * allocates and frees its own device buffers. */
+int bats_debug_gelu(const float* x, int n, float* y);
+
 /* ---- learned flux correction (a small MLP on tensor cores) -------------
  * Network: 40 inputs -> 64 -> 64 -> 8 outputs, tanh-form GELU after the two
  * hidden layers, BF16 weights and activations with FP32 accumulation.

@@ -114,6 +114,7 @@ def lib():
     L.bats_get_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     L.bats_get_fallbacks.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     L.bats_debug_check_conversions.argtypes = [vp, vp, ctypes.c_int, vp, vp]
+    L.bats_debug_gelu.argtypes = [vp, ctypes.c_int, vp]
     L.bats_set_mlp.argtypes = [vp, vp]
     L.bats_debug_face_data.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, vp, vp, ctypes.c_size_t]
     L.bats_mlp_create.argtypes = [vp, ctypes.c_uint64, vp, ctypes.POINTER(vp)]
@@ -339,6 +340,15 @@ def bats_debug_check_conversions(f, d):
     if rc != BATS_OK:
         raise BatsError(rc, "conversion check failed")
     return o1, o2
+
+
+def bats_debug_gelu(x):
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    y = np.zeros_like(x)
+    rc = lib().bats_debug_gelu(x.ctypes.data, int(x.size), y.ctypes.data)
+    if rc != BATS_OK:
+        raise BatsError(rc, "GELU check failed")
+    return y
 
 
 BATS_MLP_NPARAM = 7304

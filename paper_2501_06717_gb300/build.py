@@ -33,7 +33,8 @@ def _nvcc():
 def _stale(obj, src):
     if not os.path.exists(obj):
         return True
-    deps = [src, os.path.join(CSRC, "bats_internal.h"), os.path.join(ROOT, "include", "bats.h")]
+    deps = [src, os.path.join(CSRC, "bats_internal.h"), os.path.join(CSRC, "bats_tc.h"),
+            os.path.join(ROOT, "include", "bats.h")]
     return any(os.path.getmtime(d) > os.path.getmtime(obj) for d in deps)
 
 

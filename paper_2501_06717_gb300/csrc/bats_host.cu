@@ -443,7 +443,9 @@ StageArgs base_args(bats_t* h) {
 
 // make_ghosts = false: the ghost slabs in gbuf already hold this stage input's
 // values (the learned form's second launch of a stage reads the same input).
-int launch_stage_one(bats_t* h, const StageArgs& a0, bool make_ghosts = true) {
+// one_per_sm: a persistent launch of one CTA per SM (the mixed learned
+// kernel, whose network weights and tensor memory each CTA sets up once).
+int launch_stage_one(bats_t* h, const StageArgs& a0, bool make_ghosts = true, bool one_per_sm = false) {
   bool mixed = h->ph.precision == BATS_MIXED;
   StageArgs a = a0;
   if (mixed) {
@@ -464,7 +466,9 @@ int launch_stage_one(bats_t* h, const StageArgs& a0, bool make_ghosts = true) {
   }
   int nitems = (a.nblocks + a.blocks_per_item - 1) / a.blocks_per_item;
   int grid = nitems;
-  if (h->persistent) {
+  if (one_per_sm) {
+    grid = std::min(nitems, h->num_sms);
+  } else if (h->persistent) {
     int per_sm = h->ctas_per_sm > 0 ? std::min(h->ctas_per_sm, h->occ[mixed]) : h->occ[mixed];
     grid = std::min(nitems, h->num_sms * std::max(1, per_sm));
   }
@@ -484,13 +488,22 @@ int launch_reflux(bats_t* h, const StageArgs& a) {
   return BATS_OK;
 }
 
-// One stage; with the learned form, three launches (after the mixed form's
-// ghost pre-pass, made once): the network inputs of every face, the network,
-// and the stage with the correction.
+// One stage; with the learned form in FP64, three launches: the network
+// inputs of every face, the network, and the stage with the correction; in
+// the mixed form one (after the ghost pre-pass), the network run inside the
+// stage kernel on the tensor cores.
 int launch_stage(bats_t* h, const StageArgs& a) {
   if (!h->learned || a.kind >= 3 || (h->learned_last_only && !a.last)) {
     int rc = launch_stage_one(h, a);
     return rc ? rc : launch_reflux(h, a);
+  }
+  if (h->ph.precision == BATS_MIXED) {
+    // mixed form: one launch, the network fused into the stage kernel
+    StageArgs u = a;
+    u.learned = 1;
+    u.mlp = h->mlp;
+    u.Y = nullptr;
+    return launch_stage_one(h, u, true, true);
   }
   StageArgs f = a;
   f.kind = 3;

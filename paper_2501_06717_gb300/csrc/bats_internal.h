@@ -141,6 +141,7 @@ struct StageArgs {
   // 1 = same-level face slabs by tensor copies, 0 = gathered by the threads
   int32_t stage_tma;
   int32_t gbuf_mx;        // ghost-slab buffer in the mixed tile's slab layouts (1) or the generic one (0)
+  MlpDev mlp;             // mixed learned stage: the network, run fused in the stage kernel
   CUtensorMap tm[4];
 };
 

@@ -28,6 +28,7 @@
 
 #include "bats.h"
 #include "bats_internal.h"
+#include "bats_tc.h"
 
 namespace batsk {
 
@@ -37,27 +38,6 @@ __device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], uint32
       "{%0,%1,%2,%3};\n"
       : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-  return *reinterpret_cast<uint32_t*>(&v);
-}
-__device__ __forceinline__ float bf16_lo(uint32_t u) { return __uint_as_float(u << 16); }
-__device__ __forceinline__ float bf16_hi(uint32_t u) { return __uint_as_float(u & 0xffff0000u); }
-__device__ __forceinline__ float tanh_approx(float x) {
-  float r;
-  asm("tanh.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
-// GELU, tanh form, and its derivative.
-__device__ __forceinline__ float gelu_f(float x) {
-  const float k = 0.7978845608028654f;
-  return 0.5f * x * (1.0f + tanh_approx(k * (x + 0.044715f * x * x * x)));
-}
-__device__ __forceinline__ float gelu_grad_f(float x) {
-  const float k = 0.7978845608028654f;
-  float t = tanh_approx(k * (x + 0.044715f * x * x * x));
-  return 0.5f * (1.0f + t) + 0.5f * x * (1.0f - t * t) * k * (1.0f + 3.0f * 0.044715f * x * x);
 }
 
 // Shared-memory weight layout (32-bit words = BF16 pairs), rows padded so the
@@ -115,8 +95,8 @@ __device__ __forceinline__ void mlp_tile_forward(const MlpSmem& s, const uint32_
       for (int r = 0; r < 4; r++) z1[nt][r] = acc[nt][r];
     }
     const int kt = nt >> 1, hi = nt & 1;
-    a2[kt][hi * 2 + 0] = pack_bf16(gelu_f(acc[nt][0]), gelu_f(acc[nt][1]));
-    a2[kt][hi * 2 + 1] = pack_bf16(gelu_f(acc[nt][2]), gelu_f(acc[nt][3]));
+    a2[kt][hi * 2 + 0] = gelu2_pack(acc[nt][0], acc[nt][1]);
+    a2[kt][hi * 2 + 1] = gelu2_pack(acc[nt][2], acc[nt][3]);
   }
 #pragma unroll
   for (int nt = 0; nt < 8; nt++) {
@@ -133,8 +113,8 @@ __device__ __forceinline__ void mlp_tile_forward(const MlpSmem& s, const uint32_
       for (int r = 0; r < 4; r++) z2[nt][r] = acc[nt][r];
     }
     const int kt = nt >> 1, hi = nt & 1;
-    a3[kt][hi * 2 + 0] = pack_bf16(gelu_f(acc[nt][0]), gelu_f(acc[nt][1]));
-    a3[kt][hi * 2 + 1] = pack_bf16(gelu_f(acc[nt][2]), gelu_f(acc[nt][3]));
+    a3[kt][hi * 2 + 0] = gelu2_pack(acc[nt][0], acc[nt][1]);
+    a3[kt][hi * 2 + 1] = gelu2_pack(acc[nt][2], acc[nt][3]);
   }
   const float bl = s.b3[2 * t], bh = s.b3[2 * t + 1];
   y[0] = bl; y[1] = bh; y[2] = bl; y[3] = bh;
@@ -142,98 +122,7 @@ __device__ __forceinline__ void mlp_tile_forward(const MlpSmem& s, const uint32_
   for (int kt = 0; kt < 4; kt++) mma_bf16(y, a3[kt], s.w3[g * W3S + kt * 8 + t], s.w3[g * W3S + kt * 8 + 4 + t]);
 }
 
-// ---------------------------------------------------------------------------
-// Inference on tcgen05.  Operands in shared memory use the no-swizzle K-major
-// canonical layout: "core matrices" of 8 rows x 16 bytes (8 BF16 along K)
-// stored as 128 contiguous bytes; core matrices adjacent along K are LBO =
-// 128 bytes apart, those adjacent along M (or N) SBO = 16 K bytes apart.
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-// byte offset of the 16-byte chunk (row r, K chunk kc) in a canonical tile
-__device__ __forceinline__ uint32_t cm_off(int r, int kc, uint32_t sbo) {
-  return static_cast<uint32_t>(r >> 3) * sbo + static_cast<uint32_t>(kc) * 128u + static_cast<uint32_t>(r & 7) * 16u;
-}
-// Shared-memory matrix descriptor: start address >> 4 (bits 0-13), LBO >> 4
-// (16-29), SBO >> 4 (32-45), the fixed value 1 in bits 46-48, base offset 0,
-// relative LBO, no swizzle (bits 61-63 = 0).
-__device__ __forceinline__ uint64_t umma_sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  return static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4) | (static_cast<uint64_t>(lbo >> 4) << 16) |
-         (static_cast<uint64_t>(sbo >> 4) << 32) | (1ull << 46);
-}
-// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16
-// A and B (bits 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 in
-// bits 17-22, M >> 4 in bits 24-28.
-__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
-         (static_cast<uint32_t>(M >> 4) << 24);
-}
-// D[tmem] (+)= A B^T for one K = 16 slice; accum = 0 overwrites D.
-__device__ __forceinline__ void umma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                          uint32_t accum) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
-      : "memory");
-}
-// The mbarrier completes one phase once every tcgen05.mma this thread issued
-// before has finished.
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void proxy_fence_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-// 16 consecutive FP32 columns of this thread's tensor-memory lane (the wait
-// for the load sits in the same statement, so no use of the registers can be
-// scheduled ahead of it).
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-      "tcgen05.wait::ld.sync.aligned;\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr)
-      : "memory");
-#pragma unroll
-  for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
-}
-__device__ __forceinline__ void mbar_init_tc(uint64_t* bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait_tc(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Wait for an mbarrier phase for at most ~1 s of wall time; on expiry record
-// ERR_TIMEOUT and return false.
-__device__ __noinline__ bool mbar_wait_bounded_tc(uint64_t* bar, uint32_t parity, int32_t* err) {
-  if (mbar_try_wait_tc(bar, parity)) return true;
-  uint64_t t0, t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-  while (true) {
-    if (mbar_try_wait_tc(bar, parity)) return true;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    if (t - t0 > 1000000000ull) {
-      atomicOr(err, ERR_TIMEOUT);
-      return false;
-    }
-  }
-}
-
 constexpr int TC_TILE = 128;             // rows per tile (MMA M = tensor-memory lanes)
-constexpr uint32_t SBO_K48 = 768;        // 16 bytes x K = 48
-constexpr uint32_t SBO_K64 = 1024;       // 16 bytes x K = 64
 constexpr int TC_TMEM_COLS = 64;         // one FP32 accumulator of N = 64 (reused by all three layers)
 struct TcSmem {
   alignas(128) uint8_t x[TC_TILE * 96];  // X tile, K = 48
@@ -258,10 +147,10 @@ __device__ __forceinline__ void tc_hidden_cols(uint32_t taddr, const float* bias
       uint4 o;
       const float* b = bias + c0 + 16 * q + 8 * c;
       const float* z = v + 8 * c;
-      o.x = pack_bf16(gelu_f(z[0] + b[0]), gelu_f(z[1] + b[1]));
-      o.y = pack_bf16(gelu_f(z[2] + b[2]), gelu_f(z[3] + b[3]));
-      o.z = pack_bf16(gelu_f(z[4] + b[4]), gelu_f(z[5] + b[5]));
-      o.w = pack_bf16(gelu_f(z[6] + b[6]), gelu_f(z[7] + b[7]));
+      o.x = gelu2_pack(z[0] + b[0], z[1] + b[1]);
+      o.y = gelu2_pack(z[2] + b[2], z[3] + b[3]);
+      o.z = gelu2_pack(z[4] + b[4], z[5] + b[5]);
+      o.w = gelu2_pack(z[6] + b[6], z[7] + b[7]);
       *reinterpret_cast<uint4*>(h + cm_off(row, c0 / 8 + 2 * q + c, SBO_K64)) = o;
     }
   }
@@ -302,7 +191,7 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_mlp_infer(const uint32_t* __r
   }
   if (tid < 8) s.b3[tid] = m.b3[tid];
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s.tmem)),
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_saddr(&s.tmem)),
                  "r"(TC_TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -314,8 +203,8 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_mlp_infer(const uint32_t* __r
   tc_fence_after();
   const uint32_t tmem = s.tmem;
   const uint32_t tlanes = tmem + (static_cast<uint32_t>(32 * lg) << 16);  // this warp's 32 lanes
-  const uint32_t xs = smem_u32(s.x), hs = smem_u32(s.h);
-  const uint32_t w1s = smem_u32(s.w1), w2s = smem_u32(s.w2), w3s = smem_u32(s.w3);
+  const uint32_t xs = tc_saddr(s.x), hs = tc_saddr(s.h);
+  const uint32_t w1s = tc_saddr(s.w1), w2s = tc_saddr(s.w2), w3s = tc_saddr(s.w3);
   constexpr uint32_t ID64 = umma_idesc_bf16(TC_TILE, 64), ID16 = umma_idesc_bf16(TC_TILE, 16);
   uint32_t phase = 0;
   bool failed = false;
@@ -823,6 +712,32 @@ int bats_mlp_get_params(bats_mlp_t* m, float* params) {
   cudaError_t e = cudaMemcpyAsync(params, m->P, sizeof(float) * MLP_NPARAM,
                                   dev_ptr(params) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, m->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  return e == cudaSuccess ? BATS_OK : BATS_ERR_CUDA;
+}
+
+// GELU self-check: y[i] = the kernels' packed-pair GELU (BF16 results) of x[i].
+__global__ void k_debug_gelu(const float* x, int n, float* y) {
+  const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  if (i >= n) return;
+  const float x1 = i + 1 < n ? x[i + 1] : 0.f;
+  const uint32_t r = gelu2_pack(x[i], x1);
+  y[i] = bf16_lo(r);
+  if (i + 1 < n) y[i + 1] = bf16_hi(r);
+}
+
+int bats_debug_gelu(const float* x, int n, float* y) {
+  if (!x || !y || n <= 0) return BATS_ERR_INVALID_ARG;
+  float *xd = nullptr, *yd = nullptr;
+  cudaError_t e = cudaMalloc(&xd, n * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&yd, n * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemcpy(xd, x, n * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    k_debug_gelu<<<(n / 2 + 256) / 256, 256>>>(xd, n, yd);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(y, yd, n * sizeof(float), cudaMemcpyDeviceToHost);
+  cudaFree(xd);
+  cudaFree(yd);
   return e == cudaSuccess ? BATS_OK : BATS_ERR_CUDA;
 }
 

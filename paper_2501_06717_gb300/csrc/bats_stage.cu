@@ -16,6 +16,7 @@
 #include <type_traits>
 
 #include "bats_internal.h"
+#include "bats_tc.h"
 
 namespace batsk {
 
@@ -1567,6 +1568,147 @@ __device__ __forceinline__ float cells_mx_pair(const StageArgs& a, const GridDev
   return m;
 }
 
+constexpr int TC_TILE_F = 128;  // rows per tensor-core tile (MMA M = tensor-memory lanes)
+// ---------------------------------------------------------------------------
+// Learned correction fused into the mixed form's stage kernel.  At every face
+// step of the face phase the CTA's 384 threads hold 384 faces (one each):
+// thread t's face is row t % 128 of tile t / 128, the tensor-memory lane its
+// warp may read.  The three layers run on the tensor cores (tcgen05.mma,
+// M = 128, K = 16 per instruction, BF16 operands from shared memory in the
+// no-swizzle K-major canonical layout, FP32 accumulators in tensor memory,
+// 64 columns per tile), each thread turning its own row's accumulator into
+// the next layer's BF16 operand (bias, GELU) and, after the last layer, into
+// its own face's correction.
+
+struct LrnSmem {
+  alignas(128) uint8_t x[3][TC_TILE_F * 96];   // inputs, K = 48 (40 features, 8 zeros)
+  alignas(128) uint8_t h[3][TC_TILE_F * 128];  // hidden activations, K = 64
+  alignas(128) uint8_t w1[64 * 96];             // B of layer 1: N = 64, K = 48
+  alignas(128) uint8_t w2[64 * 128];            // B of layer 2: N = 64, K = 64
+  alignas(128) uint8_t w3[16 * 128];            // B of layer 3: N = 16 (8 outputs, 8 zero rows), K = 64
+  float b1[64], b2[64], b3[8];
+  uint64_t bar;                                 // MMA completion
+  uint32_t tmem;
+};
+constexpr int LRN_TMEM_COLS = 256;  // 3 tiles x 64 columns, rounded up to a power of two
+// the mixed learned kernel: the generic tile and face values, then the
+// fused network's operands and weights (128-byte aligned)
+constexpr size_t kSmemLx = (sizeof(float) * (NV * NTILE + 3 * 9 * NFACE) + 127) / 128 * 128 + sizeof(LrnSmem) + 128;
+
+// Weights and biases into shared memory (all threads), tensor memory and
+// the MMA barrier (warp 0, thread 0).
+__device__ __forceinline__ void lrn_setup(LrnSmem& s, const MlpDev& m, int tid, int nthr) {
+  for (int e = tid; e < 64 * 6; e += nthr) {
+    const int r = e / 6, kc = e % 6;
+    *reinterpret_cast<uint4*>(s.w1 + cm_off(r, kc, SBO_K48)) = *reinterpret_cast<const uint4*>(m.w1 + r * 24 + kc * 4);
+  }
+  for (int e = tid; e < 64 * 8; e += nthr) {
+    const int r = e / 8, kc = e % 8;
+    *reinterpret_cast<uint4*>(s.w2 + cm_off(r, kc, SBO_K64)) = *reinterpret_cast<const uint4*>(m.w2 + r * 32 + kc * 4);
+  }
+  for (int e = tid; e < 16 * 8; e += nthr) {
+    const int r = e / 8, kc = e % 8;
+    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+    *reinterpret_cast<uint4*>(s.w3 + cm_off(r, kc, SBO_K64)) =
+        r < 8 ? *reinterpret_cast<const uint4*>(m.w3 + r * 32 + kc * 4) : z;
+  }
+  if (tid < 64) {
+    s.b1[tid] = m.b1[tid];
+    s.b2[tid] = m.b2[tid];
+  }
+  if (tid < 8) s.b3[tid] = m.b3[tid];
+  if (tid < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_saddr(&s.tmem)),
+                 "r"(LRN_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) mbar_init_tc(&s.bar);
+}
+__device__ __forceinline__ void lrn_teardown(LrnSmem& s, int tid, bool failed, uint32_t phase, int32_t* err) {
+  // an MMA may still run after a timed-out wait: wait for it once more
+  if (failed && tid == 0) mbar_wait_bounded_tc(&s.bar, phase, err);
+  tc_fence_before();
+  __syncthreads();
+  if (tid < 32) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s.tmem), "r"(LRN_TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// Layer `layer` (0, 1, 2) of all three tiles: thread 0 issues the MMAs and
+// commits them; every thread waits (bounded).  false when the wait ran out.
+__device__ __forceinline__ bool lrn_layer(LrnSmem& s, int layer, int tid, uint32_t& phase, int32_t* err) {
+  proxy_fence_smem();
+  tc_fence_before();
+  __syncthreads();
+  if (tid == 0) {
+    tc_fence_after();
+    const uint32_t ID64 = umma_idesc_bf16(TC_TILE_F, 64), ID16 = umma_idesc_bf16(TC_TILE_F, 16);
+#pragma unroll
+    for (int t = 0; t < 3; t++) {
+      const uint32_t d = s.tmem + 64 * t;
+      if (layer == 0) {
+        const uint32_t xs = tc_saddr(s.x[t]), ws = tc_saddr(s.w1);
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+          umma_bf16(d, umma_sdesc(xs + 256 * k, 128, SBO_K48), umma_sdesc(ws + 256 * k, 128, SBO_K48), ID64, k > 0);
+      } else {
+        const uint32_t hs = tc_saddr(s.h[t]), ws = tc_saddr(layer == 1 ? s.w2 : s.w3);
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+          umma_bf16(d, umma_sdesc(hs + 256 * k, 128, SBO_K64), umma_sdesc(ws + 256 * k, 128, SBO_K64),
+                    layer == 1 ? ID64 : ID16, k > 0);
+      }
+    }
+    umma_commit(&s.bar);
+  }
+  const bool got = mbar_wait_bounded_tc(&s.bar, phase, err);
+  if (__syncthreads_or(!got)) return false;  // phase kept: the teardown waits on it once more
+  phase ^= 1u;
+  tc_fence_after();
+  return true;
+}
+
+// The network for this thread's face (row tid % 128 of tile tid / 128):
+// xrow its 48 BF16 inputs (6 chunks of 8), y its 8 outputs.  false (for
+// every thread) when a wait ran out.
+__device__ __forceinline__ bool lrn_network(LrnSmem& s, const uint4 xrow[6], float y[8], int tid, uint32_t& phase,
+                                            int32_t* err) {
+  const int tile = tid >> 7, row = tid & 127;
+  const uint32_t tl = s.tmem + (static_cast<uint32_t>(32 * ((tid >> 5) & 3)) << 16) + 64 * tile;
+#pragma unroll
+  for (int kc = 0; kc < 6; kc++) *reinterpret_cast<uint4*>(s.x[tile] + cm_off(row, kc, SBO_K48)) = xrow[kc];
+#pragma unroll 1
+  for (int layer = 0; layer < 2; layer++) {
+    if (!lrn_layer(s, layer, tid, phase, err)) return false;
+    const float* bias = layer == 0 ? s.b1 : s.b2;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      float v[16];
+      tmem_ld16(tl + 16 * q, v);
+#pragma unroll
+      for (int c = 0; c < 2; c++) {
+        const float* b = bias + 16 * q + 8 * c;
+        const float* z = v + 8 * c;
+        uint4 o;
+        o.x = gelu2_pack(z[0] + b[0], z[1] + b[1]);
+        o.y = gelu2_pack(z[2] + b[2], z[3] + b[3]);
+        o.z = gelu2_pack(z[4] + b[4], z[5] + b[5]);
+        o.w = gelu2_pack(z[6] + b[6], z[7] + b[7]);
+        *reinterpret_cast<uint4*>(s.h[tile] + cm_off(row, 2 * q + c, SBO_K64)) = o;
+      }
+    }
+  }
+  if (!lrn_layer(s, 2, tid, phase, err)) return false;
+  float v[16];
+  tmem_ld16(tl, v);
+#pragma unroll
+  for (int k = 0; k < 8; k++) y[k] = v[k] + s.b3[k];
+  return true;
+}
+
 // The fused stage (StageCfg::THREADS threads).  Per block: (1) interior by TMA, face-slab
 // ghosts by threads; (2) FP64 form: primitives in place; (3) faces of all
 // three directions at once on the first FACE_THREADS threads, two per grid
@@ -1575,7 +1717,7 @@ __device__ __forceinline__ float cells_mx_pair(const StageArgs& a, const GridDev
 // flux differences x, y, z, the sources, the update and (last stage) the CFL
 // bound.
 template <bool MIXED, int LIM, bool HAS_B0, bool LRN, int FLX>
-__global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1)
+__global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, (MIXED && !LRN) ? 2 : 1)
     k_stage(const __grid_constant__ StageArgs a) {
   using R = typename StageCfg<MIXED>::R;
   constexpr int STAGE_THREADS = StageCfg<MIXED>::THREADS;
@@ -1591,6 +1733,16 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1)
     sT = reinterpret_cast<R*>(smem_raw);
   }
   R* sF = sT + (MX ? MX_TILE : NV * NTILE);      // [3][9][576] face values
+  // mixed learned kernel: the network runs fused, on the tensor cores
+  constexpr bool LX = MIXED && LRN;
+  LrnSmem* ls = nullptr;
+  if constexpr (LX) {
+    const uintptr_t e = reinterpret_cast<uintptr_t>(sF + 3 * StageCfg<MIXED>::NFC * NFACE);
+    ls = reinterpret_cast<LrnSmem*>((e + 127) & ~uintptr_t(127));
+  }
+  const bool fused = LX && a.learned && a.kind < 3;
+  uint32_t mphase = 0;
+  bool mfail = false;  // a tensor-core wait ran out (uniform over the CTA)
   __shared__ uint64_t bar;
   __shared__ R sred[STAGE_THREADS / 32];
 
@@ -1622,7 +1774,17 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1)
   R* const fcol = sF + fd * NFC * NFACE;
 
   if (tid == 0) mbar_init(&bar, 1);
+  if constexpr (LX) {
+    if (fused) {
+      lrn_setup(*ls, a.mlp, tid, STAGE_THREADS);
+      proxy_fence_smem();
+      tc_fence_before();
+    }
+  }
   __syncthreads();
+  if constexpr (LX) {
+    if (fused) tc_fence_after();
+  }
   uint32_t parity = 0;
 
   const int nitems = (a.nblocks + a.blocks_per_item - 1) / a.blocks_per_item;
@@ -1743,11 +1905,16 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1)
             sm1[v] = limit_<R>(LIM, dm, d[v]);
             WL[v] = Wm1[v] + R(0.5) * sm1[v];
           }
+          // fused network: every thread takes five steps (the CTA's 384 faces
+          // of a step go through the network together); a lane of the upper
+          // half has four faces and computes a throw-away fifth
+          const int nsteps = (LX && fused && corr) ? 5 : nf;
 #pragma unroll 1
-          for (int k = 0; k < nf; k++) {
+          for (int k = 0; k < nsteps; k++) {
+            const bool valid = k < nf;
             const int f = f0 + k;
             R Wp[8], WR[8], s0[8], dn[8];
-            load_rot<R>(sT, rot, cidx(f + 1), Wp);
+            load_rot<R>(sT, rot, cidx(valid ? f + 1 : f), Wp);
 #pragma unroll
             for (int v = 0; v < NV; v++) {
               dn[v] = Wp[v] - W0[v];
@@ -1767,7 +1934,7 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1)
             phys_flux<R>(WR, B0r, gamma, inv_gm1, FR, UR, unR, cfR);
             R aL = Ops<R>::abs_(unL) + cfL, aR = Ops<R>::abs_(unR) + cfR;
             R cmax = aL > aR ? aL : aR;
-            const int fi = chki(fline * 9 + f, 0, NFACE);
+            const int fi = chki(fline * 9 + (f < 9 ? f : 8), 0, NFACE);  // (f = 9: the throw-away step)
             R Fr[8];
             if constexpr (FLX == FLUX_HLL) {
               // HLL with S_L = min(unL - cfL, unR - cfR, 0), S_R = max(unL + cfL,
@@ -1839,6 +2006,48 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1)
                   fo[4 + fd2] = Fr[6];
                   fo[7] = Fr[7];
                 }
+              } else if (LX && a.learned && corr) {
+                // the network on the tensor cores, with the CTA's other faces
+                // of this step; inputs as for kind 3
+                const R ir = Ops<R>::div_(R(1), rho_ref), ic = Ops<R>::div_(R(1), c_ref);
+                const R ib = Ops<R>::div_(R(1), sq * c_ref), ip = Ops<R>::div_(R(1), rho_ref * c_ref * c_ref);
+                float xin[40];
+#pragma unroll
+                for (int sidx = 0; sidx < 5; sidx++) {
+                  const R* Wsrc = sidx == 0 ? Wm2 : (sidx == 1 ? Wm1 : (sidx == 2 ? W0 : Wp));
+                  R wv[8];
+#pragma unroll
+                  for (int v = 0; v < NV; v++) wv[v] = sidx < 4 ? Wsrc[v] : R(0.5) * (WL[v] + WR[v]);
+                  xin[8 * sidx + 0] = static_cast<float>(wv[0] * ir);
+#pragma unroll
+                  for (int c = 1; c < 4; c++) xin[8 * sidx + c] = static_cast<float>(wv[c] * ic);
+#pragma unroll
+                  for (int c = 4; c < 7; c++) xin[8 * sidx + c] = static_cast<float>(wv[c] * ib);
+                  xin[8 * sidx + 7] = static_cast<float>(wv[7] * ip);
+                }
+                uint4 xrow[6];
+#pragma unroll
+                for (int q = 0; q < 5; q++)
+                  xrow[q] = make_uint4(pack_bf16(xin[8 * q], xin[8 * q + 1]), pack_bf16(xin[8 * q + 2], xin[8 * q + 3]),
+                                       pack_bf16(xin[8 * q + 4], xin[8 * q + 5]),
+                                       pack_bf16(xin[8 * q + 6], xin[8 * q + 7]));
+                xrow[5] = make_uint4(0u, 0u, 0u, 0u);
+                float yv[8];
+                if (!lrn_network(*ls, xrow, yv, tid, mphase, a.err)) {
+                  mfail = true;
+                  break;
+                }
+                const R sc0 = rho_ref * c_ref, sc1 = rho_ref * c_ref * c_ref, sc4 = sq * c_ref * c_ref;
+                const R sc7 = rho_ref * c_ref * c_ref * c_ref;
+#pragma unroll
+                for (int v = 0; v < NV; v++) {
+                  const R sc = v == 0 ? sc0 : (v < 4 ? sc1 : (v < 7 ? sc4 : sc7));
+                  R dF = R(yv[v]) * sc;
+                  const R lim = Ops<R>::abs_(R(0.5) * cmax * (UR[v] - UL[v]));
+                  dF = dF > lim ? lim : dF;
+                  dF = dF < -lim ? -lim : dF;
+                  Fr[v] = Fr[v] + dF;
+                }
               } else if (a.learned && corr) {
                 // correction back in flux units, clipped to the Rusanov dissipation
                 const float* yv = a.Y + gface * 8;
@@ -1855,6 +2064,7 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1)
                 }
               }
             }
+            if (!valid) continue;  // the throw-away fifth step
             const R bnf = R(0.5) * (WL[4] + WR[4]);  // face-averaged normal B1 (Powell)
 #pragma unroll
             for (int v = 0; v < NV; v++) {
@@ -2138,6 +2348,7 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1)
       } else {
         if (tid < FACE_THREADS) faces(true);
       }
+      if (mfail) break;  // a tensor-core wait ran out: the error is flagged, stop
       __syncthreads();
       // the staged tile's next block (its copies go out once this block's
       // cell phase has read what it needs from the tile)
@@ -2199,6 +2410,10 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, MIXED ? 2 : 1)
       __syncthreads();
       issue_next(0);
     }
+    if (mfail) break;
+  }
+  if constexpr (LX) {
+    if (fused) lrn_teardown(*ls, tid, mfail, mphase, a.err);
   }
 }
 
@@ -2590,7 +2805,7 @@ size_t stage_smem_bytes(bool mixed) {
 // dynamic shared memory of a stage kernel: the mixed plain kernel stages
 // its own tile layout
 static size_t stage_smem(bool mixed, bool lrn) {
-  return mixed ? (lrn ? StageCfg<true>::SMEM : StageCfg<true>::SMEM_MX) : StageCfg<false>::SMEM;
+  return mixed ? (lrn ? kSmemLx : StageCfg<true>::SMEM_MX) : StageCfg<false>::SMEM;
 }
 
 using StageFn = void (*)(const StageArgs);
