@@ -184,6 +184,8 @@ def learned_form_summary(stream, steps=32):
     from paper_2501_06717_gb300 import bats, learn
     t0 = time.perf_counter()
     X, Y = learn.make_pairs(variants=list(range(101, 117)), snapshots=(4, 12, 20), keep=0.3)
+    t_pairs = time.perf_counter() - t0
+    t0 = time.perf_counter()
     P, hist = learn.train(X, Y, epochs=20, lr=2e-3)
     t_train = time.perf_counter() - t0
     e_plain, e_learn = learn.evaluate(P, nsteps=16)
@@ -241,7 +243,7 @@ def learned_form_summary(stream, steps=32):
                                             "plain_2x": 2 * big2.ncells / (r["plain_2x_two_fine_steps"] * 1e-3)}}
     return {"workload": "spherical blast: 120 blocks (1x) with the trained network vs plain 1x and plain 2x "
                         "(960 blocks), fixed dt, CUDA graph",
-            "pairs": int(X.shape[0]), "train_s": t_train, "loss_first_last_epoch": [hist[0], hist[-1]],
+            "pairs": int(X.shape[0]), "pairs_s": t_pairs, "train_s": t_train, "train_epochs": 20, "train_batch": 8192, "loss_first_last_epoch": [hist[0], hist[-1]],
             "error_vs_restricted_2x": {"plain_1x": e_plain, "learned_1x": e_learn,
                                        "plain_1x_mixed": e_plain_m, "learned_1x_mixed": e_learn_m},
             "error_vs_restricted_4x_fp64": {**e4, "learned_1x_both_stages": e4["learned_1x"],

@@ -323,12 +323,27 @@ int bats_mlp_get_params(bats_mlp_t* m, float* params);
 int bats_mlp_forward(bats_mlp_t* m, const float* X, int64_t n, float* Y);
 /* Loss L = (1/(8n)) sum (y - t)^2 over n samples (X n x 40, T n x 8) and its
  * gradient (grad nullable, BATS_MLP_NPARAM floats); inputs are rounded to
- * BF16 as in inference.  Weight gradients accumulate with atomics, so their
- * last bits can vary between runs. */
+ * BF16 as in inference.  Forward and backward products run on the tensor
+ * cores (tcgen05, the weight gradients with the samples as the contracted
+ * dimension); each CTA (one per SM at most, 128 samples per tile) writes a
+ * partial sum and the partials are added in CTA order, so the result is the
+ * same bit for bit from call to call on one GPU. */
 int bats_mlp_loss_grad(bats_mlp_t* m, const float* X, const float* T, int64_t n, float* grad, double* loss);
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with learning rate lr on
  * the batch; *loss (nullable) receives the loss before the step. */
 int bats_mlp_train_step(bats_mlp_t* m, const float* X, const float* T, int64_t n, float lr, double* loss);
+/* One epoch of minibatch Adam steps on a training set already on the device:
+ * step s (s = 0 .. n_perm / batch - 1) uses samples perm[s * batch] ..
+ * perm[s * batch + batch - 1], each a row of X (n x 40 floats) and T (n x 8
+ * floats); a ragged rest of perm is not used.  X, T and perm (int64 row
+ * indices in [0, n)) are device pointers, else BATS_ERR_INVALID_ARG, as for
+ * batch < 1, n_perm < batch or lr < 0.  The steps are queued on the handle's
+ * stream and synchronised once, at the end; *mean_loss (nullable) receives the
+ * mean over the steps of each step's loss before its update.  An index
+ * outside [0, n) contributes nothing and makes the call return
+ * BATS_ERR_INVALID_ARG after the epoch (the steps still ran). */
+int bats_mlp_train_epoch(bats_mlp_t* m, const float* X, const float* T, int64_t n, const int64_t* perm,
+                         int64_t n_perm, int64_t batch, float lr, double* mean_loss);
 
 /* ---- stepping without device allocation --------------------------------
  * No counterpart in the paper: an addition for callers that cannot allocate

@@ -125,6 +125,8 @@ def lib():
     L.bats_mlp_forward.argtypes = [vp, vp, ctypes.c_int64, vp]
     L.bats_mlp_loss_grad.argtypes = [vp, vp, vp, ctypes.c_int64, vp, ctypes.POINTER(ctypes.c_double)]
     L.bats_mlp_train_step.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.c_float, ctypes.POINTER(ctypes.c_double)]
+    L.bats_mlp_train_epoch.argtypes = [vp, vp, vp, ctypes.c_int64, vp, ctypes.c_int64, ctypes.c_int64,
+                                       ctypes.c_float, ctypes.POINTER(ctypes.c_double)]
     L.bats_step_noalloc.argtypes = [ctypes.POINTER(bats_grid_desc), ctypes.POINTER(bats_physics), dp,
                                     ctypes.c_size_t, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                     ctypes.POINTER(ctypes.c_double), vp, ctypes.c_char_p, ctypes.c_size_t]
@@ -445,6 +447,18 @@ class Mlp:
         pt, _ = _ptr_and_size(T)
         loss = ctypes.c_double(0.0)
         self._rc(lib().bats_mlp_train_step(self.h, px, pt, n // 40, float(lr), ctypes.byref(loss)), "train_step")
+        return loss.value
+
+    def train_epoch(self, X, T, perm, batch, lr):
+        """Adam steps over minibatches perm[s*batch:(s+1)*batch] of the rows of
+        X (n x 40) and T (n x 8); X, T and perm (int64) are device tensors.
+        Returns the mean loss of the steps."""
+        px, n = _ptr_and_size(X)
+        pt, _ = _ptr_and_size(T)
+        pp, npm = _ptr_and_size(perm)
+        loss = ctypes.c_double(0.0)
+        self._rc(lib().bats_mlp_train_epoch(self.h, px, pt, n // 40, pp, npm, int(batch), float(lr),
+                                            ctypes.byref(loss)), "train_epoch")
         return loss.value
 
 

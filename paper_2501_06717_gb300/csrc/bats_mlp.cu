@@ -9,11 +9,9 @@
 //    tensor-memory accumulator, which eight warps read back (tcgen05.ld;
 //    two warps per row, 32 columns each), add the bias to, pass through GELU
 //    and store as the next layer's BF16 operand.
-//  * k_mlp_train: the mean-squared-error loss and its gradient for a batch;
-//    forward and the backward data products on tensor cores (warp-level
-//    mma.sync m16n8k16 BF16, activations kept in registers), the weight
-//    gradients (outer products over the tile's samples) on the CUDA cores,
-//    accumulated per CTA in shared memory and once per CTA in global memory.
+//  * k_mlp_train_tc, k_mlp_grad_reduce: the mean-squared-error loss and its
+//    gradient for a batch, every product on tcgen05 (the weight gradients
+//    with the samples as K), per-CTA partial sums added in a fixed order.
 //  * k_mlp_adam, k_mlp_pack: the Adam update of the FP32 master weights and
 //    the BF16 copies in the layouts the kernels read.
 #include <cuda_bf16.h>
@@ -31,96 +29,6 @@
 #include "bats_tc.h"
 
 namespace batsk {
-
-__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// Shared-memory weight layout (32-bit words = BF16 pairs), rows padded so the
-// B-fragment loads of a warp fall in distinct banks.
-constexpr int W1S = 28;  // W1 [64 out][48 in] -> 24 words + 4 pad
-constexpr int W2S = 36;  // W2, W2T [64][64] -> 32 words + 4 pad
-constexpr int W3S = 36;  // W3 [8][64]
-constexpr int W3TS = 12; // W3T [64 in][16 out (8 + zeros)] -> 8 words + 4 pad
-struct MlpSmem {
-  uint32_t w1[64 * W1S];
-  uint32_t w2[64 * W2S];
-  uint32_t w3[8 * W3S];
-  uint32_t w2t[64 * W2S];
-  uint32_t w3t[64 * W3TS];
-  float b1[64], b2[64], b3[8];
-};
-
-// Copy the packed device weights (MlpDev, unpadded rows) into shared memory.
-__device__ void load_mlp_smem(const MlpDev& m, MlpSmem& s) {
-  for (int e = threadIdx.x; e < 64 * 24; e += blockDim.x) s.w1[(e / 24) * W1S + e % 24] = m.w1[e];
-  for (int e = threadIdx.x; e < 64 * 32; e += blockDim.x) {
-    s.w2[(e / 32) * W2S + e % 32] = m.w2[e];
-    s.w2t[(e / 32) * W2S + e % 32] = m.w2t[e];
-  }
-  for (int e = threadIdx.x; e < 8 * 32; e += blockDim.x) s.w3[(e / 32) * W3S + e % 32] = m.w3[e];
-  for (int e = threadIdx.x; e < 64 * 8; e += blockDim.x) s.w3t[(e / 8) * W3TS + e % 8] = m.w3t[e];
-  for (int e = threadIdx.x; e < 64; e += blockDim.x) {
-    s.b1[e] = m.b1[e];
-    s.b2[e] = m.b2[e];
-  }
-  for (int e = threadIdx.x; e < 8; e += blockDim.x) s.b3[e] = m.b3[e];
-}
-
-// Forward of one 16-row tile.  a1: A fragments of the inputs (3 k-tiles).
-// Outputs: z1, z2 (pre-activations, C layout, 8 n-tiles x 4), a2, a3 (BF16
-// A fragments of H1, H2, 4 k-tiles x 4), y (C layout of the 8 outputs).
-template <bool KEEP>
-__device__ __forceinline__ void mlp_tile_forward(const MlpSmem& s, const uint32_t a1[3][4], float z1[8][4],
-                                                 float z2[8][4], uint32_t a2[4][4], uint32_t a3[4][4],
-                                                 float y[4]) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  float acc[8][4];
-#pragma unroll
-  for (int nt = 0; nt < 8; nt++) {
-    const float bl = s.b1[nt * 8 + 2 * t], bh = s.b1[nt * 8 + 2 * t + 1];
-    acc[nt][0] = bl; acc[nt][1] = bh; acc[nt][2] = bl; acc[nt][3] = bh;
-#pragma unroll
-    for (int kt = 0; kt < 3; kt++)
-      mma_bf16(acc[nt], a1[kt], s.w1[(nt * 8 + g) * W1S + kt * 8 + t], s.w1[(nt * 8 + g) * W1S + kt * 8 + 4 + t]);
-  }
-#pragma unroll
-  for (int nt = 0; nt < 8; nt++) {
-    if (KEEP) {
-#pragma unroll
-      for (int r = 0; r < 4; r++) z1[nt][r] = acc[nt][r];
-    }
-    const int kt = nt >> 1, hi = nt & 1;
-    a2[kt][hi * 2 + 0] = gelu2_pack(acc[nt][0], acc[nt][1]);
-    a2[kt][hi * 2 + 1] = gelu2_pack(acc[nt][2], acc[nt][3]);
-  }
-#pragma unroll
-  for (int nt = 0; nt < 8; nt++) {
-    const float bl = s.b2[nt * 8 + 2 * t], bh = s.b2[nt * 8 + 2 * t + 1];
-    acc[nt][0] = bl; acc[nt][1] = bh; acc[nt][2] = bl; acc[nt][3] = bh;
-#pragma unroll
-    for (int kt = 0; kt < 4; kt++)
-      mma_bf16(acc[nt], a2[kt], s.w2[(nt * 8 + g) * W2S + kt * 8 + t], s.w2[(nt * 8 + g) * W2S + kt * 8 + 4 + t]);
-  }
-#pragma unroll
-  for (int nt = 0; nt < 8; nt++) {
-    if (KEEP) {
-#pragma unroll
-      for (int r = 0; r < 4; r++) z2[nt][r] = acc[nt][r];
-    }
-    const int kt = nt >> 1, hi = nt & 1;
-    a3[kt][hi * 2 + 0] = gelu2_pack(acc[nt][0], acc[nt][1]);
-    a3[kt][hi * 2 + 1] = gelu2_pack(acc[nt][2], acc[nt][3]);
-  }
-  const float bl = s.b3[2 * t], bh = s.b3[2 * t + 1];
-  y[0] = bl; y[1] = bh; y[2] = bl; y[3] = bh;
-#pragma unroll
-  for (int kt = 0; kt < 4; kt++) mma_bf16(y, a3[kt], s.w3[g * W3S + kt * 8 + t], s.w3[g * W3S + kt * 8 + 4 + t]);
-}
 
 constexpr int TC_TILE = 128;             // rows per tile (MMA M = tensor-memory lanes)
 constexpr int TC_TMEM_COLS = 64;         // one FP32 accumulator of N = 64 (reused by all three layers)
@@ -283,155 +191,6 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_mlp_infer(const uint32_t* __r
   }
 }
 
-// Loss sum and gradient of L = (1/(8 n_total)) sum (y - t)^2 over rows
-// [0, n) of X (FP32 [n][40], rounded to BF16 on load) and T (FP32 [n][8]).
-// grad (FP32 [NPARAM], zeroed by the caller) and loss_sum accumulate.
-constexpr int TRAIN_WARPS = 4;
-struct TrainTile {           // per-warp staging of one 16-sample tile, FP32
-  float x[16][40];
-  float h1[16][64];
-  float h2[16][64];
-  float dz1[16][64];
-  float dz2[16][64];
-  float dy[16][8];
-};
-
-__global__ void __launch_bounds__(TRAIN_WARPS * 32) k_mlp_train(const float* __restrict__ X,
-                                                                const float* __restrict__ T, int64_t n,
-                                                                double inv_count, MlpDev m,
-                                                                float* __restrict__ grad,
-                                                                double* __restrict__ loss_sum) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  MlpSmem& s = *reinterpret_cast<MlpSmem*>(smem_raw);
-  TrainTile* tiles = reinterpret_cast<TrainTile*>(smem_raw + sizeof(MlpSmem));
-  float* sgrad = reinterpret_cast<float*>(smem_raw + sizeof(MlpSmem) + TRAIN_WARPS * sizeof(TrainTile));
-  load_mlp_smem(m, s);
-  for (int e = threadIdx.x; e < MLP_NPARAM; e += blockDim.x) sgrad[e] = 0.f;
-  __syncthreads();
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3, w = threadIdx.x >> 5;
-  TrainTile& tt = tiles[w];
-  const int64_t warp = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
-  const float scale = static_cast<float>(2.0 * inv_count);
-  double lsum = 0.0;
-  for (int64_t r0 = warp * 16; r0 < n; r0 += nwarps * 16) {
-    const int64_t ra = r0 + g, rb = r0 + g + 8;
-    // inputs as BF16 A fragments (and their FP32 values for the W1 gradient)
-    uint32_t a1[3][4];
-#pragma unroll
-    for (int kt = 0; kt < 3; kt++) {
-#pragma unroll
-      for (int q = 0; q < 4; q++) {
-        const int64_t r = (q & 1) ? rb : ra;
-        const int col = kt * 16 + (q >> 1) * 8 + 2 * t;
-        float v0 = 0.f, v1 = 0.f;
-        if (r < n && col < MLP_IN) {
-          v0 = X[r * MLP_IN + col];
-          v1 = X[r * MLP_IN + col + 1];
-        }
-        a1[kt][q] = pack_bf16(v0, v1);
-        if (col < MLP_IN) {
-          const int rr = (q & 1) ? g + 8 : g;
-          tt.x[rr][col] = bf16_lo(a1[kt][q]);
-          tt.x[rr][col + 1] = bf16_hi(a1[kt][q]);
-        }
-      }
-    }
-    float z1[8][4], z2[8][4], y[4];
-    uint32_t a2[4][4], a3[4][4];
-    mlp_tile_forward<true>(s, a1, z1, z2, a2, a3, y);
-    // dL/dy
-    float dy[4];
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-      const int64_t r = q < 2 ? ra : rb;
-      const int col = 2 * t + (q & 1);
-      float e = 0.f;
-      if (r < n) e = y[q] - T[r * 8 + col];
-      lsum += static_cast<double>(e) * e;
-      dy[q] = scale * e;
-      tt.dy[q < 2 ? g : g + 8][col] = dy[q];
-    }
-    // stage H1, H2 (the BF16 values the next layers saw)
-#pragma unroll
-    for (int kt = 0; kt < 4; kt++)
-#pragma unroll
-      for (int q = 0; q < 4; q++) {
-        const int rr = (q & 1) ? g + 8 : g;
-        const int col = kt * 16 + (q >> 1) * 8 + 2 * t;
-        tt.h1[rr][col] = bf16_lo(a2[kt][q]);
-        tt.h1[rr][col + 1] = bf16_hi(a2[kt][q]);
-        tt.h2[rr][col] = bf16_lo(a3[kt][q]);
-        tt.h2[rr][col + 1] = bf16_hi(a3[kt][q]);
-      }
-    // dH2 = dY W3 (K = 8 outputs, zero-padded to 16), dZ2 = dH2 * gelu'(Z2)
-    uint32_t ady[4] = {pack_bf16(dy[0], dy[1]), pack_bf16(dy[2], dy[3]), 0u, 0u};
-    uint32_t adz2[4][4];
-#pragma unroll
-    for (int nt = 0; nt < 8; nt++) {
-      float c[4] = {0.f, 0.f, 0.f, 0.f};
-      mma_bf16(c, ady, s.w3t[(nt * 8 + g) * W3TS + t], s.w3t[(nt * 8 + g) * W3TS + 4 + t]);
-#pragma unroll
-      for (int q = 0; q < 4; q++) c[q] *= gelu_grad_f(z2[nt][q]);
-      const int kt = nt >> 1, hi = nt & 1;
-      adz2[kt][hi * 2 + 0] = pack_bf16(c[0], c[1]);
-      adz2[kt][hi * 2 + 1] = pack_bf16(c[2], c[3]);
-      const int col = nt * 8 + 2 * t;
-      tt.dz2[g][col] = c[0];
-      tt.dz2[g][col + 1] = c[1];
-      tt.dz2[g + 8][col] = c[2];
-      tt.dz2[g + 8][col + 1] = c[3];
-    }
-    // dH1 = dZ2 W2, dZ1 = dH1 * gelu'(Z1)
-#pragma unroll
-    for (int nt = 0; nt < 8; nt++) {
-      float c[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-      for (int kt = 0; kt < 4; kt++)
-        mma_bf16(c, adz2[kt], s.w2t[(nt * 8 + g) * W2S + kt * 8 + t], s.w2t[(nt * 8 + g) * W2S + kt * 8 + 4 + t]);
-      const int col = nt * 8 + 2 * t;
-      tt.dz1[g][col] = c[0] * gelu_grad_f(z1[nt][0]);
-      tt.dz1[g][col + 1] = c[1] * gelu_grad_f(z1[nt][1]);
-      tt.dz1[g + 8][col] = c[2] * gelu_grad_f(z1[nt][2]);
-      tt.dz1[g + 8][col + 1] = c[3] * gelu_grad_f(z1[nt][3]);
-    }
-    __syncwarp();
-    // weight and bias gradients: sums over the tile's 16 samples
-    for (int e = lane; e < MLP_NPARAM; e += 32) {
-      float acc = 0.f;
-      if (e < 2560) {
-        const int o = e / 40, i = e % 40;
-#pragma unroll 4
-        for (int r = 0; r < 16; r++) acc += tt.dz1[r][o] * tt.x[r][i];
-      } else if (e < 2624) {
-        const int o = e - 2560;
-        for (int r = 0; r < 16; r++) acc += tt.dz1[r][o];
-      } else if (e < 6720) {
-        const int o = (e - 2624) >> 6, i = (e - 2624) & 63;
-#pragma unroll 4
-        for (int r = 0; r < 16; r++) acc += tt.dz2[r][o] * tt.h1[r][i];
-      } else if (e < 6784) {
-        const int o = e - 6720;
-        for (int r = 0; r < 16; r++) acc += tt.dz2[r][o];
-      } else if (e < 7296) {
-        const int o = (e - 6784) >> 6, i = (e - 6784) & 63;
-#pragma unroll 4
-        for (int r = 0; r < 16; r++) acc += tt.dy[r][o] * tt.h2[r][i];
-      } else {
-        const int o = e - 7296;
-        for (int r = 0; r < 16; r++) acc += tt.dy[r][o];
-      }
-      atomicAdd(&sgrad[e], acc);
-    }
-    __syncwarp();
-  }
-  // loss: warp sum, then one atomic per warp
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
-  if (lane == 0) atomicAdd(loss_sum, lsum);
-  __syncthreads();
-  for (int e = threadIdx.x; e < MLP_NPARAM; e += blockDim.x) atomicAdd(&grad[e], sgrad[e]);
-}
 
 // Adam (Kingma & Ba 2015) on the FP32 master weights, bias-corrected.
 __global__ void k_mlp_adam(float* __restrict__ p, const float* __restrict__ gr, float* __restrict__ m1,
@@ -489,13 +248,374 @@ __global__ void k_rows_to_bf16(const float* __restrict__ X, uint32_t* __restrict
 }
 
 // ---------------------------------------------------------------------------
+// Training on tcgen05.  One CTA of 128 threads per SM, persistent over
+// 128-sample tiles; thread t owns sample t of the tile (tensor-memory lane t).
+// Every product is a tcgen05.mma with the FP32 accumulator in tensor memory:
+//   forward   Z1 = X W1^T, Z2 = H1 W2^T, Y = H2 W3^T          (M = samples)
+//   backward  dH2 = dY W3, dH1 = dZ2 W2                         (M = samples)
+//   weights   dW1|db1 = dZ1^T [X | 1], dW2|db2 = dZ2^T [H1 | 1],
+//             dW3^T|db3 = [H2 | 1]^T dY                         (K = samples)
+// For the weight products the threads store the per-sample factors
+// transposed (a column per sample), which makes them K-major operands with
+// the samples along K; a row of ones appended to one factor gives the bias
+// gradient in an extra accumulator row or column.  The weight accumulators
+// live in tensor memory across all of a CTA's tiles (a fixed order of
+// accumulation), each CTA writes its partial gradient, and a second kernel
+// sums the partials in CTA order: the gradient is the same bit for bit from
+// run to run.
+
+constexpr int TT = 128;              // samples per tile
+constexpr uint32_t SBO_KT = 16 * TT; // K = 128 samples: 2048 bytes per 8-row group
+constexpr uint32_t SBO_K16 = 256;    // K = 16
+struct TrainTc {
+  alignas(128) uint8_t a1[TT * 128];   // X (K = 48), then H1 (K = 64), then dZ2 (K = 64): A operands, M = samples
+  alignas(128) uint8_t a2[TT * 128];   // H2 (K = 64), then dY (K = 16)
+  alignas(128) uint8_t xt[48 * 256];   // [X | 1]^T: rows 0-39 features, 40 ones, 41-47 zero; K = samples
+  alignas(128) uint8_t h1t[80 * 256];  // [H1 | 1]^T: rows 0-63, 64 ones, 65-79 zero
+  alignas(128) uint8_t h2t[128 * 256]; // [H2 | 1]^T as the A of dW3^T: rows 0-63, 64 ones, 65-127 zero
+  alignas(128) uint8_t dyt[16 * 256];  // dY^T: rows 0-7, 8-15 zero
+  alignas(128) uint8_t dz2t[128 * 256];// dZ2^T: rows 0-63, 64-127 zero
+  alignas(128) uint8_t dz1t[128 * 256];// dZ1^T: rows 0-63, 64-127 zero
+  alignas(128) uint8_t w1[64 * 96];    // B of Z1: N = 64, K = 48
+  alignas(128) uint8_t w2[64 * 128];   // B of Z2: N = 64, K = 64
+  alignas(128) uint8_t w3[16 * 128];   // B of Y: N = 16 (8 zero rows), K = 64
+  alignas(128) uint8_t w3t[64 * 32];   // B of dH2: N = 64, K = 16 (W3^T, 8 zero columns)
+  alignas(128) uint8_t w2t[64 * 128];  // B of dH1: N = 64, K = 64 (W2^T)
+  float b1[64], b2[64], b3[8];
+  double wloss[4];
+  uint64_t bar;
+  uint32_t tmem;
+};
+// tensor-memory columns of the accumulators
+constexpr uint32_t TM_Z1 = 0, TM_Z2 = 64, TM_Y = 128, TM_DH2 = 160, TM_DH1 = 224, TM_D1 = 288, TM_D2 = 352,
+                   TM_D3 = 448, TM_COLS = 512;
+
+// one BF16 (bits) of a K = 128-sample transposed operand: row r, sample k
+__device__ __forceinline__ void st_t(uint8_t* buf, int r, int k, uint16_t v) {
+  *reinterpret_cast<uint16_t*>(buf + cm_off(r, k >> 3, SBO_KT) + (k & 7) * 2) = v;
+}
+__device__ __forceinline__ uint16_t bf16_bits(float v) {
+  return static_cast<uint16_t>(pack_bf16(v, 0.f) & 0xffffu);
+}
+
+// The MMAs of one group (issued by thread 0, committed, waited for by all
+// threads, bounded): false when the wait ran out.
+template <class F>
+__device__ __forceinline__ bool tt_group(TrainTc& s, int t, uint32_t& phase, int32_t* err, F issue) {
+  proxy_fence_smem();
+  tc_fence_before();
+  __syncthreads();
+  if (t == 0) {
+    tc_fence_after();
+    issue();
+    umma_commit(&s.bar);
+  }
+  const bool got = mbar_wait_bounded_tc(&s.bar, phase, err);
+  if (__syncthreads_or(!got)) return false;
+  phase ^= 1u;
+  tc_fence_after();
+  return true;
+}
+
+__global__ void __launch_bounds__(TT, 1) k_mlp_train_tc(const float* __restrict__ X, const float* __restrict__ T,
+                                                       const int64_t* __restrict__ idx, int64_t nrows,
+                                                       int64_t n, double inv_count, MlpDev m,
+                                                       float* __restrict__ partial, double* __restrict__ partial_loss,
+                                                       int32_t* err) {
+  extern __shared__ __align__(128) unsigned char tt_smem_raw[];
+  TrainTc& s = *reinterpret_cast<TrainTc*>((reinterpret_cast<uintptr_t>(tt_smem_raw) + 127) & ~uintptr_t(127));
+  const int t = threadIdx.x, warp = t >> 5;
+  // weights in the canonical layouts; the constant rows and columns of the
+  // transposed operands (ones, zeros)
+  for (int e = t; e < 64 * 6; e += TT) {
+    const int r = e / 6, kc = e % 6;
+    *reinterpret_cast<uint4*>(s.w1 + cm_off(r, kc, SBO_K48)) = *reinterpret_cast<const uint4*>(m.w1 + r * 24 + kc * 4);
+  }
+  for (int e = t; e < 64 * 8; e += TT) {
+    const int r = e / 8, kc = e % 8;
+    *reinterpret_cast<uint4*>(s.w2 + cm_off(r, kc, SBO_K64)) = *reinterpret_cast<const uint4*>(m.w2 + r * 32 + kc * 4);
+    *reinterpret_cast<uint4*>(s.w2t + cm_off(r, kc, SBO_K64)) = *reinterpret_cast<const uint4*>(m.w2t + r * 32 + kc * 4);
+  }
+  for (int e = t; e < 16 * 8; e += TT) {
+    const int r = e / 8, kc = e % 8;
+    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+    *reinterpret_cast<uint4*>(s.w3 + cm_off(r, kc, SBO_K64)) =
+        r < 8 ? *reinterpret_cast<const uint4*>(m.w3 + r * 32 + kc * 4) : z;
+  }
+  for (int e = t; e < 64 * 2; e += TT) {
+    const int r = e / 2, kc = e % 2;
+    *reinterpret_cast<uint4*>(s.w3t + cm_off(r, kc, SBO_K16)) = *reinterpret_cast<const uint4*>(m.w3t + r * 8 + kc * 4);
+  }
+  if (t < 64) {
+    s.b1[t] = m.b1[t];
+    s.b2[t] = m.b2[t];
+  }
+  if (t < 8) s.b3[t] = m.b3[t];
+  {
+    const uint16_t one = bf16_bits(1.f);
+    for (int r = 40; r < 48; r++) st_t(s.xt, r, t, r == 40 ? one : 0);
+    for (int r = 64; r < 80; r++) st_t(s.h1t, r, t, r == 64 ? one : 0);
+    for (int r = 64; r < 128; r++) {
+      st_t(s.h2t, r, t, r == 64 ? one : 0);
+      st_t(s.dz2t, r, t, 0);
+      st_t(s.dz1t, r, t, 0);
+    }
+    for (int r = 8; r < 16; r++) st_t(s.dyt, r, t, 0);
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_saddr(&s.tmem)),
+                 "r"(TM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (t == 0) mbar_init_tc(&s.bar);
+  proxy_fence_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tm = s.tmem;
+  const uint32_t tl = tm + (static_cast<uint32_t>(32 * warp) << 16);  // this warp's lanes
+  const uint32_t a1s = tc_saddr(s.a1), a2s = tc_saddr(s.a2), xts = tc_saddr(s.xt), h1ts = tc_saddr(s.h1t);
+  const uint32_t h2ts = tc_saddr(s.h2t), dyts = tc_saddr(s.dyt), dz2ts = tc_saddr(s.dz2t), dz1ts = tc_saddr(s.dz1t);
+  const uint32_t w1s = tc_saddr(s.w1), w2s = tc_saddr(s.w2), w3s = tc_saddr(s.w3), w3ts = tc_saddr(s.w3t),
+                 w2ts = tc_saddr(s.w2t);
+  const float scale = static_cast<float>(2.0 * inv_count);
+  uint32_t phase = 0;
+  bool failed = false, any = false;
+  double lsum = 0.0;
+  const int64_t ntiles = (n + TT - 1) / TT;
+  for (int64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
+    const int64_t rt = tile * TT + t;
+    int64_t r = rt < n && idx ? idx[rt] : rt;  // the sample's row of X and T
+    if (idx && rt < n && (r < 0 || r >= nrows)) {  // an index outside X: no contribution, flagged
+      atomicOr(err, ERR_BOUNDS);
+      r = -1;
+    }
+    const bool valid = rt < n && r >= 0;
+    // X row t (BF16) as the A of Z1, and its column of [X | 1]^T
+    {
+      float x[40];
+#pragma unroll
+      for (int i = 0; i < 40; i++) x[i] = valid ? X[r * 40 + i] : 0.f;
+#pragma unroll
+      for (int kc = 0; kc < 6; kc++) {
+        uint4 o = make_uint4(0u, 0u, 0u, 0u);
+        if (kc < 5)
+          o = make_uint4(pack_bf16(x[8 * kc], x[8 * kc + 1]), pack_bf16(x[8 * kc + 2], x[8 * kc + 3]),
+                         pack_bf16(x[8 * kc + 4], x[8 * kc + 5]), pack_bf16(x[8 * kc + 6], x[8 * kc + 7]));
+        *reinterpret_cast<uint4*>(s.a1 + cm_off(t, kc, SBO_K48)) = o;
+      }
+#pragma unroll
+      for (int i = 0; i < 40; i++) st_t(s.xt, i, t, bf16_bits(x[i]));
+    }
+    const uint32_t I64 = umma_idesc_bf16(TT, 64), I16 = umma_idesc_bf16(TT, 16), I48 = umma_idesc_bf16(TT, 48),
+                   I80 = umma_idesc_bf16(TT, 80);
+    // Z1 = X W1^T
+    if (!tt_group(s, t, phase, err, [&]() {
+          for (int k = 0; k < 3; k++)
+            umma_bf16(tm + TM_Z1, umma_sdesc(a1s + 256 * k, 128, SBO_K48), umma_sdesc(w1s + 256 * k, 128, SBO_K48),
+                      I64, k > 0);
+        })) { failed = true; break; }
+    // H1 = GELU(Z1 + b1): the A of Z2 (into a1) and a column of [H1 | 1]^T
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      float v[16];
+      tmem_ld16(tl + TM_Z1 + 16 * q, v);
+#pragma unroll
+      for (int c = 0; c < 2; c++) {
+        const float* b = s.b1 + 16 * q + 8 * c;
+        const float* z = v + 8 * c;
+        uint4 o;
+        o.x = gelu2_pack(z[0] + b[0], z[1] + b[1]);
+        o.y = gelu2_pack(z[2] + b[2], z[3] + b[3]);
+        o.z = gelu2_pack(z[4] + b[4], z[5] + b[5]);
+        o.w = gelu2_pack(z[6] + b[6], z[7] + b[7]);
+        *reinterpret_cast<uint4*>(s.a1 + cm_off(t, 2 * q + c, SBO_K64)) = o;
+        const uint32_t w[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+          st_t(s.h1t, 16 * q + 8 * c + 2 * j, t, static_cast<uint16_t>(w[j] & 0xffffu));
+          st_t(s.h1t, 16 * q + 8 * c + 2 * j + 1, t, static_cast<uint16_t>(w[j] >> 16));
+        }
+      }
+    }
+    // Z2 = H1 W2^T
+    if (!tt_group(s, t, phase, err, [&]() {
+          for (int k = 0; k < 4; k++)
+            umma_bf16(tm + TM_Z2, umma_sdesc(a1s + 256 * k, 128, SBO_K64), umma_sdesc(w2s + 256 * k, 128, SBO_K64),
+                      I64, k > 0);
+        })) { failed = true; break; }
+    // H2 = GELU(Z2 + b2): the A of Y (into a2) and a column of [H2 | 1]^T
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      float v[16];
+      tmem_ld16(tl + TM_Z2 + 16 * q, v);
+#pragma unroll
+      for (int c = 0; c < 2; c++) {
+        const float* b = s.b2 + 16 * q + 8 * c;
+        const float* z = v + 8 * c;
+        uint4 o;
+        o.x = gelu2_pack(z[0] + b[0], z[1] + b[1]);
+        o.y = gelu2_pack(z[2] + b[2], z[3] + b[3]);
+        o.z = gelu2_pack(z[4] + b[4], z[5] + b[5]);
+        o.w = gelu2_pack(z[6] + b[6], z[7] + b[7]);
+        *reinterpret_cast<uint4*>(s.a2 + cm_off(t, 2 * q + c, SBO_K64)) = o;
+        const uint32_t w[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+          st_t(s.h2t, 16 * q + 8 * c + 2 * j, t, static_cast<uint16_t>(w[j] & 0xffffu));
+          st_t(s.h2t, 16 * q + 8 * c + 2 * j + 1, t, static_cast<uint16_t>(w[j] >> 16));
+        }
+      }
+    }
+    // Y = H2 W3^T (N = 16: the 8 outputs and 8 zero columns)
+    if (!tt_group(s, t, phase, err, [&]() {
+          for (int k = 0; k < 4; k++)
+            umma_bf16(tm + TM_Y, umma_sdesc(a2s + 256 * k, 128, SBO_K64), umma_sdesc(w3s + 256 * k, 128, SBO_K64),
+                      I16, k > 0);
+        })) { failed = true; break; }
+    // dL/dY = 2 (y - t) / (8 n): the A of dH2 (into a2, K = 16) and dY^T
+    {
+      float v[16];
+      tmem_ld16(tl + TM_Y, v);
+      float dy[8];
+#pragma unroll
+      for (int o = 0; o < 8; o++) {
+        const float e = valid ? (v[o] + s.b3[o]) - T[r * 8 + o] : 0.f;
+        lsum += static_cast<double>(e) * e;
+        dy[o] = scale * e;
+      }
+      *reinterpret_cast<uint4*>(s.a2 + cm_off(t, 0, SBO_K16)) =
+          make_uint4(pack_bf16(dy[0], dy[1]), pack_bf16(dy[2], dy[3]), pack_bf16(dy[4], dy[5]), pack_bf16(dy[6], dy[7]));
+      *reinterpret_cast<uint4*>(s.a2 + cm_off(t, 1, SBO_K16)) = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+      for (int o = 0; o < 8; o++) st_t(s.dyt, o, t, bf16_bits(dy[o]));
+    }
+    // dH2 = dY W3
+    if (!tt_group(s, t, phase, err, [&]() {
+          umma_bf16(tm + TM_DH2, umma_sdesc(a2s, 128, SBO_K16), umma_sdesc(w3ts, 128, SBO_K16), I64, 0);
+        })) { failed = true; break; }
+    // dZ2 = dH2 GELU'(Z2 + b2): the A of dH1 (into a1) and a column of dZ2^T
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      float dh[16], z[16];
+      tmem_ld16(tl + TM_DH2 + 16 * q, dh);
+      tmem_ld16(tl + TM_Z2 + 16 * q, z);
+#pragma unroll
+      for (int c = 0; c < 2; c++) {
+        float g[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) g[j] = dh[8 * c + j] * gelu_grad_f(z[8 * c + j] + s.b2[16 * q + 8 * c + j]);
+        *reinterpret_cast<uint4*>(s.a1 + cm_off(t, 2 * q + c, SBO_K64)) =
+            make_uint4(pack_bf16(g[0], g[1]), pack_bf16(g[2], g[3]), pack_bf16(g[4], g[5]), pack_bf16(g[6], g[7]));
+#pragma unroll
+        for (int j = 0; j < 8; j++) st_t(s.dz2t, 16 * q + 8 * c + j, t, bf16_bits(g[j]));
+      }
+    }
+    // dH1 = dZ2 W2
+    if (!tt_group(s, t, phase, err, [&]() {
+          for (int k = 0; k < 4; k++)
+            umma_bf16(tm + TM_DH1, umma_sdesc(a1s + 256 * k, 128, SBO_K64), umma_sdesc(w2ts + 256 * k, 128, SBO_K64),
+                      I64, k > 0);
+        })) { failed = true; break; }
+    // dZ1 = dH1 GELU'(Z1 + b1): a column of dZ1^T
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      float dh[16], z[16];
+      tmem_ld16(tl + TM_DH1 + 16 * q, dh);
+      tmem_ld16(tl + TM_Z1 + 16 * q, z);
+#pragma unroll
+      for (int j = 0; j < 16; j++)
+        st_t(s.dz1t, 16 * q + j, t, bf16_bits(dh[j] * gelu_grad_f(z[j] + s.b1[16 * q + j])));
+    }
+    // the weight gradients of this tile, added to the CTA's accumulators:
+    // [dW1 | db1] += dZ1^T [X | 1], [dW2 | db2] += dZ2^T [H1 | 1],
+    // [dW3^T ; db3] += [H2 | 1]^T dY (K = the tile's 128 samples)
+    const uint32_t acc0 = any ? 1u : 0u;
+    if (!tt_group(s, t, phase, err, [&]() {
+          for (int k = 0; k < 8; k++) {
+            const uint32_t acc = k > 0 ? 1u : acc0;
+            umma_bf16(tm + TM_D1, umma_sdesc(dz1ts + 256 * k, 128, SBO_KT), umma_sdesc(xts + 256 * k, 128, SBO_KT),
+                      I48, acc);
+            umma_bf16(tm + TM_D2, umma_sdesc(dz2ts + 256 * k, 128, SBO_KT), umma_sdesc(h1ts + 256 * k, 128, SBO_KT),
+                      I80, acc);
+            umma_bf16(tm + TM_D3, umma_sdesc(h2ts + 256 * k, 128, SBO_KT), umma_sdesc(dyts + 256 * k, 128, SBO_KT),
+                      I16, acc);
+          }
+        })) { failed = true; break; }
+    any = true;
+  }
+  // this CTA's partial gradient in the parameter order W1, b1, W2, b2, W3, b3
+  float* pg = partial + static_cast<int64_t>(blockIdx.x) * MLP_NPARAM;
+  if (!failed) {
+    float d1[48], d2[80], d3[16];
+#pragma unroll
+    for (int q = 0; q < 3; q++) tmem_ld16(tl + TM_D1 + 16 * q, d1 + 16 * q);
+#pragma unroll
+    for (int q = 0; q < 5; q++) tmem_ld16(tl + TM_D2 + 16 * q, d2 + 16 * q);
+    tmem_ld16(tl + TM_D3, d3);
+    if (!any) {
+#pragma unroll
+      for (int i = 0; i < 48; i++) d1[i] = 0.f;
+#pragma unroll
+      for (int i = 0; i < 80; i++) d2[i] = 0.f;
+#pragma unroll
+      for (int i = 0; i < 16; i++) d3[i] = 0.f;
+    }
+    if (t < 64) {
+#pragma unroll
+      for (int i = 0; i < 40; i++) pg[t * 40 + i] = d1[i];
+      pg[2560 + t] = d1[40];
+#pragma unroll
+      for (int i = 0; i < 64; i++) pg[2624 + t * 64 + i] = d2[i];
+      pg[6720 + t] = d2[64];
+#pragma unroll
+      for (int o = 0; o < 8; o++) pg[6784 + o * 64 + t] = d3[o];
+    } else if (t == 64) {
+#pragma unroll
+      for (int o = 0; o < 8; o++) pg[7296 + o] = d3[o];
+    }
+  }
+  // the CTA's loss: each thread's samples in tile order, then the threads in a fixed order
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+  if ((t & 31) == 0) s.wloss[warp] = lsum;
+  // an MMA may still run after a timed-out wait: wait for it once more
+  if (failed && t == 0) mbar_wait_bounded_tc(&s.bar, phase, err);
+  tc_fence_before();
+  __syncthreads();
+  if (t == 0) partial_loss[blockIdx.x] = ((s.wloss[0] + s.wloss[1]) + s.wloss[2]) + s.wloss[3];
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(TM_COLS) : "memory");
+  }
+}
+
+// grad[e] = sum over the CTAs c = 0, 1, ... of partial[c][e] (a fixed
+// order); *loss = the same sum of the partial losses.
+__global__ void k_mlp_grad_reduce(const float* __restrict__ partial, const double* __restrict__ partial_loss,
+                                  int nparts, float* __restrict__ grad, double* __restrict__ loss) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < MLP_NPARAM) {
+    float acc = 0.f;
+    for (int c = 0; c < nparts; c++) acc += partial[static_cast<int64_t>(c) * MLP_NPARAM + e];
+    grad[e] = acc;
+  }
+  if (e == 0) {
+    double l = 0.0;
+    for (int c = 0; c < nparts; c++) l += partial_loss[c];
+    *loss = l;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Host-side launchers.
 
-size_t mlp_train_smem() { return sizeof(MlpSmem) + TRAIN_WARPS * sizeof(TrainTile) + MLP_NPARAM * sizeof(float); }
 
+constexpr size_t kTrainTcSmem = sizeof(TrainTc) + 128;
 cudaError_t mlp_setup() {
-  return cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              static_cast<int>(mlp_train_smem()));
+  return cudaFuncSetAttribute(k_mlp_train_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(kTrainTcSmem));
 }
 cudaError_t launch_mlp_pack(const float* P, const MlpDev& m, cudaStream_t st) {
   k_mlp_pack<<<8, 256, 0, st>>>(P, m);
@@ -513,13 +633,23 @@ cudaError_t launch_mlp_infer(const uint32_t* X, float* Y, int64_t n, const MlpDe
   k_mlp_infer<<<grid, TC_THREADS, sizeof(TcSmem), st>>>(X, Y, n, m, err);
   return cudaGetLastError();
 }
-cudaError_t launch_mlp_train(const float* X, const float* T, int64_t n, const MlpDev& m, float* grad, double* loss,
-                             int nsm, cudaStream_t st) {
+// The loss sum and the gradient on the tensor cores: one CTA per SM (at most
+// one per tile), each writing a partial gradient and loss, then their sum in
+// CTA order (the result is the same bit for bit from run to run).  partial:
+// nsm x MLP_NPARAM floats, partial_loss: nsm doubles.
+// idx (nullable, device): sample i is row idx[i] of X and T (nrows rows);
+// without it sample i is row i.
+cudaError_t launch_mlp_train(const float* X, const float* T, const int64_t* idx, int64_t nrows, int64_t n,
+                             const MlpDev& m, float* grad, double* loss, float* partial, double* partial_loss,
+                             int32_t* err, int nsm, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  int64_t tiles = (n + 15) / 16;
-  int grid = static_cast<int>(std::min<int64_t>((tiles + TRAIN_WARPS - 1) / TRAIN_WARPS, static_cast<int64_t>(nsm)));
-  k_mlp_train<<<grid, TRAIN_WARPS * 32, mlp_train_smem(), st>>>(X, T, n, 1.0 / (8.0 * static_cast<double>(n)), m,
-                                                                 grad, loss);
+  const int64_t tiles = (n + TT - 1) / TT;
+  const int grid = static_cast<int>(std::min<int64_t>(tiles, static_cast<int64_t>(nsm)));
+  k_mlp_train_tc<<<grid, TT, kTrainTcSmem, st>>>(X, T, idx, nrows, n, 1.0 / (8.0 * static_cast<double>(n)), m,
+                                                  partial, partial_loss, err);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_mlp_grad_reduce<<<(MLP_NPARAM + 255) / 256, 256, 0, st>>>(partial, partial_loss, grid, grad, loss);
   return cudaGetLastError();
 }
 cudaError_t launch_mlp_adam(float* p, const float* g, float* m1, float* m2, float lr, int step, cudaStream_t st) {
@@ -585,7 +715,11 @@ struct bats_mlp {
   float *X = nullptr, *T = nullptr, *Y = nullptr;
   uint32_t* Xb = nullptr;
   int64_t cap = 0;
-  int32_t* errw = nullptr;  // device error bits of the inference kernel (ERR_TIMEOUT)
+  int32_t* errw = nullptr;  // device error bits of the inference and training kernels (ERR_TIMEOUT)
+  float* partial = nullptr;          // per-CTA partial gradients of a training pass [nsm][NPARAM]
+  double* partial_loss = nullptr;    // and losses [nsm]
+  double* step_loss = nullptr;       // per-step losses of an epoch [step_cap]
+  int64_t step_cap = 0;
 };
 
 namespace {
@@ -631,10 +765,24 @@ int grad_pass(bats_mlp_t* m, const float* X, const float* T, int64_t n) {
   if (rc) return rc;
   if ((rc = copy_in(m, m->X, X, static_cast<size_t>(n) * 40)) || (rc = copy_in(m, m->T, T, static_cast<size_t>(n) * 8)))
     return rc;
-  if (cudaMemsetAsync(m->G, 0, sizeof(float) * MLP_NPARAM, m->stream) != cudaSuccess ||
-      cudaMemsetAsync(m->loss, 0, sizeof(double), m->stream) != cudaSuccess ||
-      launch_mlp_train(m->X, m->T, n, m->w, m->G, m->loss, m->nsm, m->stream) != cudaSuccess)
+  if (launch_mlp_train(m->X, m->T, nullptr, n, n, m->w, m->G, m->loss, m->partial, m->partial_loss, m->errw,
+                       m->nsm, m->stream) != cudaSuccess)
     return BATS_ERR_CUDA;
+  return BATS_OK;
+}
+
+// The error bits of the kernels since the last check (cleared): a bounded
+// tensor-core wait that ran out is BATS_ERR_TIMEOUT, a sample index outside
+// the training set BATS_ERR_INVALID_ARG.
+int mlp_check_err(bats_mlp_t* m) {
+  int32_t eb = 0;
+  if (cudaMemcpyAsync(&eb, m->errw, sizeof(int32_t), cudaMemcpyDeviceToHost, m->stream) != cudaSuccess ||
+      cudaStreamSynchronize(m->stream) != cudaSuccess)
+    return BATS_ERR_CUDA;
+  if (eb) {
+    cudaMemsetAsync(m->errw, 0, sizeof(int32_t), m->stream);
+    return (eb & ERR_TIMEOUT) ? BATS_ERR_TIMEOUT : BATS_ERR_INVALID_ARG;
+  }
   return BATS_OK;
 }
 
@@ -659,6 +807,8 @@ int bats_mlp_create(const float* params, uint64_t seed, void* cuda_stream, bats_
   if (e == cudaSuccess) e = cudaMalloc(&m->loss, sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&m->errw, sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMemset(m->errw, 0, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&m->partial, sizeof(float) * MLP_NPARAM * m->nsm);
+  if (e == cudaSuccess) e = cudaMalloc(&m->partial_loss, sizeof(double) * m->nsm);
   if (e == cudaSuccess) e = mlp_alloc(&m->w);
   if (e != cudaSuccess) {
     bats_mlp_destroy(m);
@@ -689,6 +839,9 @@ void bats_mlp_destroy(bats_mlp_t* m) {
   cudaFree(m->P);
   cudaFree(m->loss);
   cudaFree(m->errw);
+  cudaFree(m->partial);
+  cudaFree(m->partial_loss);
+  cudaFree(m->step_loss);
   cudaFree(m->X);
   cudaFree(m->T);
   cudaFree(m->Y);
@@ -757,7 +910,7 @@ int bats_mlp_forward(bats_mlp_t* m, const float* X, int64_t n, float* Y) {
   if (e != cudaSuccess) return BATS_ERR_CUDA;
   if (eb) {
     cudaMemsetAsync(m->errw, 0, sizeof(int32_t), m->stream);
-    return BATS_ERR_TIMEOUT;
+    return (eb & ERR_TIMEOUT) ? BATS_ERR_TIMEOUT : BATS_ERR_INVALID_ARG;
   }
   return BATS_OK;
 }
@@ -773,6 +926,7 @@ int bats_mlp_loss_grad(bats_mlp_t* m, const float* X, const float* T, int64_t n,
                         dev_ptr(grad) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, m->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
   if (e != cudaSuccess) return BATS_ERR_CUDA;
+  if ((rc = mlp_check_err(m))) return rc;
   if (loss) *loss = ls / (8.0 * static_cast<double>(n));
   return BATS_OK;
 }
@@ -790,7 +944,47 @@ int bats_mlp_train_step(bats_mlp_t* m, const float* X, const float* T, int64_t n
     if (cudaMemcpyAsync(&ls, m->loss, sizeof(double), cudaMemcpyDeviceToHost, m->stream) != cudaSuccess ||
         cudaStreamSynchronize(m->stream) != cudaSuccess)
       return BATS_ERR_CUDA;
+    if ((rc = mlp_check_err(m))) return rc;
     *loss = ls / (8.0 * static_cast<double>(n));
+  }
+  return BATS_OK;
+}
+
+int bats_mlp_train_epoch(bats_mlp_t* m, const float* X, const float* T, int64_t n, const int64_t* perm,
+                         int64_t n_perm, int64_t batch, float lr, double* mean_loss) {
+  if (!m || !X || !T || !perm || n <= 0 || batch < 1 || n_perm < batch || !(lr >= 0.f)) return BATS_ERR_INVALID_ARG;
+  if (!dev_ptr(X) || !dev_ptr(T) || !dev_ptr(perm)) return BATS_ERR_INVALID_ARG;
+  const int64_t steps = n_perm / batch;
+  if (steps > m->step_cap) {
+    cudaFree(m->step_loss);
+    m->step_loss = nullptr;
+    m->step_cap = 0;
+    if (cudaMalloc(&m->step_loss, sizeof(double) * steps) != cudaSuccess) {
+      cudaGetLastError();
+      return BATS_ERR_OUT_OF_MEMORY;
+    }
+    m->step_cap = steps;
+  }
+  for (int64_t s = 0; s < steps; s++) {
+    if (launch_mlp_train(X, T, perm + s * batch, n, batch, m->w, m->G, m->step_loss + s, m->partial,
+                         m->partial_loss, m->errw, m->nsm, m->stream) != cudaSuccess)
+      return BATS_ERR_CUDA;
+    m->step++;
+    if (launch_mlp_adam(m->P, m->G, m->M1, m->M2, lr, m->step, m->stream) != cudaSuccess ||
+        launch_mlp_pack(m->P, m->w, m->stream) != cudaSuccess)
+      return BATS_ERR_CUDA;
+  }
+  std::vector<double> ls(static_cast<size_t>(steps));
+  if (cudaMemcpyAsync(ls.data(), m->step_loss, sizeof(double) * steps, cudaMemcpyDeviceToHost, m->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(m->stream) != cudaSuccess)
+    return BATS_ERR_CUDA;
+  int rc = mlp_check_err(m);
+  if (rc) return rc;
+  if (mean_loss) {
+    double acc = 0.0;
+    for (double v : ls) acc += v / (8.0 * static_cast<double>(batch));
+    *mean_loss = acc / static_cast<double>(steps);
   }
   return BATS_OK;
 }

@@ -14,7 +14,8 @@ network's target is (target - Rusanov) rotated into the face frame and divided
 by the flux units of the face (rho_ref c_ref, rho_ref c_ref^2,
 sqrt(rho_ref) c_ref^2, rho_ref c_ref^3).
 
-Training: Adam on the GPU (bats_mlp_train_step), minibatches of face samples.
+Training: Adam on the GPU, minibatches of face samples; the pairs stay on the
+device and each epoch is one library call (bats_mlp_train_epoch).
 
 Evaluation: the coarse grid with and without the network against the fine run
 restricted to the coarse grid, at the same time and fixed dt; and (evaluate_4x)
@@ -172,18 +173,21 @@ def make_pairs(variants, snapshots=(6, 14), cfl=0.8, keep=0.3, seed=0, precision
 
 
 def train(X, Y, epochs=4, batch=8192, lr=1e-3, seed=0, log=None):
-    """Adam on the GPU; returns (params float32, per-epoch mean loss)."""
+    """Adam on the GPU; returns (params float32, per-epoch mean loss).  The
+    minibatches of an epoch are consecutive slices of a seeded permutation of
+    the samples (a ragged rest is left out)."""
+    import torch
     rng = np.random.default_rng(seed)
     m = B.Mlp(seed=seed)
     hist = []
     n = X.shape[0]
+    Xd = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).cuda()
+    Yd = torch.from_numpy(np.ascontiguousarray(Y, dtype=np.float32)).cuda()
+    torch.cuda.synchronize()
     for ep in range(epochs):
-        perm = rng.permutation(n)
-        losses = []
-        for s in range(0, n - batch + 1, batch):
-            idx = perm[s:s + batch]
-            losses.append(m.train_step(np.ascontiguousarray(X[idx]), np.ascontiguousarray(Y[idx]), lr))
-        hist.append(float(np.mean(losses)))
+        perm = torch.from_numpy(rng.permutation(n).astype(np.int64)).cuda()
+        torch.cuda.synchronize()
+        hist.append(m.train_epoch(Xd, Yd, perm, batch, lr))
         if log:
             log("epoch %d loss %.4e" % (ep, hist[-1]))
     P = m.get_params()

@@ -108,6 +108,92 @@ def test_network_gradient_matches_oracle(B):
         assert _relnorm(g[a:b], go[a:b]) <= 3e-2, (a, b)
 
 
+@pytest.mark.parametrize("n", [1, 129, 5000])
+def test_gradient_ragged_batches_match_oracle(B, n):
+    """The trainer runs 128-row tiles, one CTA per SM: a batch of one row, a
+    ragged last tile and a batch spread over many CTAs all give the oracle's
+    loss and gradient."""
+    P = _net(21)
+    rng = np.random.default_rng(100 + n)
+    X = bf16(rng.normal(size=(n, 40)))
+    T = rng.normal(size=(n, 8)).astype(np.float32)
+    m = B.Mlp(P)
+    loss, g = m.loss_grad(X, T)
+    m.close()
+    lo, go = O.mlp_loss_grad(P.astype(np.float64), X.astype(np.float64), T.astype(np.float64))
+    assert loss == pytest.approx(lo, rel=1e-2)
+    assert _relnorm(g, go) <= 2e-2
+
+
+@pytest.mark.parametrize("n", [129, 300001])
+def test_gradient_is_the_same_bit_for_bit_run_to_run(B, n):
+    """Per-CTA partial sums are added in CTA order, never by atomics: the loss
+    and gradient of a batch do not change from call to call or handle to
+    handle."""
+    P = _net(23)
+    rng = np.random.default_rng(200 + n)
+    X = bf16(rng.normal(size=(n, 40)))
+    T = rng.normal(size=(n, 8)).astype(np.float32)
+    m = B.Mlp(P)
+    l1, g1 = m.loss_grad(X, T)
+    l2, g2 = m.loss_grad(X, T)
+    m.close()
+    m = B.Mlp(P)
+    l3, g3 = m.loss_grad(X, T)
+    m.close()
+    assert l1 == l2 == l3
+    assert np.array_equal(g1.view(np.uint32), g2.view(np.uint32))
+    assert np.array_equal(g1.view(np.uint32), g3.view(np.uint32))
+
+
+def test_train_epoch_equals_its_steps_bitwise(B):
+    """An epoch on device-resident samples (the minibatch rows gathered by
+    index inside the trainer) gives the weights of the same minibatches
+    copied and stepped one by one, bit for bit."""
+    import torch
+    rng = np.random.default_rng(31)
+    n, batch = 5000, 1024
+    X = bf16(rng.normal(size=(n, 40)))
+    T = (0.1 * rng.normal(size=(n, 8))).astype(np.float32)
+    perm = rng.permutation(n).astype(np.int64)
+    a, b = B.Mlp(seed=3), B.Mlp(seed=3)
+    la = a.train_epoch(torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda(), torch.from_numpy(perm).cuda(),
+                       batch, 1e-3)
+    lb = [b.train_step(np.ascontiguousarray(X[perm[s:s + batch]]), np.ascontiguousarray(T[perm[s:s + batch]]), 1e-3)
+          for s in range(0, n - batch + 1, batch)]
+    assert la == pytest.approx(float(np.mean(lb)), rel=1e-12)
+    assert np.array_equal(a.get_params().view(np.uint32), b.get_params().view(np.uint32))
+    a.close()
+    b.close()
+
+
+def test_train_epoch_rejects_bad_inputs(B):
+    """Host buffers, a batch larger than the permutation and an index outside
+    the sample set are refused (the index is checked before any access)."""
+    import torch
+    rng = np.random.default_rng(32)
+    n = 300
+    X = bf16(rng.normal(size=(n, 40)))
+    T = rng.normal(size=(n, 8)).astype(np.float32)
+    Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    perm = torch.arange(n, dtype=torch.int64).cuda()
+    m = B.Mlp(seed=4)
+    with pytest.raises(B.BatsError) as e:
+        m.train_epoch(X, T, perm.cpu().numpy(), 100, 1e-3)
+    assert e.value.code == B.BATS_ERR_INVALID_ARG
+    with pytest.raises(B.BatsError) as e:
+        m.train_epoch(Xd, Td, perm, n + 1, 1e-3)
+    assert e.value.code == B.BATS_ERR_INVALID_ARG
+    bad = perm.clone()
+    bad[17] = n
+    with pytest.raises(B.BatsError) as e:
+        m.train_epoch(Xd, Td, bad, 100, 1e-3)
+    assert e.value.code == B.BATS_ERR_INVALID_ARG
+    # the handle is still usable
+    assert np.isfinite(m.train_epoch(Xd, Td, perm, 100, 1e-3))
+    m.close()
+
+
 def test_training_fits_a_teacher_network(B):
     teacher = _net(5, scale=0.2)
     rng = np.random.default_rng(6)
@@ -273,20 +359,21 @@ def test_learned_last_stage_only_matches_oracle(B, precision):
 
 
 def test_gelu_pair_within_its_bound(B):
-    """The kernels' GELU (two values per tanh.approx.bf16x2, BF16 result)
+    """The kernels' GELU (two values per tanh.approx.f16x2, BF16 result)
     against the exact tanh-form GELU: |gelu2 - gelu| <= 0.5 |x| |dt| + the
-    final BF16 rounding (2^-8 of the value, 1e-30 floor), with |dt| <= 9e-3:
-    the BF16 rounding of the tanh argument moves tanh by at most
-    max_u |u| sech^2(u) 2^-9 < 9e-4, and the BF16 result of tanh is allowed
-    two BF16 units (2 x 2^-8) near |t| = 1.  Over [-12, 12] and at the tails."""
+    final BF16 rounding (2^-8 of the value, 1e-30 floor), with |dt| <= 2e-3:
+    the FP16 rounding of the tanh argument moves tanh by at most
+    max_u |u| sech^2(u) 2^-11 < 2.2e-4, and the FP16 result of tanh is
+    allowed a few units of 2^-11 near |t| = 1.  Over [-12, 12] and at the
+    tails (beyond the FP16 range the argument is +-inf, tanh +-1)."""
     x = np.concatenate([np.linspace(-12, 12, 200001), [-40.0, -7.5, 0.0, 1e-3, -1e-3, 7.5, 40.0]]).astype(np.float32)
     y = B.bats_debug_gelu(x)
     xd = x.astype(np.float64)
     exact = 0.5 * xd * (1 + np.tanh(0.7978845608028654 * (xd + 0.044715 * xd ** 3)))
     err = np.abs(y - exact)
-    bound = 0.5 * np.abs(xd) * 9e-3 + np.abs(exact) * 2.0 ** -8 + 1e-30
+    bound = 0.5 * np.abs(xd) * 2e-3 + np.abs(exact) * 2.0 ** -8 + 1e-30
     print("GELU pair: largest error / bound", float((err / bound).max()), "at x =", float(x[np.argmax(err / bound)]),
           "largest error", float(err.max()))
     assert np.all(err <= bound), (float((err / bound).max()), float(x[np.argmax(err / bound)]))
     assert np.all(y[x >= 6] == pytest.approx(x[x >= 6].astype(np.float64), rel=2 ** -8))
-    assert np.all(np.abs(y[x <= -6]) <= 0.5 * np.abs(xd[x <= -6]) * 9e-3)
+    assert np.all(np.abs(y[x <= -6]) <= 0.5 * np.abs(xd[x <= -6]) * 2e-3)
