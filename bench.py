@@ -60,6 +60,15 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+def _bf16_peak():
+    p = os.path.join(HERE, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops"]), "measured (burst)"
+    return 1900.0, "fallback"
+
+
 def _kernel_sha():
     with open(os.path.join(HERE, "paper_2501_06717_gb300", "csrc", "bats_stage.cu"), "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()
@@ -255,6 +264,49 @@ def learned_form_summary(stream, steps=32):
 
 
 # --------------------------------------------------------------------------
+# The network alone on the tensor cores
+
+MLP_FLOPS_PER_ROW = 2 * (40 * 64 + 64 * 64 + 64 * 8)   # 14,336 algorithmic
+MLP_BYTES_PER_ROW = 48 * 2 + 8 * 4                      # BF16 inputs (padded to 48) + FP32 outputs
+
+
+def mlp_inference_summary(stream, rows=2_000_000, reps=20):
+    """k_mlp_infer over `rows` face rows of N(0, 1) BF16 inputs (192 MB of
+    inputs, larger than L2) with a seeded network, timed with CUDA events on
+    the handle's stream over `reps` back-to-back launches."""
+    import torch
+    from paper_2501_06717_gb300 import bats
+    g = torch.Generator(device="cuda").manual_seed(5)
+    Xh = torch.zeros(rows, 48, dtype=torch.bfloat16, device="cuda")
+    Xh[:, :40] = torch.randn(rows, 40, device="cuda", generator=g).to(torch.bfloat16)
+    Xb = Xh.view(torch.int32)
+    Y = torch.empty(rows, 8, device="cuda")
+    P = (0.3 * np.random.default_rng(6).normal(size=bats.BATS_MLP_NPARAM)).astype(np.float32)
+    m = bats.Mlp(P, stream=stream)
+    torch.cuda.synchronize()
+    for _ in range(3):
+        m.forward_bf16(Xb, Y)
+    m.sync()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        m.forward_bf16(Xb, Y)
+    e1.record(stream)
+    m.sync()
+    ms = e0.elapsed_time(e1) / reps
+    m.close()
+    peak, how = _bf16_peak()
+    hbm, hbm_how = _peaks()
+    tf = rows * MLP_FLOPS_PER_ROW / (ms * 1e-3) / 1e12
+    gbs = rows * MLP_BYTES_PER_ROW / (ms * 1e-3) / 1e9
+    return {"kernel": "k_mlp_infer", "rows": rows, "ms_per_launch": ms, "rows_per_s": rows / (ms * 1e-3),
+            "flops_per_row": MLP_FLOPS_PER_ROW, "tflops": tf, "bf16_peak_tflops": peak, "peak_kind": how,
+            "frac_bf16_peak": tf / peak, "bytes_per_row": MLP_BYTES_PER_ROW, "gbs": gbs,
+            "frac_hbm": gbs / hbm, "hbm_peak_kind": hbm_how, "inputs": "larger than L2"}
+
+
+# --------------------------------------------------------------------------
 # The other paper-shaped grids (one grid each)
 
 
@@ -355,6 +407,7 @@ def main():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-form summary")
     ap.add_argument("--learned-only", action="store_true", help="only the learned-form summary (profiling)")
     ap.add_argument("--no-others", action="store_true", help="skip the other paper-shaped grids")
+    ap.add_argument("--mlp-only", action="store_true", help="only the standalone network inference (profiling)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -366,6 +419,11 @@ def main():
         return run_reference(args, rank, world)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
+    if args.mlp_only:
+        import torch
+        torch.cuda.set_device(local)
+        print(json.dumps({"mlp_inference": mlp_inference_summary(torch.cuda.Stream())}), flush=True)
+        return 0
     if args.learned_only:
         import torch
         torch.cuda.set_device(local)
@@ -491,6 +549,7 @@ def main():
     learned = None
     if rank == 0 and world == 1 and not args.no_learned and args.workload == "batched":
         learned = learned_form_summary(stream)
+        learned["mlp_inference_2M_rows"] = mlp_inference_summary(stream)
     others = None
     if rank == 0 and world == 1 and not args.no_others and args.workload == "batched":
         others = other_workloads(stream)

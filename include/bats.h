@@ -266,10 +266,13 @@ int bats_debug_check_conversions(const float* f, const double* d, int n, double*
 
 /* Self-check of the network's activation (the learned correction's GELU,
  * tanh form, Hendrycks & Gimpel): y[i] = the kernels' GELU of x[i] as they
- * compute it for the hidden activations -- two values at a time, the tanh by
- * one tanh.approx.bf16x2, the result rounded to BF16.  n host values;
- * allocates and frees its own device buffers. */
-int bats_debug_gelu(const float* x, int n, float* y);
+ * compute it for the hidden activations -- two values at a time in packed
+ * FP32 around tanh.approx.f32, the result rounded to BF16.  variant 0: the
+ * fused learned stage and the trainer; variant 1: the inference kernel,
+ * which rounds twice the GELU (its next layer's weights halved), returned
+ * halved (exact).  n host values; allocates and frees its own device
+ * buffers; BATS_ERR_INVALID_ARG for another variant. */
+int bats_debug_gelu(const float* x, int n, int variant, float* y);
 
 /* ---- learned flux correction (a small MLP on tensor cores) -------------
  * Network: 40 inputs -> 64 -> 64 -> 8 outputs, tanh-form GELU after the two
@@ -321,6 +324,17 @@ int bats_mlp_get_params(bats_mlp_t* m, float* params);
  * accumulation in tensor memory).  BATS_ERR_TIMEOUT if a bounded device wait
  * ran out (the handle stays usable). */
 int bats_mlp_forward(bats_mlp_t* m, const float* X, int64_t n, float* Y);
+/* Y (n x 8 floats) = network(Xb), Xb the inputs already rounded to BF16:
+ * n rows of 24 words, word j holding inputs 2j (low half) and 2j + 1 (high
+ * half), words 20..23 zero -- the layout bats_debug_face_data's inputs take
+ * once rounded.  Device pointers, 16-byte aligned, else
+ * BATS_ERR_INVALID_ARG.  Queued on the handle's stream without a
+ * synchronisation; bats_mlp_sync reports its errors. */
+int bats_mlp_forward_bf16(bats_mlp_t* m, const uint32_t* Xb, int64_t n, float* Y);
+/* Waits for the handle's stream; BATS_ERR_TIMEOUT if a bounded device wait of
+ * a kernel queued since the last check ran out, BATS_ERR_INVALID_ARG for a
+ * sample index outside its training set (both cleared). */
+int bats_mlp_sync(bats_mlp_t* m);
 /* Loss L = (1/(8n)) sum (y - t)^2 over n samples (X n x 40, T n x 8) and its
  * gradient (grad nullable, BATS_MLP_NPARAM floats); inputs are rounded to
  * BF16 as in inference.  Forward and backward products run on the tensor

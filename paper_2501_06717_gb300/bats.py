@@ -114,7 +114,7 @@ def lib():
     L.bats_get_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     L.bats_get_fallbacks.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     L.bats_debug_check_conversions.argtypes = [vp, vp, ctypes.c_int, vp, vp]
-    L.bats_debug_gelu.argtypes = [vp, ctypes.c_int, vp]
+    L.bats_debug_gelu.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp]
     L.bats_set_mlp.argtypes = [vp, vp]
     L.bats_debug_face_data.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, vp, vp, ctypes.c_size_t]
     L.bats_mlp_create.argtypes = [vp, ctypes.c_uint64, vp, ctypes.POINTER(vp)]
@@ -123,6 +123,8 @@ def lib():
     L.bats_mlp_set_params.argtypes = [vp, vp]
     L.bats_mlp_get_params.argtypes = [vp, vp]
     L.bats_mlp_forward.argtypes = [vp, vp, ctypes.c_int64, vp]
+    L.bats_mlp_forward_bf16.argtypes = [vp, vp, ctypes.c_int64, vp]
+    L.bats_mlp_sync.argtypes = [vp]
     L.bats_mlp_loss_grad.argtypes = [vp, vp, vp, ctypes.c_int64, vp, ctypes.POINTER(ctypes.c_double)]
     L.bats_mlp_train_step.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.c_float, ctypes.POINTER(ctypes.c_double)]
     L.bats_mlp_train_epoch.argtypes = [vp, vp, vp, ctypes.c_int64, vp, ctypes.c_int64, ctypes.c_int64,
@@ -344,10 +346,10 @@ def bats_debug_check_conversions(f, d):
     return o1, o2
 
 
-def bats_debug_gelu(x):
+def bats_debug_gelu(x, variant=0):
     x = np.ascontiguousarray(x, dtype=np.float32)
     y = np.zeros_like(x)
-    rc = lib().bats_debug_gelu(x.ctypes.data, int(x.size), y.ctypes.data)
+    rc = lib().bats_debug_gelu(x.ctypes.data, int(x.size), int(variant), y.ctypes.data)
     if rc != BATS_OK:
         raise BatsError(rc, "GELU check failed")
     return y
@@ -431,6 +433,18 @@ class Mlp:
         Y = np.zeros((n, 8), np.float32)
         self._rc(lib().bats_mlp_forward(self.h, px, n, Y.ctypes.data), "forward")
         return Y
+
+    def forward_bf16(self, Xb, Y):
+        """Queues Y = network(Xb) on the handle's stream: Xb (n x 24 int32
+        words of BF16 pairs) and Y (n x 8 float32) device tensors."""
+        px, n = _ptr_and_size(Xb)
+        py, ny = _ptr_and_size(Y)
+        if n % 24 or ny != (n // 24) * 8:
+            raise ValueError("Xb must be n x 24 words and Y n x 8 floats")
+        self._rc(lib().bats_mlp_forward_bf16(self.h, px, n // 24, py), "forward_bf16")
+
+    def sync(self):
+        self._rc(lib().bats_mlp_sync(self.h), "sync")
 
     def loss_grad(self, X, T):
         X = X if hasattr(X, "data_ptr") else np.ascontiguousarray(X, dtype=np.float32)

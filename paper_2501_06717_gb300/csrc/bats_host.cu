@@ -45,6 +45,7 @@ cudaError_t launch_fp64_fma_rate(double* out, int ctas, int iters, cudaStream_t 
 cudaError_t read_index_flag(int32_t* out);
 cudaError_t launch_debug_wait_timeout(int32_t* err, cudaStream_t st);
 cudaError_t mlp_alloc(MlpDev* w);
+cudaError_t mlp_setup();
 void mlp_free(MlpDev* w);
 cudaError_t launch_mlp_pack(const float* P, const MlpDev& m, cudaStream_t st);
 cudaError_t launch_mlp_infer(const uint32_t* X, float* Y, int64_t n, const MlpDev& m, int nsm, int32_t* err,
@@ -1193,6 +1194,7 @@ int bats_set_mlp(bats_t* h, const float* params) {
         (rc = dev_alloc(h, &h->Yb, nf * 8)))
       return rc;
     CK(h, mlp_alloc(&h->mlp));
+    CK(h, mlp_setup());
   }
   CK(h, cudaMemcpyAsync(h->mlp_params, params, sizeof(float) * MLP_NPARAM,
                         is_device_ptr(params) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));

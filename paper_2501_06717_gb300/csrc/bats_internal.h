@@ -85,6 +85,12 @@ constexpr int MLP_NPARAM = MLP_H * MLP_IN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_
 struct MlpDev {
   uint32_t *w1, *w2, *w3, *w2t, *w3t;  // [64][24], [64][32], [8][32], [64][32], [64][8]
   float *b1, *b2, *b3;
+  // the inference kernel's layouts, biases folded into the products: each
+  // row's bias as a BF16 pair (hi, lo = b - hi) at K 40, 41 (layer 1, K =
+  // 48) or 64, 65 (layers 2 and 3, K = 80, weights halved: that kernel's
+  // hidden activations are twice the GELU).  w1b [64][24], w2b [64][40],
+  // w3b [16][40] (rows 8..15 zero)
+  uint32_t *w1b, *w2b, *w3b;
 };
 
 // Refluxing: one coarse face that borders a refined region.  The register

@@ -30,162 +30,307 @@
 
 namespace batsk {
 
-constexpr int TC_TILE = 128;             // rows per tile (MMA M = tensor-memory lanes)
-constexpr int TC_TMEM_COLS = 64;         // one FP32 accumulator of N = 64 (reused by all three layers)
+constexpr int TC_TILE = 128;        // rows per tile (MMA M = tensor-memory lanes)
+constexpr int TC_STREAMS = 4;       // tiles in flight per CTA (one CTA per SM)
+constexpr int TC_THREADS = 32 * (4 * TC_STREAMS + 1);  // four warps per stream + the MMA warp
+constexpr int TC_TMEM_COLS = 512;   // two regions of 64 columns per stream
+constexpr uint32_t SBO_K80 = 1280;  // 16 bytes x K = 80
 struct TcSmem {
-  alignas(128) uint8_t x[TC_TILE * 96];  // X tile, K = 48
-  alignas(128) uint8_t h[TC_TILE * 128]; // hidden activations, K = 64 (H1, then H2)
-  alignas(128) uint8_t w1[64 * 96];      // B of layer 1: N = 64, K = 48
-  alignas(128) uint8_t w2[64 * 128];     // B of layer 2: N = 64, K = 64
-  alignas(128) uint8_t w3[16 * 128];     // B of layer 3: N = 16 (8 outputs, 8 zero rows), K = 64
-  float b1[64], b2[64], b3[8];
-  uint64_t bar;
+  alignas(128) uint8_t w1[64 * 96];   // B of layer 1: N = 64, K = 48
+  alignas(128) uint8_t w2[64 * 160];  // B of layer 2: N = 64, K = 80 (weights halved)
+  alignas(128) uint8_t w3[16 * 160];  // B of layer 3: N = 16 (8 outputs, 8 zero rows), K = 80 (halved)
+  uint64_t opready[TC_STREAMS];       // 128 arrivals: the stream's operand is in tensor memory
+  uint64_t accready[TC_STREAMS];      // tcgen05.commit: the stream's layer is in tensor memory
   uint32_t tmem;
 };
 
-// Bias, GELU and BF16 rounding of 32 accumulator columns c0..c0+31 of this
-// thread's lane (at taddr) into row `row` of the canonical K = 64 tile h.
-__device__ __forceinline__ void tc_hidden_cols(uint32_t taddr, const float* bias, uint8_t* h, int row, int c0) {
+__device__ __forceinline__ void mbar_init_count(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc_saddr(bar)), "r"(count) : "memory");
+}
+// Non-blocking test of an mbarrier phase (mbarrier.try_wait may suspend the
+// thread for a while when the phase is not complete: a thread serving
+// several barriers polls with this instead).
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(tc_saddr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// true in one lane of the (converged) warp
+__device__ __forceinline__ bool elect_one() {
+  uint32_t pred;
+  asm volatile(
+      "{\n .reg .b32 r;\n .reg .pred p;\n elect.sync r|p, 0xffffffff;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(pred));
+  return pred != 0;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc_saddr(bar)) : "memory");
+}
+// D[tmem] (+)= A B^T for one K = 16 slice, A (M = 128 rows = lanes, K packed
+// two BF16 per 32-bit column, 8 columns per slice) in tensor memory
+__device__ __forceinline__ void umma_bf16_ts(uint32_t dtmem, uint32_t atmem, uint64_t bdesc, uint32_t idesc,
+                                             uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(dtmem),
+      "r"(atmem), "l"(bdesc), "r"(idesc), "r"(accum)
+      : "memory");
+}
+// 32 consecutive FP32 columns of this thread's tensor-memory lane, the wait
+// for the load in the same statement.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
+}
+// 16 + 8 (x24) or 32 + 8 (x40) words into consecutive columns of this
+// thread's lane, waiting for the stores
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* r) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* r) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(r[0]),
+               "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+               : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// Twice the GELU of the 64 accumulator columns of this thread's lane at taddr
+// (the biases came in through the products), as 32 BF16 pairs written back
+// over the first 32 of those columns, then the bias column pair (ones) and
+// zeros: the next layer's A, K = 80.
+__device__ __forceinline__ void tc_hidden_row(uint32_t taddr) {
+  uint32_t h[40];
 #pragma unroll
   for (int q = 0; q < 2; q++) {
-    float v[16];
-    tmem_ld16(taddr + 16 * q, v);
+    float z[32];
+    tmem_ld32(taddr + 32 * q, z);
 #pragma unroll
-    for (int c = 0; c < 2; c++) {
-      uint4 o;
-      const float* b = bias + c0 + 16 * q + 8 * c;
-      const float* z = v + 8 * c;
-      o.x = gelu2_pack(z[0] + b[0], z[1] + b[1]);
-      o.y = gelu2_pack(z[2] + b[2], z[3] + b[3]);
-      o.z = gelu2_pack(z[4] + b[4], z[5] + b[5]);
-      o.w = gelu2_pack(z[6] + b[6], z[7] + b[7]);
-      *reinterpret_cast<uint4*>(h + cm_off(row, c0 / 8 + 2 * q + c, SBO_K64)) = o;
-    }
+    for (int c = 0; c < 16; c++) h[16 * q + c] = gelu2x_pack(z[2 * c], z[2 * c + 1]);
   }
+  h[32] = pack_bf16(1.f, 1.f);
+#pragma unroll
+  for (int c = 33; c < 40; c++) h[c] = 0u;
+  tmem_st16(taddr, h);
+  tmem_st16(taddr + 16, h + 16);
+  tmem_st8(taddr + 32, h + 32);
+  tmem_st_wait();
 }
 
-// Y[n][8] = MLP(X[n][48] BF16), 256 threads per CTA, persistent over tiles.
-// Warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (the tile rows it may
-// access) and accumulator columns 32 (w / 4) .. + 31, so two warps share each
-// row's epilogue.  Thread 0 issues the MMAs; every wait is bounded
-// (ERR_TIMEOUT in err), after which the CTA waits once more for its MMAs,
-// frees its tensor memory and returns.
-constexpr int TC_THREADS = 256;
-__global__ void __launch_bounds__(TC_THREADS, 4) k_mlp_infer(const uint32_t* __restrict__ X, float* __restrict__ Y,
+// Y[n][8] = MLP(X[n][48] BF16), one persistent CTA per SM, warp specialised:
+// TC_STREAMS streams of four warps, each stream with a tile of its own in
+// flight (the CTA's tiles k = s, s + TC_STREAMS, ..), thread t of the stream
+// owning row t (tensor-memory lane t; warp w reads and writes lanes
+// 32 (w % 4) ..), and one warp issuing every MMA.  Every A operand lives in
+// tensor memory, written by the stream's threads (tcgen05.st): the inputs,
+// then each layer's activations over the accumulator they came from, so
+// shared memory carries only the weights.  A stream's two 64-column regions
+// alternate: layer 1 reads X from region 1 into region 0, layer 2 reads H1
+// (region 0) into region 1, layer 3 reads H2 (region 1) into region 0.  A
+// stream hands its operand to the MMA warp through opready (all 128 threads
+// arrive) and gets the layer back through accready (tcgen05.commit), so no
+// stream waits for another.  The biases ride in the products (ones in the
+// bias columns, the bias pairs in the weights); the hidden activations are
+// twice the GELU (the next layer's weights halved), a hidden pair costing
+// one packed-FP32 chain around two tanh.approx.f32.  Every wait is bounded
+// (ERR_TIMEOUT in err); a stream whose wait ran out stops, the MMA warp
+// stops once no stream has moved for the same time and waits once more for
+// its MMAs in flight, and the CTA frees its tensor memory and returns.
+__global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_infer(const uint32_t* __restrict__ X, float* __restrict__ Y,
                                                              int64_t n, MlpDev m, int32_t* err) {
   extern __shared__ __align__(128) unsigned char tc_smem_raw[];
-  TcSmem& s = *reinterpret_cast<TcSmem*>(tc_smem_raw);
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int lg = warp & 3, ch = warp >> 2;   // lane group, column half
-  const int trow = 32 * lg + (tid & 31);     // the tile row of this thread's lane
-  // weights into the canonical layouts (16-byte chunks), biases
-  for (int e = tid; e < 64 * 6; e += TC_THREADS) {
+  TcSmem& s = *reinterpret_cast<TcSmem*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 127) & ~uintptr_t(127));
+  const int t = threadIdx.x, warp = t >> 5;
+  constexpr int MMA_WARP = 4 * TC_STREAMS;
+  // weights into the canonical layouts (16-byte chunks)
+  for (int e = t; e < 64 * 6; e += TC_THREADS) {
     const int r = e / 6, kc = e % 6;
-    *reinterpret_cast<uint4*>(s.w1 + cm_off(r, kc, SBO_K48)) = *reinterpret_cast<const uint4*>(m.w1 + r * 24 + kc * 4);
+    *reinterpret_cast<uint4*>(s.w1 + cm_off(r, kc, SBO_K48)) = *reinterpret_cast<const uint4*>(m.w1b + r * 24 + kc * 4);
   }
-  for (int e = tid; e < 64 * 8; e += TC_THREADS) {
-    const int r = e / 8, kc = e % 8;
-    *reinterpret_cast<uint4*>(s.w2 + cm_off(r, kc, SBO_K64)) = *reinterpret_cast<const uint4*>(m.w2 + r * 32 + kc * 4);
+  for (int e = t; e < 64 * 10; e += TC_THREADS) {
+    const int r = e / 10, kc = e % 10;
+    *reinterpret_cast<uint4*>(s.w2 + cm_off(r, kc, SBO_K80)) = *reinterpret_cast<const uint4*>(m.w2b + r * 40 + kc * 4);
   }
-  for (int e = tid; e < 16 * 8; e += TC_THREADS) {
-    const int r = e / 8, kc = e % 8;
-    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
-    *reinterpret_cast<uint4*>(s.w3 + cm_off(r, kc, SBO_K64)) =
-        r < 8 ? *reinterpret_cast<const uint4*>(m.w3 + r * 32 + kc * 4) : z;
+  for (int e = t; e < 16 * 10; e += TC_THREADS) {
+    const int r = e / 10, kc = e % 10;
+    *reinterpret_cast<uint4*>(s.w3 + cm_off(r, kc, SBO_K80)) = *reinterpret_cast<const uint4*>(m.w3b + r * 40 + kc * 4);
   }
-  if (tid < 64) {
-    s.b1[tid] = m.b1[tid];
-    s.b2[tid] = m.b2[tid];
-  }
-  if (tid < 8) s.b3[tid] = m.b3[tid];
-  if (warp == 0) {
+  if (warp == MMA_WARP) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_saddr(&s.tmem)),
                  "r"(TC_TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  if (tid == 0) mbar_init_tc(&s.bar);
+  if (t == 0) {
+    for (int q = 0; q < TC_STREAMS; q++) {
+      mbar_init_count(&s.opready[q], TC_TILE);
+      mbar_init_count(&s.accready[q], 1);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
   proxy_fence_smem();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = s.tmem;
-  const uint32_t tlanes = tmem + (static_cast<uint32_t>(32 * lg) << 16);  // this warp's 32 lanes
-  const uint32_t xs = tc_saddr(s.x), hs = tc_saddr(s.h);
-  const uint32_t w1s = tc_saddr(s.w1), w2s = tc_saddr(s.w2), w3s = tc_saddr(s.w3);
-  constexpr uint32_t ID64 = umma_idesc_bf16(TC_TILE, 64), ID16 = umma_idesc_bf16(TC_TILE, 16);
-  uint32_t phase = 0;
-  bool failed = false;
   const int64_t ntiles = (n + TC_TILE - 1) / TC_TILE;
-  // input: thread tid carries half (three 16-byte chunks) of row tid % 128,
-  // loaded one tile ahead (zeros past n)
-  const int xr = tid & (TC_TILE - 1), xk0 = 3 * (tid / TC_TILE);
-  auto load_part = [&](int64_t r, uint4 xv[3]) {
+  auto tile_of = [&](int64_t k) { return static_cast<int64_t>(blockIdx.x) + k * gridDim.x; };
+
+  if (warp == MMA_WARP) {
+    // the whole warp polls and builds the descriptors (warp-uniform values),
+    // one elected lane issues
+    const uint64_t bd1 = umma_sdesc(tc_saddr(s.w1), 128, SBO_K48), bd2 = umma_sdesc(tc_saddr(s.w2), 128, SBO_K80),
+                   bd3 = umma_sdesc(tc_saddr(s.w3), 128, SBO_K80);
+    constexpr uint32_t ID64 = umma_idesc_bf16(TC_TILE, 64), ID16 = umma_idesc_bf16(TC_TILE, 16);
+    uint32_t oph[TC_STREAMS], layer[TC_STREAMS], acph[TC_STREAMS];
+    int64_t left[TC_STREAMS];  // layer steps still to issue per stream
+    bool inflight[TC_STREAMS];
+    int64_t total = 0;
 #pragma unroll
-    for (int k = 0; k < 3; k++) xv[k] = make_uint4(0u, 0u, 0u, 0u);
-    if (r < n) {
-      const uint4* src = reinterpret_cast<const uint4*>(X + r * 24) + xk0;
-#pragma unroll
-      for (int k = 0; k < 3; k++) xv[k] = src[k];
+    for (int q = 0; q < TC_STREAMS; q++) {
+      oph[q] = layer[q] = acph[q] = 0u;
+      inflight[q] = false;
+      int64_t nt = 0;
+      if (tile_of(q) < ntiles) nt = (ntiles - 1 - tile_of(q)) / (static_cast<int64_t>(gridDim.x) * TC_STREAMS) + 1;
+      left[q] = 3 * nt;
+      total += left[q];
     }
-  };
-  uint4 xn[3];
-  load_part(static_cast<int64_t>(blockIdx.x) * TC_TILE + xr, xn);
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    // the input chunks into the canonical K = 48 tile; the next tile's on
-    // their way while this tile runs through the three layers
+    uint64_t t0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    while (total > 0) {
+      bool moved = false;
 #pragma unroll
-    for (int k = 0; k < 3; k++) *reinterpret_cast<uint4*>(s.x + cm_off(xr, xk0 + k, SBO_K48)) = xn[k];
-    load_part(tile * TC_TILE + xr + static_cast<int64_t>(gridDim.x) * TC_TILE, xn);
-#pragma unroll 1
-    for (int layer = 0; layer < 3; layer++) {
-      // operands written by the threads -> visible to the tensor cores
-      proxy_fence_smem();
-      tc_fence_before();
-      __syncthreads();
-      if (tid == 0) {
+      for (int q = 0; q < TC_STREAMS; q++) {
+        if (left[q] == 0 || !mbar_test_wait(&s.opready[q], oph[q])) continue;
+        oph[q] ^= 1u;
         tc_fence_after();
-        if (layer == 0) {
+        const uint32_t r0 = tmem + 128 * q, r1 = r0 + 64;  // the stream's two regions
+        const uint32_t l = layer[q];
+        if (elect_one()) {
+          // K slice k: A 8 columns further, B 256 bytes further (16 in the
+          // descriptor's address field)
+          if (l == 0) {
 #pragma unroll
-          for (int k = 0; k < 3; k++)
-            umma_bf16(tmem, umma_sdesc(xs + 256 * k, 128, SBO_K48), umma_sdesc(w1s + 256 * k, 128, SBO_K48), ID64,
-                      k > 0);
-        } else {
-          const uint32_t ws = layer == 1 ? w2s : w3s;
+            for (int k = 0; k < 3; k++) umma_bf16_ts(r0, r1 + 8 * k, bd1 + 16 * k, ID64, k);
+          } else if (l == 1) {
 #pragma unroll
-          for (int k = 0; k < 4; k++)
-            umma_bf16(tmem, umma_sdesc(hs + 256 * k, 128, SBO_K64), umma_sdesc(ws + 256 * k, 128, SBO_K64),
-                      layer == 1 ? ID64 : ID16, k > 0);
+            for (int k = 0; k < 5; k++) umma_bf16_ts(r1, r0 + 8 * k, bd2 + 16 * k, ID64, k);
+          } else {
+#pragma unroll
+            for (int k = 0; k < 5; k++) umma_bf16_ts(r0, r1 + 8 * k, bd3 + 16 * k, ID16, k);
+          }
+          umma_commit(&s.accready[q]);
         }
-        umma_commit(&s.bar);
+        __syncwarp();
+        acph[q] ^= 1u;
+        inflight[q] = true;
+        layer[q] = l == 2 ? 0u : l + 1u;
+        left[q]--;
+        total--;
+        moved = true;
       }
-      const bool got = mbar_wait_bounded_tc(&s.bar, phase, err);
-      if (__syncthreads_or(!got)) {
-        failed = true;
-        break;
-      }
-      phase ^= 1u;
-      tc_fence_after();
-      if (layer < 2) {
-        tc_hidden_cols(tlanes + 32 * ch, layer == 0 ? s.b1 : s.b2, s.h, trow, 32 * ch);
-      } else if (ch == 0) {
-        float v[16];
-        tmem_ld16(tlanes, v);
-        const int64_t row = tile * TC_TILE + trow;
-        if (row < n) {
-          float4* dst = reinterpret_cast<float4*>(Y + row * 8);
-          dst[0] = make_float4(v[0] + s.b3[0], v[1] + s.b3[1], v[2] + s.b3[2], v[3] + s.b3[3]);
-          dst[1] = make_float4(v[4] + s.b3[4], v[5] + s.b3[5], v[6] + s.b3[6], v[7] + s.b3[7]);
+      if (moved) {
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+      } else {
+        uint64_t tn;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(tn));
+        if (tn - t0 > 1000000000ull) {
+          if ((t & 31) == 0) atomicOr(err, ERR_TIMEOUT);
+          break;
         }
       }
     }
-    if (failed) break;
+    // the last commit of each stream: wait (bounded) until its MMAs are done
+#pragma unroll
+    for (int q = 0; q < TC_STREAMS; q++)
+      if (inflight[q]) mbar_wait_bounded_tc(&s.accready[q], acph[q] ^ 1u, err);
+  } else {
+    const int st = warp >> 2;                     // this warp's stream
+    const int trow = 32 * (warp & 3) + (t & 31);  // the tile row of this thread's lane
+    const uint32_t r0 = tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16) + 128 * st, r1 = r0 + 64;
+    // the 40 inputs (20 words) of this row of tile k, zeros past n
+    auto load_row = [&](int64_t k, uint4 xv[5]) {
+      const int64_t r = tile_of(k) * TC_TILE + trow;
+#pragma unroll
+      for (int c = 0; c < 5; c++) xv[c] = make_uint4(0u, 0u, 0u, 0u);
+      if (r < n) {
+        const uint4* src = reinterpret_cast<const uint4*>(X + r * 24);
+#pragma unroll
+        for (int c = 0; c < 5; c++) xv[c] = src[c];
+      }
+    };
+    // operand in tensor memory (stores waited for) -> MMA warp
+    auto hand_over = [&]() {
+      tc_fence_before();
+      mbar_arrive(&s.opready[st]);
+    };
+    uint32_t aph = 0;
+    auto wait_acc = [&]() -> bool {
+      const bool got = mbar_wait_bounded_tc(&s.accready[st], aph, err);
+      aph ^= 1u;
+      tc_fence_after();
+      return got;
+    };
+    uint4 xv[5];
+    load_row(st, xv);
+    for (int64_t k = st; tile_of(k) < ntiles; k += TC_STREAMS) {
+      {  // X (K = 48: 20 words of inputs, the bias column pair, zeros) into region 1
+        uint32_t w[24];
+#pragma unroll
+        for (int c = 0; c < 5; c++) {
+          w[4 * c] = xv[c].x;
+          w[4 * c + 1] = xv[c].y;
+          w[4 * c + 2] = xv[c].z;
+          w[4 * c + 3] = xv[c].w;
+        }
+        w[20] = pack_bf16(1.f, 1.f);
+        w[21] = w[22] = w[23] = 0u;
+        tmem_st16(r1, w);
+        tmem_st8(r1 + 16, w + 16);
+        tmem_st_wait();
+      }
+      load_row(k + TC_STREAMS, xv);
+      hand_over();
+      if (!wait_acc()) break;
+      tc_hidden_row(r0);
+      hand_over();
+      if (!wait_acc()) break;
+      tc_hidden_row(r1);
+      hand_over();
+      if (!wait_acc()) break;
+      float v[32];
+      tmem_ld32(r0, v);
+      const int64_t row = tile_of(k) * TC_TILE + trow;
+      if (row < n) {
+        float4* dst = reinterpret_cast<float4*>(Y + row * 8);
+        dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+        dst[1] = make_float4(v[4], v[5], v[6], v[7]);
+      }
+      tc_fence_before();
+    }
   }
-  // an MMA may still run after a timed-out wait: wait for it once more
-  if (failed && tid == 0) mbar_wait_bounded_tc(&s.bar, phase, err);
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) {
+  if (warp == MMA_WARP) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
   }
@@ -209,6 +354,12 @@ __global__ void k_mlp_adam(float* __restrict__ p, const float* __restrict__ gr, 
 // BF16 pair layouts: w1 [64][24] (inputs 40..47 zero), w2 [64][32],
 // w3 [8][32], w2t [64][32] (transposed), w3t [64][8] (transposed, outputs
 // 8..15 zero), and the FP32 biases.
+// A bias as the BF16 pair (hi, lo): hi = BF16(b), lo = BF16(b - hi); with
+// 1.0 in both matching input columns the product adds b to 2^-16 relative.
+__device__ __forceinline__ uint32_t bias_pair(float b) {
+  const float hi = __bfloat162float(__float2bfloat16_rn(b));
+  return pack_bf16(hi, b - hi);
+}
 __global__ void k_mlp_pack(const float* __restrict__ P, MlpDev m) {
   const float* W1 = P;
   const float* B1 = W1 + 64 * 40;
@@ -234,6 +385,26 @@ __global__ void k_mlp_pack(const float* __restrict__ P, MlpDev m) {
       m.b2[e] = B2[e];
     }
     if (e < 8) m.b3[e] = B3[e];
+  }
+  // folded-bias layouts of the inference kernel
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 64 * 40; e += gridDim.x * blockDim.x) {
+    const int r = e / 40, c = e % 40;
+    if (c < 24) {
+      uint32_t w1 = 0u;
+      if (c < 20) w1 = pack_bf16(W1[r * 40 + 2 * c], W1[r * 40 + 2 * c + 1]);
+      else if (c == 20) w1 = bias_pair(B1[r]);
+      m.w1b[r * 24 + c] = w1;
+    }
+    uint32_t w = 0u;
+    if (c < 32) w = pack_bf16(0.5f * W2[r * 64 + 2 * c], 0.5f * W2[r * 64 + 2 * c + 1]);
+    else if (c == 32) w = bias_pair(B2[r]);
+    m.w2b[r * 40 + c] = w;
+    if (r < 16) {
+      uint32_t w3 = 0u;
+      if (r < 8 && c < 32) w3 = pack_bf16(0.5f * W3[r * 64 + 2 * c], 0.5f * W3[r * 64 + 2 * c + 1]);
+      else if (r < 8 && c == 32) w3 = bias_pair(B3[r]);
+      m.w3b[r * 40 + c] = w3;
+    }
   }
 }
 
@@ -613,24 +784,28 @@ __global__ void k_mlp_grad_reduce(const float* __restrict__ partial, const doubl
 
 
 constexpr size_t kTrainTcSmem = sizeof(TrainTc) + 128;
+constexpr size_t kInferSmem = sizeof(TcSmem) + 128;
 cudaError_t mlp_setup() {
-  return cudaFuncSetAttribute(k_mlp_train_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              static_cast<int>(kTrainTcSmem));
+  cudaError_t e = cudaFuncSetAttribute(k_mlp_train_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(kTrainTcSmem));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kInferSmem));
+  return e;
 }
 cudaError_t launch_mlp_pack(const float* P, const MlpDev& m, cudaStream_t st) {
   k_mlp_pack<<<8, 256, 0, st>>>(P, m);
   return cudaGetLastError();
 }
 // X: n rows of 24 words (16-byte aligned), Y: n rows of 8 floats (16-byte
-// aligned); 4 CTAs per SM at most (shared memory 45 KB, tensor memory 64 of
-// the SM's 512 columns each).
+// aligned); one CTA per SM (all 512 tensor-memory columns, 19 KB of shared
+// memory).
 cudaError_t launch_mlp_infer(const uint32_t* X, float* Y, int64_t n, const MlpDev& m, int nsm, int32_t* err,
                              cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   if ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Y)) & 15u) return cudaErrorInvalidValue;
   const int64_t tiles = (n + TC_TILE - 1) / TC_TILE;
-  const int grid = static_cast<int>(std::min<int64_t>(tiles, static_cast<int64_t>(nsm) * 4));
-  k_mlp_infer<<<grid, TC_THREADS, sizeof(TcSmem), st>>>(X, Y, n, m, err);
+  const int grid = static_cast<int>(std::min<int64_t>(tiles, static_cast<int64_t>(nsm)));
+  k_mlp_infer<<<grid, TC_THREADS, kInferSmem, st>>>(X, Y, n, m, err);
   return cudaGetLastError();
 }
 // The loss sum and the gradient on the tensor cores: one CTA per SM (at most
@@ -668,7 +843,7 @@ cudaError_t launch_rows_to_bf16(const float* X, uint32_t* Xb, int64_t n, cudaStr
 
 // Device weight set: one allocation holding the BF16 layouts and biases.
 cudaError_t mlp_alloc(MlpDev* w) {
-  const size_t words = 64 * 24 + 64 * 32 + 8 * 32 + 64 * 32 + 64 * 8;
+  const size_t words = 64 * 24 + 64 * 32 + 8 * 32 + 64 * 32 + 64 * 8 + 64 * 24 + 64 * 40 + 16 * 40;
   void* p = nullptr;
   cudaError_t e = cudaMalloc(&p, words * 4 + (64 + 64 + 8) * 4);
   if (e != cudaSuccess) return e;
@@ -678,7 +853,10 @@ cudaError_t mlp_alloc(MlpDev* w) {
   w->w3 = w->w2 + 64 * 32;
   w->w2t = w->w3 + 8 * 32;
   w->w3t = w->w2t + 64 * 32;
-  float* f = reinterpret_cast<float*>(w->w3t + 64 * 8);
+  w->w1b = w->w3t + 64 * 8;
+  w->w2b = w->w1b + 64 * 24;
+  w->w3b = w->w2b + 64 * 40;
+  float* f = reinterpret_cast<float*>(w->w3b + 16 * 40);
   w->b1 = f;
   w->b2 = f + 64;
   w->b3 = f + 128;
@@ -869,23 +1047,24 @@ int bats_mlp_get_params(bats_mlp_t* m, float* params) {
 }
 
 // GELU self-check: y[i] = the kernels' packed-pair GELU (BF16 results) of x[i].
-__global__ void k_debug_gelu(const float* x, int n, float* y) {
+__global__ void k_debug_gelu(const float* x, int n, int variant, float* y) {
   const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
   if (i >= n) return;
   const float x1 = i + 1 < n ? x[i + 1] : 0.f;
-  const uint32_t r = gelu2_pack(x[i], x1);
-  y[i] = bf16_lo(r);
-  if (i + 1 < n) y[i + 1] = bf16_hi(r);
+  const uint32_t r = variant ? gelu2x_pack(x[i], x1) : gelu2_pack(x[i], x1);
+  const float sc = variant ? 0.5f : 1.f;
+  y[i] = sc * bf16_lo(r);
+  if (i + 1 < n) y[i + 1] = sc * bf16_hi(r);
 }
 
-int bats_debug_gelu(const float* x, int n, float* y) {
-  if (!x || !y || n <= 0) return BATS_ERR_INVALID_ARG;
+int bats_debug_gelu(const float* x, int n, int variant, float* y) {
+  if (!x || !y || n <= 0 || variant < 0 || variant > 1) return BATS_ERR_INVALID_ARG;
   float *xd = nullptr, *yd = nullptr;
   cudaError_t e = cudaMalloc(&xd, n * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&yd, n * sizeof(float));
   if (e == cudaSuccess) e = cudaMemcpy(xd, x, n * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) {
-    k_debug_gelu<<<(n / 2 + 256) / 256, 256>>>(xd, n, yd);
+    k_debug_gelu<<<(n / 2 + 256) / 256, 256>>>(xd, n, variant, yd);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaMemcpy(y, yd, n * sizeof(float), cudaMemcpyDeviceToHost);
@@ -913,6 +1092,18 @@ int bats_mlp_forward(bats_mlp_t* m, const float* X, int64_t n, float* Y) {
     return (eb & ERR_TIMEOUT) ? BATS_ERR_TIMEOUT : BATS_ERR_INVALID_ARG;
   }
   return BATS_OK;
+}
+
+int bats_mlp_forward_bf16(bats_mlp_t* m, const uint32_t* Xb, int64_t n, float* Y) {
+  if (!m || !Xb || !Y || n <= 0) return BATS_ERR_INVALID_ARG;
+  if (!dev_ptr(Xb) || !dev_ptr(Y)) return BATS_ERR_INVALID_ARG;
+  return launch_mlp_infer(Xb, Y, n, m->w, m->nsm, m->errw, m->stream) == cudaSuccess ? BATS_OK : BATS_ERR_CUDA;
+}
+
+int bats_mlp_sync(bats_mlp_t* m) {
+  if (!m) return BATS_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize(m->stream) != cudaSuccess) return BATS_ERR_CUDA;
+  return mlp_check_err(m);
 }
 
 int bats_mlp_loss_grad(bats_mlp_t* m, const float* X, const float* T, int64_t n, float* grad, double* loss) {

@@ -7,8 +7,6 @@
 #pragma once
 #include <cstdint>
 #include <cuda_bf16.h>
-#include <cuda_fp16.h>
-#include <cstring>
 #include <cuda_runtime.h>
 
 #include "bats_internal.h"
@@ -34,29 +32,34 @@ __device__ __forceinline__ float gelu_f(float x) {
   const float k = 0.7978845608028654f;
   return 0.5f * x * (1.0f + tanh_approx(k * (x + 0.044715f * x * x * x)));
 }
-// Two GELUs (tanh form) rounded to a BF16 pair (x0 in the low half), the
-// tanh evaluated for both by one tanh.approx.f16x2 (one special-function
-// operation for two values; its arguments are rounded to FP16 first, FP16
-// having 11 significant bits against BF16's 8).  Error against the exact
-// GELU: the argument's FP16 rounding moves tanh by at most
-// max_u |u| sech^2(u) 2^-11 < 2.2e-4, the FP16 result of tanh adds a few
-// 2^-12, so |gelu2 - gelu| <= 0.5 |x| 1.5e-3 + the final BF16 rounding
-// (2^-9 relative), the size of the BF16 rounding every hidden activation
-// gets anyway.  Arguments beyond the FP16 range become +-inf, whose tanh is
-// +-1: the GELU's limits.
+// Two GELUs (tanh form) rounded to a BF16 pair (x0 in the low half), in
+// packed FP32 arithmetic around one tanh.approx.f32 per value:
+// u = x (k + k 0.044715 x^2), gelu = h + h tanh(u) with h = x / 2.  The
+// hardware tanh has an absolute error of a few 2^-12, so
+// |gelu2 - gelu| <= 0.5 |x| 1e-3 + the final BF16 rounding (2^-9 relative),
+// the size of the BF16 rounding every hidden activation gets anyway.  For
+// |x| beyond the FP32 range of x^2 the argument is +-inf and tanh +-1: the
+// GELU's limits.
+__device__ __forceinline__ float2 gelu_arg2(float2 x) {
+  const float k = 0.7978845608028654f, c = 0.7978845608028654f * 0.044715f;
+  return __fmul2_rn(x, __ffma2_rn(__fmul2_rn(x, x), make_float2(c, c), make_float2(k, k)));
+}
 __device__ __forceinline__ uint32_t gelu2_pack(float x0, float x1) {
-  const float k = 0.7978845608028654f;
+  const float2 u = gelu_arg2(make_float2(x0, x1));
+  const float2 t = make_float2(tanh_approx(u.x), tanh_approx(u.y));
+  const float2 h = __fmul2_rn(make_float2(0.5f, 0.5f), make_float2(x0, x1));
+  const float2 g = __ffma2_rn(h, t, h);
+  return pack_bf16(g.x, g.y);
+}
+// Twice the GELU pair, x (1 + tanh(u)), for a layer whose next layer takes
+// weights halved (exactly, in BF16): one multiplication fewer per pair, and
+// BF16(2 g) = 2 BF16(g), so the next layer's products are the same.
+__device__ __forceinline__ uint32_t gelu2x_pack(float x0, float x1) {
   const float2 x = make_float2(x0, x1);
-  const float2 xx = __fmul2_rn(x, x);
-  const float2 u = __fmul2_rn(make_float2(k, k), __ffma2_rn(__fmul2_rn(xx, x), make_float2(0.044715f, 0.044715f), x));
-  uint32_t ub, tb;
-  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(ub) : "f"(u.y), "f"(u.x));  // u.x in the low half
-  asm("tanh.approx.f16x2 %0, %1;" : "=r"(tb) : "r"(ub));
-  __half2 th;
-  memcpy(&th, &tb, sizeof(th));
-  const float2 t = __half22float2(th);
-  const float2 h = __fmul2_rn(__fmul2_rn(make_float2(0.5f, 0.5f), x), __fadd2_rn(make_float2(1.f, 1.f), t));
-  return pack_bf16(h.x, h.y);
+  const float2 u = gelu_arg2(x);
+  const float2 t = make_float2(tanh_approx(u.x), tanh_approx(u.y));
+  const float2 g = __ffma2_rn(x, t, x);
+  return pack_bf16(g.x, g.y);
 }
 __device__ __forceinline__ float gelu_grad_f(float x) {
   const float k = 0.7978845608028654f;

@@ -358,16 +358,17 @@ def test_learned_last_stage_only_matches_oracle(B, precision):
     assert err <= (3e-2 if precision == "fp64" else 5e-2) * effect
 
 
-def test_gelu_pair_within_its_bound(B):
-    """The kernels' GELU (two values per tanh.approx.f16x2, BF16 result)
-    against the exact tanh-form GELU: |gelu2 - gelu| <= 0.5 |x| |dt| + the
-    final BF16 rounding (2^-8 of the value, 1e-30 floor), with |dt| <= 2e-3:
-    the FP16 rounding of the tanh argument moves tanh by at most
-    max_u |u| sech^2(u) 2^-11 < 2.2e-4, and the FP16 result of tanh is
-    allowed a few units of 2^-11 near |t| = 1.  Over [-12, 12] and at the
-    tails (beyond the FP16 range the argument is +-inf, tanh +-1)."""
-    x = np.concatenate([np.linspace(-12, 12, 200001), [-40.0, -7.5, 0.0, 1e-3, -1e-3, 7.5, 40.0]]).astype(np.float32)
-    y = B.bats_debug_gelu(x)
+@pytest.mark.parametrize("variant", [0, 1])
+def test_gelu_pair_within_its_bound(B, variant):
+    """The kernels' GELU (packed FP32 around tanh.approx.f32, BF16 result;
+    variant 1 the inference kernel's doubled form, halved) against the exact
+    tanh-form GELU: |gelu2 - gelu| <= 0.5 |x| |dt| + the final BF16 rounding
+    (2^-8 of the value, 1e-30 floor), with |dt| <= 2e-3, several times the
+    hardware tanh's absolute error.  Over [-12, 12] and at the tails (beyond
+    the FP32 range of x^2 the argument is +-inf, tanh +-1)."""
+    x = np.concatenate([np.linspace(-12, 12, 200001),
+                        [-3e19, -40.0, -7.5, 0.0, 1e-3, -1e-3, 7.5, 40.0, 3e19]]).astype(np.float32)
+    y = B.bats_debug_gelu(x, variant)
     xd = x.astype(np.float64)
     exact = 0.5 * xd * (1 + np.tanh(0.7978845608028654 * (xd + 0.044715 * xd ** 3)))
     err = np.abs(y - exact)
