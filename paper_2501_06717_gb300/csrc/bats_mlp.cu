@@ -32,32 +32,19 @@ namespace batsk {
 
 constexpr int TC_TILE = 128;        // rows per tile (MMA M = tensor-memory lanes)
 constexpr int TC_STREAMS = 4;       // tiles in flight per CTA (one CTA per SM)
-constexpr int TC_THREADS = 32 * (4 * TC_STREAMS + 1);  // four warps per stream + the MMA warp
+constexpr int TC_THREADS = 32 * 4 * TC_STREAMS;  // four warps per stream
 constexpr int TC_TMEM_COLS = 512;   // two regions of 64 columns per stream
 constexpr uint32_t SBO_K80 = 1280;  // 16 bytes x K = 80
 struct TcSmem {
   alignas(128) uint8_t w1[64 * 96];   // B of layer 1: N = 64, K = 48
   alignas(128) uint8_t w2[64 * 160];  // B of layer 2: N = 64, K = 80 (weights halved)
   alignas(128) uint8_t w3[16 * 160];  // B of layer 3: N = 16 (8 outputs, 8 zero rows), K = 80 (halved)
-  uint64_t opready[TC_STREAMS];       // 128 arrivals: the stream's operand is in tensor memory
   uint64_t accready[TC_STREAMS];      // tcgen05.commit: the stream's layer is in tensor memory
   uint32_t tmem;
 };
 
 __device__ __forceinline__ void mbar_init_count(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc_saddr(bar)), "r"(count) : "memory");
-}
-// Non-blocking test of an mbarrier phase (mbarrier.try_wait may suspend the
-// thread for a while when the phase is not complete: a thread serving
-// several barriers polls with this instead).
-__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(tc_saddr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
 }
 // true in one lane of the (converged) warp
 __device__ __forceinline__ bool elect_one() {
@@ -66,9 +53,6 @@ __device__ __forceinline__ bool elect_one() {
       "{\n .reg .b32 r;\n .reg .pred p;\n elect.sync r|p, 0xffffffff;\n selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(pred));
   return pred != 0;
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc_saddr(bar)) : "memory");
 }
 // D[tmem] (+)= A B^T for one K = 16 slice, A (M = 128 rows = lanes, K packed
 // two BF16 per 32-bit column, 8 columns per slice) in tensor memory
@@ -136,31 +120,30 @@ __device__ __forceinline__ void tc_hidden_row(uint32_t taddr) {
   tmem_st_wait();
 }
 
-// Y[n][8] = MLP(X[n][48] BF16), one persistent CTA per SM, warp specialised:
-// TC_STREAMS streams of four warps, each stream with a tile of its own in
-// flight (the CTA's tiles k = s, s + TC_STREAMS, ..), thread t of the stream
-// owning row t (tensor-memory lane t; warp w reads and writes lanes
-// 32 (w % 4) ..), and one warp issuing every MMA.  Every A operand lives in
-// tensor memory, written by the stream's threads (tcgen05.st): the inputs,
-// then each layer's activations over the accumulator they came from, so
-// shared memory carries only the weights.  A stream's two 64-column regions
-// alternate: layer 1 reads X from region 1 into region 0, layer 2 reads H1
-// (region 0) into region 1, layer 3 reads H2 (region 1) into region 0.  A
-// stream hands its operand to the MMA warp through opready (all 128 threads
-// arrive) and gets the layer back through accready (tcgen05.commit), so no
-// stream waits for another.  The biases ride in the products (ones in the
-// bias columns, the bias pairs in the weights); the hidden activations are
-// twice the GELU (the next layer's weights halved), a hidden pair costing
-// one packed-FP32 chain around two tanh.approx.f32.  Every wait is bounded
-// (ERR_TIMEOUT in err); a stream whose wait ran out stops, the MMA warp
-// stops once no stream has moved for the same time and waits once more for
-// its MMAs in flight, and the CTA frees its tensor memory and returns.
+// Y[n][8] = MLP(X[n][48] BF16), one persistent CTA per SM: TC_STREAMS
+// streams of four warps, each stream with a tile of its own in flight (the
+// CTA's tiles k = s, s + TC_STREAMS, ..), thread t of the stream owning row t
+// (tensor-memory lane t; warp w reads and writes lanes 32 (w % 4) ..).  Every
+// A operand lives in tensor memory, written by the stream's threads
+// (tcgen05.st): the inputs, then each layer's activations over the
+// accumulator they came from, so shared memory carries only the weights.  A
+// stream's two 64-column regions alternate: layer 1 reads X from region 1
+// into region 0, layer 2 reads H1 (region 0) into region 1, layer 3 reads H2
+// (region 1) into region 0.  Each stream issues its own MMAs (one elected
+// thread of its first warp, after a barrier of the stream's 128 threads) and
+// commits them to its own mbarrier, so a stream waits for its own products
+// only.  The biases ride in the products (ones in the bias columns, the bias
+// pairs in the weights); the hidden activations are twice the GELU (the next
+// layer's weights halved), a hidden pair costing one packed-FP32 chain
+// around two tanh.approx.f32.  Every wait is bounded (ERR_TIMEOUT in err); a
+// stream whose wait ran out (in any of its threads: the stream's barrier
+// carries the flag) waits once more for its MMAs in flight and stops, and
+// the CTA frees its tensor memory and returns.
 __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_infer(const uint32_t* __restrict__ X, float* __restrict__ Y,
                                                              int64_t n, MlpDev m, int32_t* err) {
   extern __shared__ __align__(128) unsigned char tc_smem_raw[];
   TcSmem& s = *reinterpret_cast<TcSmem*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 127) & ~uintptr_t(127));
   const int t = threadIdx.x, warp = t >> 5;
-  constexpr int MMA_WARP = 4 * TC_STREAMS;
   // weights into the canonical layouts (16-byte chunks)
   for (int e = t; e < 64 * 6; e += TC_THREADS) {
     const int r = e / 6, kc = e % 6;
@@ -174,17 +157,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_infer(const uint32_t* __r
     const int r = e / 10, kc = e % 10;
     *reinterpret_cast<uint4*>(s.w3 + cm_off(r, kc, SBO_K80)) = *reinterpret_cast<const uint4*>(m.w3b + r * 40 + kc * 4);
   }
-  if (warp == MMA_WARP) {
+  if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_saddr(&s.tmem)),
                  "r"(TC_TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (t == 0) {
-    for (int q = 0; q < TC_STREAMS; q++) {
-      mbar_init_count(&s.opready[q], TC_TILE);
-      mbar_init_count(&s.accready[q], 1);
-    }
+    for (int q = 0; q < TC_STREAMS; q++) mbar_init_count(&s.accready[q], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   proxy_fence_smem();
@@ -194,143 +174,113 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_infer(const uint32_t* __r
   const uint32_t tmem = s.tmem;
   const int64_t ntiles = (n + TC_TILE - 1) / TC_TILE;
   auto tile_of = [&](int64_t k) { return static_cast<int64_t>(blockIdx.x) + k * gridDim.x; };
-
-  if (warp == MMA_WARP) {
-    // the whole warp polls and builds the descriptors (warp-uniform values),
-    // one elected lane issues
-    const uint64_t bd1 = umma_sdesc(tc_saddr(s.w1), 128, SBO_K48), bd2 = umma_sdesc(tc_saddr(s.w2), 128, SBO_K80),
-                   bd3 = umma_sdesc(tc_saddr(s.w3), 128, SBO_K80);
-    constexpr uint32_t ID64 = umma_idesc_bf16(TC_TILE, 64), ID16 = umma_idesc_bf16(TC_TILE, 16);
-    uint32_t oph[TC_STREAMS], layer[TC_STREAMS], acph[TC_STREAMS];
-    int64_t left[TC_STREAMS];  // layer steps still to issue per stream
-    bool inflight[TC_STREAMS];
-    int64_t total = 0;
-#pragma unroll
-    for (int q = 0; q < TC_STREAMS; q++) {
-      oph[q] = layer[q] = acph[q] = 0u;
-      inflight[q] = false;
-      int64_t nt = 0;
-      if (tile_of(q) < ntiles) nt = (ntiles - 1 - tile_of(q)) / (static_cast<int64_t>(gridDim.x) * TC_STREAMS) + 1;
-      left[q] = 3 * nt;
-      total += left[q];
-    }
-    uint64_t t0;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-    while (total > 0) {
-      bool moved = false;
-#pragma unroll
-      for (int q = 0; q < TC_STREAMS; q++) {
-        if (left[q] == 0 || !mbar_test_wait(&s.opready[q], oph[q])) continue;
-        oph[q] ^= 1u;
+  const int st = warp >> 2;                     // this warp's stream
+  const int trow = 32 * (warp & 3) + (t & 31);  // the tile row of this thread's lane
+  const uint32_t lanes = static_cast<uint32_t>(32 * (warp & 3)) << 16;
+  const uint32_t r0 = tmem + lanes + 128 * st, r1 = r0 + 64;  // this lane in the stream's two regions
+  const uint32_t m0 = tmem + 128 * st, m1 = m0 + 64;          // the regions as MMA operands (lane 0)
+  const uint64_t bd1 = umma_sdesc(tc_saddr(s.w1), 128, SBO_K48), bd2 = umma_sdesc(tc_saddr(s.w2), 128, SBO_K80),
+                 bd3 = umma_sdesc(tc_saddr(s.w3), 128, SBO_K80);
+  constexpr uint32_t ID64 = umma_idesc_bf16(TC_TILE, 64), ID16 = umma_idesc_bf16(TC_TILE, 16);
+  uint64_t* bar = &s.accready[st];
+  uint32_t aph = 0;
+  bool pending = false;  // an MMA group of this stream not yet waited for (issuing thread's view)
+  // operands of layer l in tensor memory (stores waited for) in every thread
+  // of the stream -> its MMAs, issued by one thread; false if some thread of
+  // the stream saw a wait run out
+  auto issue = [&](int l, bool ok) -> bool {
+    tc_fence_before();
+    uint32_t any_bad;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.eq.u32 p, %1, 0;\n bar.red.or.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(any_bad)
+        : "r"(ok ? 1u : 0u), "r"(1 + st), "r"(TC_TILE)
+        : "memory");
+    if (any_bad) return false;
+    if ((warp & 3) == 0) {
+      if (elect_one()) {
         tc_fence_after();
-        const uint32_t r0 = tmem + 128 * q, r1 = r0 + 64;  // the stream's two regions
-        const uint32_t l = layer[q];
-        if (elect_one()) {
-          // K slice k: A 8 columns further, B 256 bytes further (16 in the
-          // descriptor's address field)
-          if (l == 0) {
+        // K slice k: A 8 columns further, B 256 bytes further (16 in the
+        // descriptor's address field)
+        if (l == 0) {
 #pragma unroll
-            for (int k = 0; k < 3; k++) umma_bf16_ts(r0, r1 + 8 * k, bd1 + 16 * k, ID64, k);
-          } else if (l == 1) {
+          for (int k = 0; k < 3; k++) umma_bf16_ts(m0, m1 + 8 * k, bd1 + 16 * k, ID64, k);
+        } else if (l == 1) {
 #pragma unroll
-            for (int k = 0; k < 5; k++) umma_bf16_ts(r1, r0 + 8 * k, bd2 + 16 * k, ID64, k);
-          } else {
+          for (int k = 0; k < 5; k++) umma_bf16_ts(m1, m0 + 8 * k, bd2 + 16 * k, ID64, k);
+        } else {
 #pragma unroll
-            for (int k = 0; k < 5; k++) umma_bf16_ts(r0, r1 + 8 * k, bd3 + 16 * k, ID16, k);
-          }
-          umma_commit(&s.accready[q]);
+          for (int k = 0; k < 5; k++) umma_bf16_ts(m0, m1 + 8 * k, bd3 + 16 * k, ID16, k);
         }
-        __syncwarp();
-        acph[q] ^= 1u;
-        inflight[q] = true;
-        layer[q] = l == 2 ? 0u : l + 1u;
-        left[q]--;
-        total--;
-        moved = true;
+        umma_commit(bar);
       }
-      if (moved) {
-        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-      } else {
-        uint64_t tn;
-        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(tn));
-        if (tn - t0 > 1000000000ull) {
-          if ((t & 31) == 0) atomicOr(err, ERR_TIMEOUT);
-          break;
-        }
-      }
+      __syncwarp();
     }
-    // the last commit of each stream: wait (bounded) until its MMAs are done
-#pragma unroll
-    for (int q = 0; q < TC_STREAMS; q++)
-      if (inflight[q]) mbar_wait_bounded_tc(&s.accready[q], acph[q] ^ 1u, err);
-  } else {
-    const int st = warp >> 2;                     // this warp's stream
-    const int trow = 32 * (warp & 3) + (t & 31);  // the tile row of this thread's lane
-    const uint32_t r0 = tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16) + 128 * st, r1 = r0 + 64;
-    // the 40 inputs (20 words) of this row of tile k, zeros past n
-    auto load_row = [&](int64_t k, uint4 xv[5]) {
-      const int64_t r = tile_of(k) * TC_TILE + trow;
-#pragma unroll
-      for (int c = 0; c < 5; c++) xv[c] = make_uint4(0u, 0u, 0u, 0u);
-      if (r < n) {
-        const uint4* src = reinterpret_cast<const uint4*>(X + r * 24);
-#pragma unroll
-        for (int c = 0; c < 5; c++) xv[c] = src[c];
-      }
-    };
-    // operand in tensor memory (stores waited for) -> MMA warp
-    auto hand_over = [&]() {
-      tc_fence_before();
-      mbar_arrive(&s.opready[st]);
-    };
-    uint32_t aph = 0;
-    auto wait_acc = [&]() -> bool {
-      const bool got = mbar_wait_bounded_tc(&s.accready[st], aph, err);
+    pending = true;
+    return true;
+  };
+  auto wait_acc = [&]() -> bool {
+    const bool got = mbar_wait_bounded_tc(bar, aph, err);
+    if (got) {
       aph ^= 1u;
-      tc_fence_after();
-      return got;
-    };
-    uint4 xv[5];
-    load_row(st, xv);
-    for (int64_t k = st; tile_of(k) < ntiles; k += TC_STREAMS) {
-      {  // X (K = 48: 20 words of inputs, the bias column pair, zeros) into region 1
-        uint32_t w[24];
+      pending = false;
+    }
+    tc_fence_after();
+    return got;
+  };
+  // the 40 inputs (20 words) of this row of tile k, zeros past n
+  auto load_row = [&](int64_t k, uint4 xv[5]) {
+    const int64_t r = tile_of(k) * TC_TILE + trow;
 #pragma unroll
-        for (int c = 0; c < 5; c++) {
-          w[4 * c] = xv[c].x;
-          w[4 * c + 1] = xv[c].y;
-          w[4 * c + 2] = xv[c].z;
-          w[4 * c + 3] = xv[c].w;
-        }
-        w[20] = pack_bf16(1.f, 1.f);
-        w[21] = w[22] = w[23] = 0u;
-        tmem_st16(r1, w);
-        tmem_st8(r1 + 16, w + 16);
-        tmem_st_wait();
+    for (int c = 0; c < 5; c++) xv[c] = make_uint4(0u, 0u, 0u, 0u);
+    if (r < n) {
+      const uint4* src = reinterpret_cast<const uint4*>(X + r * 24);
+#pragma unroll
+      for (int c = 0; c < 5; c++) xv[c] = src[c];
+    }
+  };
+  uint4 xv[5];
+  load_row(st, xv);
+  bool ok = true;
+  for (int64_t k = st; tile_of(k) < ntiles; k += TC_STREAMS) {
+    {  // X (K = 48: 20 words of inputs, the bias column pair, zeros) into region 1
+      uint32_t w[24];
+#pragma unroll
+      for (int c = 0; c < 5; c++) {
+        w[4 * c] = xv[c].x;
+        w[4 * c + 1] = xv[c].y;
+        w[4 * c + 2] = xv[c].z;
+        w[4 * c + 3] = xv[c].w;
       }
-      load_row(k + TC_STREAMS, xv);
-      hand_over();
-      if (!wait_acc()) break;
-      tc_hidden_row(r0);
-      hand_over();
-      if (!wait_acc()) break;
-      tc_hidden_row(r1);
-      hand_over();
-      if (!wait_acc()) break;
-      float v[32];
-      tmem_ld32(r0, v);
-      const int64_t row = tile_of(k) * TC_TILE + trow;
-      if (row < n) {
-        float4* dst = reinterpret_cast<float4*>(Y + row * 8);
-        dst[0] = make_float4(v[0], v[1], v[2], v[3]);
-        dst[1] = make_float4(v[4], v[5], v[6], v[7]);
-      }
-      tc_fence_before();
+      w[20] = pack_bf16(1.f, 1.f);
+      w[21] = w[22] = w[23] = 0u;
+      tmem_st16(r1, w);
+      tmem_st8(r1 + 16, w + 16);
+      tmem_st_wait();
+    }
+    load_row(k + TC_STREAMS, xv);
+    if (!issue(0, ok)) break;
+    ok = wait_acc();
+    tc_hidden_row(r0);
+    if (!issue(1, ok)) break;
+    ok = wait_acc();
+    tc_hidden_row(r1);
+    if (!issue(2, ok)) break;
+    ok = wait_acc();
+    float v[32];
+    tmem_ld32(r0, v);
+    const int64_t row = tile_of(k) * TC_TILE + trow;
+    if (ok && row < n) {
+      float4* dst = reinterpret_cast<float4*>(Y + row * 8);
+      dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+      dst[1] = make_float4(v[4], v[5], v[6], v[7]);
     }
   }
+  // after a timed-out wait this stream's MMAs may still run: wait once more
+  if (pending && !ok) mbar_wait_bounded_tc(bar, aph, err);
   tc_fence_before();
   __syncthreads();
-  if (warp == MMA_WARP) {
+  if (warp == 0) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
   }
