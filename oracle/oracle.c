@@ -56,7 +56,7 @@ enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_INFLOW = 2 };
 enum { LIM_MINMOD = 0, LIM_MC = 1, LIM_NONE = 2 };
 enum { RK_MIDPOINT = 0, RK_SSP2 = 1, RK_EULER = 2 };
 enum { B0_NONE = 0, B0_UNIFORM = 1, B0_DIPOLE = 2, B0_LINEAR = 3 };
-enum { FLUX_RUSANOV = 0, FLUX_HLL = 1 };
+enum { FLUX_RUSANOV = 0, FLUX_HLL = 1, FLUX_LINDE = 2 };
 enum { OR_OK = 0, OR_EINVAL = -1, OR_EUNBALANCED = -2, OR_ENOMEM = -3 };
 enum { GT_INTERIOR = 0, GT_COPY = 1, GT_RESTRICT = 2, GT_PROLONG = 3, GT_INFLOW = 4 };
 
@@ -83,7 +83,8 @@ typedef struct {
   const double* mlp;     /* MLP_NPARAM weights (W1,b1,W2,b2,W3,b3), row-major [out][in] */
   int32_t local_dt;      /* 1 = local time stepping: each cell its own dt (steady-state runs) */
   int32_t reflux;        /* 1 = conservative flux correction at resolution changes */
-  int32_t flux;          /* FLUX_RUSANOV, or FLUX_HLL (two-state HLL, Davis wave-speed bounds) */
+  int32_t flux;          /* FLUX_RUSANOV, FLUX_HLL (two-state HLL, Davis wave-speed bounds) or
+                            FLUX_LINDE (HLL with the contact wave restored) */
   int32_t learned_last_only; /* learned form: 1 = the correction in the last stage of a step only (the
                               * stage whose fluxes enter U^{n+1}, where the training target is defined) */
 } or_desc;
@@ -277,7 +278,7 @@ static int grid_init(grid_t* G, const or_desc* d, double dummy_unused) {
   G->d = d;
   if (!d || !d->leaves || d->n_leaves <= 0) return OR_EINVAL;
   if (!(d->gamma > 1.0)) return OR_EINVAL;
-  if (d->flux < FLUX_RUSANOV || d->flux > FLUX_HLL) return OR_EINVAL;
+  if (d->flux < FLUX_RUSANOV || d->flux > FLUX_LINDE) return OR_EINVAL;
   if (d->flux != FLUX_RUSANOV && d->learned) return OR_EINVAL; /* the correction is defined on Rusanov */
   for (int a = 0; a < 3; a++) {
     if (d->root[a] <= 0 || !(d->hi[a] > d->lo[a])) return OR_EINVAL;
@@ -619,19 +620,28 @@ static int in_body(const or_desc* d, const double x[3]) {
 }
 
 /* Numerical flux from the two face states' physical fluxes F, states U,
- * normal speeds un and fast speeds cf.
+ * primitives W (x, y, z components), normal speeds un and fast speeds cf.
  *  Rusanov: F = (F_L + F_R)/2 - cmax (U_R - U_L)/2,
  *           cmax = max(|un_L| + cf_L, |un_R| + cf_R).
  *  HLL (Harten, Lax and van Leer 1983), with the wave-speed bounds of Davis
  *  (1988) S_L = min(un_L - cf_L, un_R - cf_R), S_R = max(un_L + cf_L,
  *  un_R + cf_R): F = F_L where S_L >= 0, F = F_R where S_R <= 0, else
  *  F = (S_R F_L - S_L F_R + S_L S_R (U_R - U_L)) / (S_R - S_L).
- *  The paper's solver uses the Linde flux, which adds a contact-restoring
- *  term to HLL; it is not given in the paper, so HLL stands in for it. */
-static void numerical_flux(int kind, const double FL[NV], const double FR[NV], const double UL[NV],
-                           const double UR[NV], double unL, double unR, double cfL, double cfR,
-                           double F[NV]) {
-  if (kind == FLUX_HLL) {
+ *  Linde (the paper's flux, Section 5.1, cited to Linde 2002 without its
+ *  formula): HLL with the contact (entropy) wave restored -- HLL's
+ *  dissipation S_L S_R / (S_R - S_L) (U_R - U_L) smears a density jump that no
+ *  wave but the flow carries; the part of the jump along the contact's
+ *  eigenvector r = (1, u, 0, |u|^2 / 2) (density, momentum, field, energy at
+ *  fixed pressure, velocity and field), of strength alpha = (rho_R - rho_L)
+ *  - (p_R - p_L) / c^2, is taken back out with the weight
+ *  delta = c / (c + |u_n|):  F = F_HLL - delta alpha S_L S_R / (S_R - S_L) r,
+ *  with u, rho, p the means of the two face states and c^2 = gamma p / rho
+ *  (reading 18).  `contact` scales the restored part (1 for the flux, 0 gives
+ *  HLL). */
+static void numerical_flux(int kind, int dir, double gamma, const double WL[NV], const double WR[NV],
+                           const double FL[NV], const double FR[NV], const double UL[NV], const double UR[NV],
+                           double unL, double unR, double cfL, double cfR, double contact, double F[NV]) {
+  if (kind == FLUX_HLL || kind == FLUX_LINDE) {
     double SL = fmin(unL - cfL, unR - cfR);
     double SR = fmax(unL + cfL, unR + cfR);
     if (SL >= 0.0) {
@@ -641,6 +651,17 @@ static void numerical_flux(int kind, const double FL[NV], const double FR[NV], c
     } else {
       for (int v = 0; v < NV; v++)
         F[v] = (SR * FL[v] - SL * FR[v] + SL * SR * (UR[v] - UL[v])) / (SR - SL);
+      if (kind == FLUX_LINDE) {
+        double rho = 0.5 * (WL[0] + WR[0]), p = 0.5 * (WL[7] + WR[7]), u[3];
+        for (int c = 0; c < 3; c++) u[c] = 0.5 * (WL[1 + c] + WR[1 + c]);
+        double c2 = gamma * p / rho, cs = sqrt(c2);
+        double alpha = (WR[0] - WL[0]) - (WR[7] - WL[7]) / c2;
+        double delta = cs / (cs + fabs(u[dir]));
+        double q = contact * delta * alpha * SL * SR / (SR - SL);
+        F[0] -= q;
+        for (int c = 0; c < 3; c++) F[1 + c] -= q * u[c];
+        F[7] -= q * 0.5 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+      }
     }
     return;
   }
@@ -673,7 +694,7 @@ static void face_flux(const grid_t* G, int dir, const double* Wt /* [12^3][8] */
   phys_flux(d, dir, WR, B0f, FR, UR, &unR, &cfR);
   double aL = fabs(unL) + cfL, aR = fabs(unR) + cfR;
   double cmax = aL > aR ? aL : aR;
-  numerical_flux(d->flux, FL, FR, UL, UR, unL, unR, cfL, cfR, out->F);
+  numerical_flux(d->flux, dir, d->gamma, WL, WR, FL, FR, UL, UR, unL, unR, cfL, cfR, 1.0, out->F);
   if (d->learned && d->mlp) {
     double Ws[32], x[MLP_IN], h1[MLP_H], h2[MLP_H], y[MLP_OUT], sc[MLP_OUT];
     memcpy(Ws, Wm2, 64); memcpy(Ws + 8, Wm1, 64); memcpy(Ws + 16, Wp0, 64); memcpy(Ws + 24, Wp1, 64);
@@ -1210,5 +1231,15 @@ void or_numerical_flux(const or_desc* d, int dir, const double WL[NV], const dou
   double FL[NV], FR[NV], UL[NV], UR[NV], unL, unR, cfL, cfR;
   phys_flux(d, dir, WL, B0, FL, UL, &unL, &cfL);
   phys_flux(d, dir, WR, B0, FR, UR, &unR, &cfR);
-  numerical_flux(d->flux, FL, FR, UL, UR, unL, unR, cfL, cfR, F);
+  numerical_flux(d->flux, dir, d->gamma, WL, WR, FL, FR, UL, UR, unL, unR, cfL, cfR, 1.0, F);
+}
+
+/* The same with the Linde flux's restored contact part scaled by `contact`
+ * (0: the HLL flux). */
+void or_numerical_flux_contact(const or_desc* d, int dir, const double WL[NV], const double WR[NV],
+                               const double B0[3], double contact, double F[NV]) {
+  double FL[NV], FR[NV], UL[NV], UR[NV], unL, unR, cfL, cfR;
+  phys_flux(d, dir, WL, B0, FL, UL, &unL, &cfL);
+  phys_flux(d, dir, WR, B0, FR, UR, &unR, &cfR);
+  numerical_flux(d->flux, dir, d->gamma, WL, WR, FL, FR, UL, UR, unL, unR, cfL, cfR, contact, F);
 }

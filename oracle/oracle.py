@@ -98,6 +98,7 @@ def lib():
         _lib.or_limiter.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double]
         _lib.or_limiter.restype = ctypes.c_double
         _lib.or_numerical_flux.argtypes = [D, ctypes.c_int, dp, dp, dp, dp]
+        _lib.or_numerical_flux_contact.argtypes = [D, ctypes.c_int, dp, dp, dp, ctypes.c_double, dp]
         _lib.or_num_threads.restype = ctypes.c_int
         _lib.or_set_threads.argtypes = [ctypes.c_int]
         _lib.or_mlp_forward.argtypes = [dp, dp, dp, dp, dp]
@@ -298,15 +299,20 @@ def set_threads(n):
     lib().or_set_threads(int(n))
 
 
-def numerical_flux(prob, direction, WL, WR, B0=(0.0, 0.0, 0.0)):
-    """The numerical flux (prob.flux: Rusanov or HLL) through a face along
-    `direction` between the primitive face states WL and WR."""
+def numerical_flux(prob, direction, WL, WR, B0=(0.0, 0.0, 0.0), contact=None):
+    """The numerical flux (prob.flux: Rusanov, HLL or Linde) through a face
+    along `direction` between the primitive face states WL and WR; `contact`
+    scales the Linde flux's restored contact part (0: HLL)."""
     b = _Bound(prob)
     WL = np.ascontiguousarray(WL, dtype=np.float64).reshape(8)
     WR = np.ascontiguousarray(WR, dtype=np.float64).reshape(8)
     B0 = np.ascontiguousarray(B0, dtype=np.float64).reshape(3)
     out = np.zeros(8)
-    lib().or_numerical_flux(b.ref(), int(direction), _dp(WL), _dp(WR), _dp(B0), _dp(out))
+    if contact is None:
+        lib().or_numerical_flux(b.ref(), int(direction), _dp(WL), _dp(WR), _dp(B0), _dp(out))
+    else:
+        lib().or_numerical_flux_contact(b.ref(), int(direction), _dp(WL), _dp(WR), _dp(B0), float(contact),
+                                        _dp(out))
     return out
 
 

@@ -17,7 +17,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libbats.so")
 # the checked build: every kernel index range-tested (tests only)
 OUT_CHECKED = os.path.join(HERE, "_build_checked")
-SOURCES = ["bats_stage.cu", "bats_host.cu", "bats_noalloc.cu", "bats_mlp.cu"]
+SOURCES = ["bats_stage.cu", "bats_stage_flux.cu", "bats_host.cu", "bats_noalloc.cu", "bats_mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]
@@ -34,7 +34,7 @@ def _stale(obj, src):
     if not os.path.exists(obj):
         return True
     deps = [src, os.path.join(CSRC, "bats_internal.h"), os.path.join(CSRC, "bats_tc.h"),
-            os.path.join(ROOT, "include", "bats.h")]
+            os.path.join(CSRC, "bats_stage_kernel.h"), os.path.join(ROOT, "include", "bats.h")]
     return any(os.path.getmtime(d) > os.path.getmtime(obj) for d in deps)
 
 

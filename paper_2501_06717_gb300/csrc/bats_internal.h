@@ -73,10 +73,10 @@ struct PhysDev {
   double gamma, gm1, inv_gm1;
   float gammaf, gm1f, inv_gm1f, padf_;
   int32_t limiter, rk, precision, b0, powell, learned;  // limiter 2: first order; rk 2: one stage
-  int32_t flux, padi_;                                  // FLUX_RUSANOV or FLUX_HLL
+  int32_t flux, padi_;                                  // FLUX_RUSANOV, FLUX_HLL or FLUX_LINDE
   double b0p[12];
 };
-enum { FLUX_RUSANOV = 0, FLUX_HLL = 1 };
+enum { FLUX_RUSANOV = 0, FLUX_HLL = 1, FLUX_LINDE = 2 };
 
 // Learned flux correction: network sizes and the device weight set (BF16
 // pairs in the layouts the tensor-core kernels read, FP32 biases).

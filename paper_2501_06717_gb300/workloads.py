@@ -34,7 +34,7 @@ BC_PERIODIC, BC_OUTFLOW, BC_INFLOW = 0, 1, 2
 LIM_MINMOD, LIM_MC, LIM_NONE = 0, 1, 2
 RK_MIDPOINT, RK_SSP2, RK_EULER = 0, 1, 2
 B0_NONE, B0_UNIFORM, B0_DIPOLE, B0_LINEAR = 0, 1, 2, 3
-FLUX_RUSANOV, FLUX_HLL = 0, 1
+FLUX_RUSANOV, FLUX_HLL, FLUX_LINDE = 0, 1, 2
 
 NC = 8  # cells per block per axis
 
@@ -63,7 +63,7 @@ class Problem:
     mlp: np.ndarray = None
     local_dt: int = 0
     reflux: int = 0
-    flux: int = 0               # FLUX_RUSANOV or FLUX_HLL
+    flux: int = 0               # FLUX_RUSANOV, FLUX_HLL or FLUX_LINDE
     learned_last_only: int = 0  # learned form: the correction in the last stage of a step only
 
     @property

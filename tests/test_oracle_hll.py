@@ -196,11 +196,13 @@ def test_hll_with_the_learned_correction_is_rejected():
     defined on the Rusanov flux only; unknown flux kinds are rejected too."""
     q = W.orszag_tang()
     assert O.validate(q) == 0
-    q.flux = W.FLUX_HLL
-    assert O.validate(q) == 0
-    q.learned = 1
-    q.mlp = np.zeros(O.MLP_NPARAM)
-    assert O.validate(q) != 0
-    q.learned = 0
-    q.flux = 2
-    assert O.validate(q) != 0
+    for flux in (W.FLUX_HLL, W.FLUX_LINDE):
+        q.flux = flux
+        assert O.validate(q) == 0
+        q.learned = 1
+        q.mlp = np.zeros(O.MLP_NPARAM)
+        assert O.validate(q) != 0
+        q.learned = 0
+    for flux in (-1, 3):
+        q.flux = flux
+        assert O.validate(q) != 0
