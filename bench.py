@@ -343,6 +343,29 @@ def other_workloads(stream, steps=20, fp64_steps=4):
                 row[pname] = prob.ncells * n / (e0.elapsed_time(e1) * 1e-3)
         del prob
         out[name] = row
+    # Section 5.1's one-GPU run: the Table 2 fast-wave grid at m = 6 (960
+    # blocks of 8^3 here; 10^3 in the paper) with the Linde flux, 500 steps at
+    # CFL 0.8, one CUDA graph of all 500 steps per precision
+    prob = W.fast_wave(m=6)
+    prob.flux = W.FLUX_LINDE
+    row = {"blocks": prob.nb, "cells": prob.ncells, "steps": 500, "flux": "linde",
+           "paper_table3_one_gpu_total_s": {"A100": 5.76, "V100": 7.68},
+           "paper_cells": prob.nb * 1000}
+    for pname, prec in (("mixed", bats.BATS_MIXED), ("fp64", bats.BATS_FP64)):
+        with bats.Solver(prob, precision=prec, stream=stream, persistent=1, use_graph=1) as s:
+            s.set_state(0, prob.U0)
+            s.step(500, prob.cfl)   # captures the 500-step graph
+            s.set_state(0, prob.U0)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.step(500, prob.cfl)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            sec = e0.elapsed_time(e1) * 1e-3
+            row[pname] = {"total_s": sec, "cell_updates_per_s": prob.ncells * 500 / sec}
+    out["fast_wave_table2_m6_linde_500_steps"] = row
     return out
 
 
@@ -408,6 +431,7 @@ def main():
     ap.add_argument("--learned-only", action="store_true", help="only the learned-form summary (profiling)")
     ap.add_argument("--no-others", action="store_true", help="skip the other paper-shaped grids")
     ap.add_argument("--mlp-only", action="store_true", help="only the standalone network inference (profiling)")
+    ap.add_argument("--others-only", action="store_true", help="only the other paper-shaped grids")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -419,6 +443,11 @@ def main():
         return run_reference(args, rank, world)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
+    if args.others_only:
+        import torch
+        torch.cuda.set_device(local)
+        print(json.dumps({"other_workloads_cell_updates_per_s": other_workloads(torch.cuda.Stream())}), flush=True)
+        return 0
     if args.mlp_only:
         import torch
         torch.cuda.set_device(local)

@@ -50,7 +50,7 @@ enum { BATS_LIM_MINMOD = 0, BATS_LIM_MC = 1, BATS_LIM_NONE = 2 };
 enum { BATS_RK_MIDPOINT = 0, BATS_RK_SSP2 = 1, BATS_RK_EULER = 2 };
 enum { BATS_FP64 = 0, BATS_MIXED = 1 };
 enum { BATS_B0_NONE = 0, BATS_B0_UNIFORM = 1, BATS_B0_DIPOLE = 2, BATS_B0_LINEAR = 3 };
-enum { BATS_FLUX_RUSANOV = 0, BATS_FLUX_HLL = 1 };
+enum { BATS_FLUX_RUSANOV = 0, BATS_FLUX_HLL = 1, BATS_FLUX_LINDE = 2 };
 enum { BATS_PHASE_STAGE = 0, BATS_PHASE_DT = 1, BATS_PHASE_TOTAL = 2, BATS_NUM_PHASES = 3 };
 
 typedef struct bats bats_t;
@@ -109,14 +109,21 @@ typedef struct {
  *                 round-off on periodic grids without sources.  Not with
  *                 `learned` (BATS_ERR_INVALID_ARG).
  *  flux           numerical face flux: BATS_FLUX_RUSANOV (Algorithm 1's
- *                 "calc_face_flux" with the Rusanov flux, the default), or
+ *                 "calc_face_flux" with the Rusanov flux, the default),
  *                 BATS_FLUX_HLL, the two-state Harten-Lax-van Leer flux with
  *                 the wave-speed bounds S_L = min(un_L - cf_L, un_R - cf_R),
- *                 S_R = max(un_L + cf_L, un_R + cf_R) (the base of the Linde
- *                 flux that Section 5 names; its contact-restoring term is not
- *                 given in the paper and not included).  HLL is not available
- *                 with `learned` (the correction is clipped by the Rusanov
- *                 dissipation): BATS_ERR_INVALID_ARG.
+ *                 S_R = max(un_L + cf_L, un_R + cf_R), or BATS_FLUX_LINDE, the
+ *                 flux of Section 5.1's runs (Linde 2002, cited without its
+ *                 formula): HLL with the contact wave restored,
+ *                 F = F_HLL - delta alpha S_L S_R / (S_R - S_L) r with
+ *                 alpha = minmod((rho_R - rho_L) - (p_R - p_L) / c^2,
+ *                 rho_R - rho_L) (the density jump no pressure jump carries,
+ *                 at most the density jump itself),
+ *                 delta = c / (c + |u_n|), r = (1, u, 0, |u|^2 / 2), u, rho, p
+ *                 the means of the two face states and c^2 = gamma p / rho.
+ *                 Neither HLL nor Linde is available with `learned` (the
+ *                 correction is clipped by the Rusanov dissipation):
+ *                 BATS_ERR_INVALID_ARG.
  *  learned_last_only  learned form: 1 = apply the correction in the last
  *                 stage of each two-stage step only (the stage whose fluxes
  *                 make U^{n+1}, and the one whose fine fluxes the training

@@ -632,8 +632,10 @@ static int in_body(const or_desc* d, const double x[3]) {
  *  dissipation S_L S_R / (S_R - S_L) (U_R - U_L) smears a density jump that no
  *  wave but the flow carries; the part of the jump along the contact's
  *  eigenvector r = (1, u, 0, |u|^2 / 2) (density, momentum, field, energy at
- *  fixed pressure, velocity and field), of strength alpha = (rho_R - rho_L)
- *  - (p_R - p_L) / c^2, is taken back out with the weight
+ *  fixed pressure, velocity and field), of strength alpha =
+ *  minmod((rho_R - rho_L) - (p_R - p_L) / c^2, rho_R - rho_L) (the density
+ *  jump not carried by the pressure jump, never more than the density jump
+ *  itself nor of the other sign), is taken back out with the weight
  *  delta = c / (c + |u_n|):  F = F_HLL - delta alpha S_L S_R / (S_R - S_L) r,
  *  with u, rho, p the means of the two face states and c^2 = gamma p / rho
  *  (reading 18).  `contact` scales the restored part (1 for the flux, 0 gives
@@ -655,7 +657,7 @@ static void numerical_flux(int kind, int dir, double gamma, const double WL[NV],
         double rho = 0.5 * (WL[0] + WR[0]), p = 0.5 * (WL[7] + WR[7]), u[3];
         for (int c = 0; c < 3; c++) u[c] = 0.5 * (WL[1 + c] + WR[1 + c]);
         double c2 = gamma * p / rho, cs = sqrt(c2);
-        double alpha = (WR[0] - WL[0]) - (WR[7] - WL[7]) / c2;
+        double alpha = minmod((WR[0] - WL[0]) - (WR[7] - WL[7]) / c2, WR[0] - WL[0]);
         double delta = cs / (cs + fabs(u[dir]));
         double q = contact * delta * alpha * SL * SR / (SR - SL);
         F[0] -= q;

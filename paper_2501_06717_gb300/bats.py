@@ -29,7 +29,7 @@ BATS_LIM_MINMOD, BATS_LIM_MC, BATS_LIM_NONE = 0, 1, 2
 BATS_RK_MIDPOINT, BATS_RK_SSP2, BATS_RK_EULER = 0, 1, 2
 BATS_FP64, BATS_MIXED = 0, 1
 BATS_B0_NONE, BATS_B0_UNIFORM, BATS_B0_DIPOLE, BATS_B0_LINEAR = 0, 1, 2, 3
-BATS_FLUX_RUSANOV, BATS_FLUX_HLL = 0, 1
+BATS_FLUX_RUSANOV, BATS_FLUX_HLL, BATS_FLUX_LINDE = 0, 1, 2
 BATS_PHASE_STAGE, BATS_PHASE_DT, BATS_PHASE_TOTAL, BATS_NUM_PHASES = 0, 1, 2, 3
 
 

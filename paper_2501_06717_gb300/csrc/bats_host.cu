@@ -753,7 +753,7 @@ int bats_create(const bats_grid_desc* grids, int n_grids, const bats_physics* ph
   if (!(phys->gamma > 1.0)) return fail(nullptr, BATS_ERR_INVALID_ARG, "gamma must exceed 1");
   if (phys->reflux && phys->learned)
     return fail(nullptr, BATS_ERR_INVALID_ARG, "refluxing is not available with the learned correction");
-  if (phys->flux < BATS_FLUX_RUSANOV || phys->flux > BATS_FLUX_HLL)
+  if (phys->flux < BATS_FLUX_RUSANOV || phys->flux > BATS_FLUX_LINDE)
     return fail(nullptr, BATS_ERR_INVALID_ARG, "bad flux kind");
   if (phys->flux != BATS_FLUX_RUSANOV && phys->learned)
     return fail(nullptr, BATS_ERR_INVALID_ARG, "the learned correction is defined on the Rusanov flux only");

@@ -278,7 +278,7 @@ extern "C" int bats_step_noalloc(const bats_grid_desc* grid, const bats_physics*
   if (phys->precision != BATS_FP64 || phys->learned)
     return report(err, err_len, BATS_ERR_INVALID_ARG, "bats_step_noalloc runs the FP64 form only");
   if (phys->limiter < 0 || phys->limiter > 2 || phys->rk < 0 || phys->rk > 2 || phys->b0 < 0 || phys->b0 > 3 ||
-      phys->flux < BATS_FLUX_RUSANOV || phys->flux > BATS_FLUX_HLL)
+      phys->flux < BATS_FLUX_RUSANOV || phys->flux > BATS_FLUX_LINDE)
     return report(err, err_len, BATS_ERR_INVALID_ARG, "bad physics enumeration");
   // options that change the physics and need buffers this entry point does
   // not keep (the flux register, the per-cell time steps): refused, never

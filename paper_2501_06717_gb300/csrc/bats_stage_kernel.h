@@ -1024,12 +1024,13 @@ __device__ __forceinline__ float limit_f(float a, float b) {
   else return minmod_med(a, b);
 }
 
-// Twice the numerical flux (Rusanov or HLL) of one face in the face frame from
+// Twice the numerical flux (Rusanov, HLL or Linde) of one face in the face frame from
 // the pairs W2[v] = (left, right) of reconstructed primitives and the face's
 // B0 (components in the frame).  The same physics as phys_flux + the flux
 // combination of the generic path: split-field flux, fast speed with the
 // total field, F = (F_L + F_R)/2 - cmax (U_R - U_L)/2 with cmax the larger
-// |u_n| + c_f (Rusanov), or the two-state HLL flux.
+// |u_n| + c_f (Rusanov), the two-state HLL flux, or HLL with the contact wave
+// restored (Linde).
 // dsgn = 1: W2 = (left, right); dsgn = -1: W2 = (right, left).
 template <bool HAS_B0, int FLX>
 __device__ __forceinline__ void face_flux2(const float2 W2[8], const float B0r[3], float gamma, float inv_gm1,
@@ -1056,7 +1057,8 @@ __device__ __forceinline__ void face_flux2(const float2 W2[8], const float B0r[3
   const float2 cf = make_float2(sqrt_approx(t.x), sqrt_approx(t.y));
   // coefficients of the combination 2F = sum over the two sides of (cF F + cU U)
   float2 cF = p_bc(1.f), cU;
-  if constexpr (FLX == FLUX_HLL) {
+  float lq = 0.f;  // Linde: twice the restored contact part's weight, delta alpha S_L S_R / (S_R - S_L)
+  if constexpr (FLX == FLUX_HLL || FLX == FLUX_LINDE) {
     // S_L = min(unL - cfL, unR - cfR, 0), S_R = max(unL + cfL, unR + cfR, 0),
     // F = F_L - k ((F_R - F_L) - S_R (U_R - U_L)), k = S_L / (S_R - S_L)
     const float2 lo = p_fma(cf, p_bc(-1.f), u0), hi = p_add(u0, cf);
@@ -1066,12 +1068,24 @@ __device__ __forceinline__ void face_flux2(const float2 W2[8], const float B0r[3
     cF = dsgn > 0.f ? make_float2(2.f + k2, -k2) : make_float2(-k2, 2.f + k2);
     const float ks = dsgn * (k2 * sr);
     cU = make_float2(-ks, ks);
+    if constexpr (FLX == FLUX_LINDE) {
+      // the contact wave restored: alpha = minmod((rho_R - rho_L) - (p_R - p_L)
+      // / c^2, rho_R - rho_L), delta = c / (c + |u_n|), with the means of the
+      // two sides and c^2 = gamma p / rho (W2's order is (left, right) when
+      // dsgn = 1)
+      const float rm = 0.5f * p_sum(rho), pm = 0.5f * p_sum(p);
+      const float c2 = gamma * pm * rcp_approx(rm), cs = sqrt_approx(c2);
+      const float drho = dsgn * (rho.y - rho.x);
+      const float alpha = minmod_med(drho - dsgn * (p.y - p.x) * rcp_approx(c2), drho);
+      const float delta = cs * rcp_approx(cs + fabsf(0.5f * p_sum(u0)));
+      lq = den > 0.f ? 2.f * delta * alpha * (sl * sr) * rcp_approx(den) : 0.f;
+    }
   } else {
     const float cmax = dsgn * fmaxf(fabsf(u0.x) + cf.x, fabsf(u0.y) + cf.y);
     cU = make_float2(cmax, -cmax);
   }
   auto comb = [&](float2 F, float2 U) -> float {
-    if constexpr (FLX == FLUX_HLL) return p_sum(p_fma(F, cF, p_mul(U, cU)));
+    if constexpr (FLX == FLUX_HLL || FLX == FLUX_LINDE) return p_sum(p_fma(F, cF, p_mul(U, cU)));
     else return p_sum(p_fma(U, cU, F));
   };
   // split-field physical fluxes of both sides
@@ -1098,11 +1112,18 @@ __device__ __forceinline__ void face_flux2(const float2 W2[8], const float B0r[3
   Fr2[1] = comb(F1, m0);
   Fr2[2] = comb(F2, m1);
   Fr2[3] = comb(F3, m2);
-  if constexpr (FLX == FLUX_HLL) Fr2[4] = p_sum(p_mul(b0, cU));
-  else Fr2[4] = p_sum(p_mul(b0, cU));
+  Fr2[4] = p_sum(p_mul(b0, cU));
   Fr2[5] = comb(F5, b1);
   Fr2[6] = comb(F6, b2);
   Fr2[7] = comb(F7, e1);
+  if constexpr (FLX == FLUX_LINDE) {
+    const float um0 = 0.5f * p_sum(u0), um1 = 0.5f * p_sum(u1), um2 = 0.5f * p_sum(u2);
+    Fr2[0] -= lq;
+    Fr2[1] -= lq * um0;
+    Fr2[2] -= lq * um1;
+    Fr2[3] -= lq * um2;
+    Fr2[7] -= lq * 0.5f * (um0 * um0 + um1 * um1 + um2 * um2);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1891,7 +1912,7 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, (MIXED && !LRN) ? 2 
             R cmax = aL > aR ? aL : aR;
             const int fi = chki(fline * 9 + (f < 9 ? f : 8), 0, NFACE);  // (f = 9: the throw-away step)
             R Fr[8];
-            if constexpr (FLX == FLUX_HLL) {
+            if constexpr (FLX == FLUX_HLL || FLX == FLUX_LINDE) {
               // HLL with S_L = min(unL - cfL, unR - cfR, 0), S_R = max(unL + cfL,
               // unR + cfR, 0):  F = F_L - S_L/(S_R - S_L) ((F_R - F_L) - S_R (U_R - U_L)),
               // which is F_L when every wave moves right (S_L = 0), F_R when every
@@ -1905,6 +1926,24 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, (MIXED && !LRN) ? 2 
               const R kk = den > zero ? Ops<R>::div_(sl, den) : zero;
 #pragma unroll
               for (int v = 0; v < NV; v++) Fr[v] = FL[v] - kk * ((FR[v] - FL[v]) - sr * (UR[v] - UL[v]));
+              if constexpr (FLX == FLUX_LINDE) {
+                // Linde: the contact wave restored, F -= delta alpha S_L S_R / (S_R - S_L) r,
+                // alpha = minmod((rho_R - rho_L) - (p_R - p_L) / c^2, rho_R - rho_L),
+                // delta = c / (c + |u_n|), r = (1, u, 0, |u|^2 / 2), means of the two
+                // face states, c^2 = gamma p / rho
+                const R rm = R(0.5) * (WL[0] + WR[0]), pm = R(0.5) * (WL[7] + WR[7]);
+                const R um0 = R(0.5) * (WL[1] + WR[1]), um1 = R(0.5) * (WL[2] + WR[2]),
+                        um2 = R(0.5) * (WL[3] + WR[3]);
+                const R c2 = Ops<R>::div_(gamma * pm, rm), cs = Ops<R>::sqrt_(c2);
+                const R alpha = minmod_<R>((WR[0] - WL[0]) - Ops<R>::div_(WR[7] - WL[7], c2), WR[0] - WL[0]);
+                const R delta = Ops<R>::div_(cs, cs + Ops<R>::abs_(um0));
+                const R q = den > zero ? Ops<R>::div_(delta * alpha * (sl * sr), den) : zero;
+                Fr[0] -= q;
+                Fr[1] -= q * um0;
+                Fr[2] -= q * um1;
+                Fr[3] -= q * um2;
+                Fr[7] -= q * (R(0.5) * ((um0 * um0 + um1 * um1) + um2 * um2));
+              }
             } else {
 #pragma unroll
               for (int v = 0; v < NV; v++) Fr[v] = R(0.5) * (FL[v] + FR[v]) - R(0.5) * cmax * (UR[v] - UL[v]);

@@ -112,12 +112,12 @@ def test_binding_refuses_to_run_without_the_library(tmp_path, monkeypatch):
 
 
 def test_create_rejects_bad_options_and_empty_grids(libbats):
-    """Unknown enumerations, refluxing or the HLL flux with the learned
-    correction, and an empty leaf list are refused on the host, before any
-    CUDA call."""
+    """Unknown enumerations, refluxing or the HLL or Linde flux with the
+    learned correction, and an empty leaf list are refused on the host, before
+    any CUDA call."""
     root = (2, 2, 2)
     q = W.Problem("v", (0, 0, 0), (1, 1, 1), root, W.as_leaf_array(W.uniform_leaves(root)), (W.BC_PERIODIC,) * 6)
-    for field, bad in (("limiter", 3), ("rk", 3), ("local_dt", 2), ("flux", 2), ("flux", -1)):
+    for field, bad in (("limiter", 3), ("rk", 3), ("local_dt", 2), ("flux", 3), ("flux", -1)):
         ph = libbats.physics_from(q)
         setattr(ph, field, bad)
         with pytest.raises(libbats.BatsError) as e:
@@ -129,11 +129,12 @@ def test_create_rejects_bad_options_and_empty_grids(libbats):
     with pytest.raises(libbats.BatsError) as e:
         libbats.bats_create([q], ph)
     assert e.value.code == libbats.BATS_ERR_INVALID_ARG and "reflux" in str(e.value)
-    ph = libbats.physics_from(q)
-    ph.flux = libbats.BATS_FLUX_HLL
-    ph.learned = 1
-    with pytest.raises(libbats.BatsError) as e:
-        libbats.bats_create([q], ph)
-    assert e.value.code == libbats.BATS_ERR_INVALID_ARG and "Rusanov" in str(e.value)
+    for flux in (libbats.BATS_FLUX_HLL, libbats.BATS_FLUX_LINDE):
+        ph = libbats.physics_from(q)
+        ph.flux = flux
+        ph.learned = 1
+        with pytest.raises(libbats.BatsError) as e:
+            libbats.bats_create([q], ph)
+        assert e.value.code == libbats.BATS_ERR_INVALID_ARG and "Rusanov" in str(e.value)
     q.leaves = np.zeros((0, 4), np.int32)
     assert _create_code(libbats, q)[0] == libbats.BATS_ERR_INVALID_ARG
