@@ -34,7 +34,6 @@ constexpr int TC_TILE = 128;        // rows per tile (MMA M = tensor-memory lane
 constexpr int TC_STREAMS = 4;       // tiles in flight per CTA (one CTA per SM)
 constexpr int TC_THREADS = 32 * 4 * TC_STREAMS;  // four warps per stream
 constexpr int TC_TMEM_COLS = 512;   // two regions of 64 columns per stream
-constexpr uint32_t SBO_K80 = 1280;  // 16 bytes x K = 80
 struct TcSmem {
   alignas(128) uint8_t w1[64 * 96];   // B of layer 1: N = 64, K = 48
   alignas(128) uint8_t w2[64 * 160];  // B of layer 2: N = 64, K = 80 (weights halved)
@@ -46,14 +45,6 @@ struct TcSmem {
 __device__ __forceinline__ void mbar_init_count(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc_saddr(bar)), "r"(count) : "memory");
 }
-// true in one lane of the (converged) warp
-__device__ __forceinline__ bool elect_one() {
-  uint32_t pred;
-  asm volatile(
-      "{\n .reg .b32 r;\n .reg .pred p;\n elect.sync r|p, 0xffffffff;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(pred));
-  return pred != 0;
-}
 // D[tmem] (+)= A B^T for one K = 16 slice, A (M = 128 rows = lanes, K packed
 // two BF16 per 32-bit column, 8 columns per slice) in tensor memory
 __device__ __forceinline__ void umma_bf16_ts(uint32_t dtmem, uint32_t atmem, uint64_t bdesc, uint32_t idesc,
@@ -63,23 +54,6 @@ __device__ __forceinline__ void umma_bf16_ts(uint32_t dtmem, uint32_t atmem, uin
       " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(dtmem),
       "r"(atmem), "l"(bdesc), "r"(idesc), "r"(accum)
       : "memory");
-}
-// 32 consecutive FP32 columns of this thread's tensor-memory lane, the wait
-// for the load in the same statement.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-      "tcgen05.wait::ld.sync.aligned;\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr)
-      : "memory");
-#pragma unroll
-  for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
 }
 // 16 + 8 (x24) or 32 + 8 (x40) words into consecutive columns of this
 // thread's lane, waiting for the stores

@@ -1553,17 +1553,19 @@ constexpr int TC_TILE_F = 128;  // rows per tensor-core tile (MMA M = tensor-mem
 // M = 128, K = 16 per instruction, BF16 operands from shared memory in the
 // no-swizzle K-major canonical layout, FP32 accumulators in tensor memory,
 // 64 columns per tile), each thread turning its own row's accumulator into
-// the next layer's BF16 operand (bias, GELU) and, after the last layer, into
-// its own face's correction.
+// the next layer's BF16 operand and, after the last layer, into its own
+// face's correction.  As in the inference kernel the biases ride in the
+// products (ones in the inputs' and activations' bias columns, the bias
+// pairs in the weights) and the hidden activations are twice the GELU (the
+// next layer's weights halved).
 
 struct LrnSmem {
-  alignas(128) uint8_t x[3][TC_TILE_F * 96];   // inputs, K = 48 (40 features, 8 zeros)
-  alignas(128) uint8_t h[3][TC_TILE_F * 128];  // hidden activations, K = 64
+  alignas(128) uint8_t x[3][TC_TILE_F * 96];   // inputs, K = 48 (40 features, the bias columns, zeros)
+  alignas(128) uint8_t h[3][TC_TILE_F * 160];  // hidden activations, K = 80 (64, the bias columns, zeros)
   alignas(128) uint8_t w1[64 * 96];             // B of layer 1: N = 64, K = 48
-  alignas(128) uint8_t w2[64 * 128];            // B of layer 2: N = 64, K = 64
-  alignas(128) uint8_t w3[16 * 128];            // B of layer 3: N = 16 (8 outputs, 8 zero rows), K = 64
-  float b1[64], b2[64], b3[8];
-  uint64_t bar;                                 // MMA completion
+  alignas(128) uint8_t w2[64 * 160];            // B of layer 2: N = 64, K = 80 (weights halved)
+  alignas(128) uint8_t w3[16 * 160];            // B of layer 3: N = 16 (8 outputs, 8 zero rows), K = 80 (halved)
+  uint64_t bar[3];                              // MMA completion, per tile (warp group)
   uint32_t tmem;
 };
 constexpr int LRN_TMEM_COLS = 256;  // 3 tiles x 64 columns, rounded up to a power of two
@@ -1571,39 +1573,43 @@ constexpr int LRN_TMEM_COLS = 256;  // 3 tiles x 64 columns, rounded up to a pow
 // fused network's operands and weights (128-byte aligned)
 constexpr size_t kSmemLx = (sizeof(float) * (NV * NTILE + 3 * 9 * NFACE) + 127) / 128 * 128 + sizeof(LrnSmem) + 128;
 
-// Weights and biases into shared memory (all threads), tensor memory and
-// the MMA barrier (warp 0, thread 0).
+// Weights into shared memory and the constant columns of the activation
+// tiles (all threads), tensor memory and the MMA barrier (warp 0, thread 0).
 __device__ __forceinline__ void lrn_setup(LrnSmem& s, const MlpDev& m, int tid, int nthr) {
   for (int e = tid; e < 64 * 6; e += nthr) {
     const int r = e / 6, kc = e % 6;
-    *reinterpret_cast<uint4*>(s.w1 + cm_off(r, kc, SBO_K48)) = *reinterpret_cast<const uint4*>(m.w1 + r * 24 + kc * 4);
+    *reinterpret_cast<uint4*>(s.w1 + cm_off(r, kc, SBO_K48)) = *reinterpret_cast<const uint4*>(m.w1b + r * 24 + kc * 4);
   }
-  for (int e = tid; e < 64 * 8; e += nthr) {
-    const int r = e / 8, kc = e % 8;
-    *reinterpret_cast<uint4*>(s.w2 + cm_off(r, kc, SBO_K64)) = *reinterpret_cast<const uint4*>(m.w2 + r * 32 + kc * 4);
+  for (int e = tid; e < 64 * 10; e += nthr) {
+    const int r = e / 10, kc = e % 10;
+    *reinterpret_cast<uint4*>(s.w2 + cm_off(r, kc, SBO_K80)) = *reinterpret_cast<const uint4*>(m.w2b + r * 40 + kc * 4);
   }
-  for (int e = tid; e < 16 * 8; e += nthr) {
-    const int r = e / 8, kc = e % 8;
-    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
-    *reinterpret_cast<uint4*>(s.w3 + cm_off(r, kc, SBO_K64)) =
-        r < 8 ? *reinterpret_cast<const uint4*>(m.w3 + r * 32 + kc * 4) : z;
+  for (int e = tid; e < 16 * 10; e += nthr) {
+    const int r = e / 10, kc = e % 10;
+    *reinterpret_cast<uint4*>(s.w3 + cm_off(r, kc, SBO_K80)) = *reinterpret_cast<const uint4*>(m.w3b + r * 40 + kc * 4);
   }
-  if (tid < 64) {
-    s.b1[tid] = m.b1[tid];
-    s.b2[tid] = m.b2[tid];
+  const uint4 ones = make_uint4(pack_bf16(1.f, 1.f), 0u, 0u, 0u), zero = make_uint4(0u, 0u, 0u, 0u);
+  for (int e = tid; e < 3 * TC_TILE_F; e += nthr) {
+    uint8_t* h = s.h[e / TC_TILE_F];
+    *reinterpret_cast<uint4*>(h + cm_off(e % TC_TILE_F, 8, SBO_K80)) = ones;
+    *reinterpret_cast<uint4*>(h + cm_off(e % TC_TILE_F, 9, SBO_K80)) = zero;
   }
-  if (tid < 8) s.b3[tid] = m.b3[tid];
   if (tid < 32) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_saddr(&s.tmem)),
                  "r"(LRN_TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  if (tid == 0) mbar_init_tc(&s.bar);
+  if (tid == 0) {
+    mbar_init_tc(&s.bar[0]);
+    mbar_init_tc(&s.bar[1]);
+    mbar_init_tc(&s.bar[2]);
+  }
 }
-__device__ __forceinline__ void lrn_teardown(LrnSmem& s, int tid, bool failed, uint32_t phase, int32_t* err) {
-  // an MMA may still run after a timed-out wait: wait for it once more
-  if (failed && tid == 0) mbar_wait_bounded_tc(&s.bar, phase, err);
+// pending: this thread's last wait on its group's barrier ran out (the group's
+// MMAs may still run): its group leader waits for them once more.
+__device__ __forceinline__ void lrn_teardown(LrnSmem& s, int tid, bool pending, uint32_t phase, int32_t* err) {
+  if (pending && (tid & 127) == 0) mbar_wait_bounded_tc(&s.bar[tid >> 7], phase, err);
   tc_fence_before();
   __syncthreads();
   if (tid < 32) {
@@ -1613,75 +1619,92 @@ __device__ __forceinline__ void lrn_teardown(LrnSmem& s, int tid, bool failed, u
   }
 }
 
-// Layer `layer` (0, 1, 2) of all three tiles: thread 0 issues the MMAs and
-// commits them; every thread waits (bounded).  false when the wait ran out.
-__device__ __forceinline__ bool lrn_layer(LrnSmem& s, int layer, int tid, uint32_t& phase, int32_t* err) {
+// A barrier of the 128 threads of warp group g (named barrier 1 + g) that
+// returns whether any of them passed `bad`.
+__device__ __forceinline__ bool group_sync_or(int g, bool bad) {
+  uint32_t any;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %2, 128, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(any)
+      : "r"(bad ? 1u : 0u), "r"(1 + g)
+      : "memory");
+  return any != 0;
+}
+
+// Layer `layer` (0, 1, 2) of this warp group's tile (the groups run apart:
+// each hands its tile to the tensor cores and waits for its own products
+// while the others compute): after a barrier of the group, one elected
+// thread of its first warp issues the MMAs (descriptors built
+// warp-uniformly; K slice k: 256 bytes further, 16 in the descriptor's
+// address field) and commits them to the group's barrier; every thread of
+// the group waits (bounded).  false for the whole group when some wait ran
+// out (pending then marks the threads whose own wait did).
+__device__ __forceinline__ bool lrn_layer(LrnSmem& s, int layer, int tid, uint32_t& phase, bool& pending,
+                                          int32_t* err) {
+  const int g = tid >> 7;
   proxy_fence_smem();
   tc_fence_before();
-  __syncthreads();
-  if (tid == 0) {
-    tc_fence_after();
-    const uint32_t ID64 = umma_idesc_bf16(TC_TILE_F, 64), ID16 = umma_idesc_bf16(TC_TILE_F, 16);
-#pragma unroll
-    for (int t = 0; t < 3; t++) {
-      const uint32_t d = s.tmem + 64 * t;
+  group_sync_or(g, false);
+  if ((tid & 127) < 32) {
+    constexpr uint32_t ID64 = umma_idesc_bf16(TC_TILE_F, 64), ID16 = umma_idesc_bf16(TC_TILE_F, 16);
+    const uint64_t bw = layer == 0 ? umma_sdesc(tc_saddr(s.w1), 128, SBO_K48)
+                                   : umma_sdesc(tc_saddr(layer == 1 ? s.w2 : s.w3), 128, SBO_K80);
+    const uint64_t ba = layer == 0 ? umma_sdesc(tc_saddr(s.x[g]), 128, SBO_K48)
+                                   : umma_sdesc(tc_saddr(s.h[g]), 128, SBO_K80);
+    if (elect_one()) {
+      tc_fence_after();
+      const uint32_t d = s.tmem + 64 * g;
       if (layer == 0) {
-        const uint32_t xs = tc_saddr(s.x[t]), ws = tc_saddr(s.w1);
 #pragma unroll
-        for (int k = 0; k < 3; k++)
-          umma_bf16(d, umma_sdesc(xs + 256 * k, 128, SBO_K48), umma_sdesc(ws + 256 * k, 128, SBO_K48), ID64, k > 0);
+        for (int k = 0; k < 3; k++) umma_bf16(d, ba + 16 * k, bw + 16 * k, ID64, k);
       } else {
-        const uint32_t hs = tc_saddr(s.h[t]), ws = tc_saddr(layer == 1 ? s.w2 : s.w3);
 #pragma unroll
-        for (int k = 0; k < 4; k++)
-          umma_bf16(d, umma_sdesc(hs + 256 * k, 128, SBO_K64), umma_sdesc(ws + 256 * k, 128, SBO_K64),
-                    layer == 1 ? ID64 : ID16, k > 0);
+        for (int k = 0; k < 5; k++) umma_bf16(d, ba + 16 * k, bw + 16 * k, layer == 1 ? ID64 : ID16, k);
       }
+      umma_commit(&s.bar[g]);
     }
-    umma_commit(&s.bar);
+    __syncwarp();
   }
-  const bool got = mbar_wait_bounded_tc(&s.bar, phase, err);
-  if (__syncthreads_or(!got)) return false;  // phase kept: the teardown waits on it once more
+  const bool got = mbar_wait_bounded_tc(&s.bar[g], phase, err);
+  if (!got) pending = true;
+  if (group_sync_or(g, !got)) return false;  // phase kept: the teardown waits on it once more
   phase ^= 1u;
   tc_fence_after();
   return true;
 }
 
 // The network for this thread's face (row tid % 128 of tile tid / 128):
-// xrow its 48 BF16 inputs (6 chunks of 8), y its 8 outputs.  false (for
-// every thread) when a wait ran out.
+// xrow its 48 BF16 inputs (6 chunks of 8; the last chunk is replaced by the
+// bias columns), y its 8 outputs.  false (for every thread of the warp group)
+// when a wait ran out.
 __device__ __forceinline__ bool lrn_network(LrnSmem& s, const uint4 xrow[6], float y[8], int tid, uint32_t& phase,
-                                            int32_t* err) {
+                                            bool& pending, int32_t* err) {
   const int tile = tid >> 7, row = tid & 127;
   const uint32_t tl = s.tmem + (static_cast<uint32_t>(32 * ((tid >> 5) & 3)) << 16) + 64 * tile;
 #pragma unroll
-  for (int kc = 0; kc < 6; kc++) *reinterpret_cast<uint4*>(s.x[tile] + cm_off(row, kc, SBO_K48)) = xrow[kc];
+  for (int kc = 0; kc < 5; kc++) *reinterpret_cast<uint4*>(s.x[tile] + cm_off(row, kc, SBO_K48)) = xrow[kc];
+  *reinterpret_cast<uint4*>(s.x[tile] + cm_off(row, 5, SBO_K48)) = make_uint4(pack_bf16(1.f, 1.f), 0u, 0u, 0u);
 #pragma unroll 1
   for (int layer = 0; layer < 2; layer++) {
-    if (!lrn_layer(s, layer, tid, phase, err)) return false;
-    const float* bias = layer == 0 ? s.b1 : s.b2;
+    if (!lrn_layer(s, layer, tid, phase, pending, err)) return false;
 #pragma unroll
-    for (int q = 0; q < 4; q++) {
-      float v[16];
-      tmem_ld16(tl + 16 * q, v);
+    for (int q = 0; q < 2; q++) {
+      float z[32];
+      tmem_ld32(tl + 32 * q, z);
 #pragma unroll
-      for (int c = 0; c < 2; c++) {
-        const float* b = bias + 16 * q + 8 * c;
-        const float* z = v + 8 * c;
-        uint4 o;
-        o.x = gelu2_pack(z[0] + b[0], z[1] + b[1]);
-        o.y = gelu2_pack(z[2] + b[2], z[3] + b[3]);
-        o.z = gelu2_pack(z[4] + b[4], z[5] + b[5]);
-        o.w = gelu2_pack(z[6] + b[6], z[7] + b[7]);
-        *reinterpret_cast<uint4*>(s.h[tile] + cm_off(row, 2 * q + c, SBO_K64)) = o;
+      for (int c = 0; c < 4; c++) {
+        const float* v = z + 8 * c;
+        *reinterpret_cast<uint4*>(s.h[tile] + cm_off(row, 4 * q + c, SBO_K80)) =
+            make_uint4(gelu2x_pack(v[0], v[1]), gelu2x_pack(v[2], v[3]), gelu2x_pack(v[4], v[5]),
+                       gelu2x_pack(v[6], v[7]));
       }
     }
   }
-  if (!lrn_layer(s, 2, tid, phase, err)) return false;
+  if (!lrn_layer(s, 2, tid, phase, pending, err)) return false;
   float v[16];
   tmem_ld16(tl, v);
 #pragma unroll
-  for (int k = 0; k < 8; k++) y[k] = v[k] + s.b3[k];
+  for (int k = 0; k < 8; k++) y[k] = v[k];
   return true;
 }
 
@@ -1718,7 +1741,8 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, (MIXED && !LRN) ? 2 
   }
   const bool fused = LX && a.learned && a.kind < 3;
   uint32_t mphase = 0;
-  bool mfail = false;  // a tensor-core wait ran out (uniform over the CTA)
+  bool mfail = false;  // a tensor-core wait ran out (uniform over the warp group, then the CTA)
+  bool mpending = false;  // this thread's own wait ran out
   __shared__ uint64_t bar;
   __shared__ R sred[STAGE_THREADS / 32];
 
@@ -2027,7 +2051,7 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, (MIXED && !LRN) ? 2 
                                        pack_bf16(xin[8 * q + 6], xin[8 * q + 7]));
                 xrow[5] = make_uint4(0u, 0u, 0u, 0u);
                 float yv[8];
-                if (!lrn_network(*ls, xrow, yv, tid, mphase, a.err)) {
+                if (!lrn_network(*ls, xrow, yv, tid, mphase, mpending, a.err)) {
                   mfail = true;
                   break;
                 }
@@ -2342,8 +2366,11 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, (MIXED && !LRN) ? 2 
       } else {
         if (tid < FACE_THREADS) faces(true);
       }
-      if (mfail) break;  // a tensor-core wait ran out: the error is flagged, stop
-      __syncthreads();
+      // a tensor-core wait ran out in some warp group: the error is flagged, stop
+      if (__syncthreads_or(mfail)) {
+        mfail = true;
+        break;
+      }
       // the staged tile's next block (its copies go out once this block's
       // cell phase has read what it needs from the tile)
       const int nblk = blk + 1 < b_end ? blk + 1 : (item + static_cast<int>(gridDim.x)) * a.blocks_per_item;
@@ -2407,7 +2434,7 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, (MIXED && !LRN) ? 2 
     if (mfail) break;
   }
   if constexpr (LX) {
-    if (fused) lrn_teardown(*ls, tid, mfail, mphase, a.err);
+    if (fused) lrn_teardown(*ls, tid, mpending, mphase, a.err);
   }
 }
 
