@@ -92,6 +92,28 @@ def test_network_forward_ragged_sizes(B, n):
     assert _relnorm(Y, Yr) <= 2e-3
 
 
+@pytest.mark.parametrize("n", [1, 129, 70001])
+def test_forward_bf16_equals_forward_bitwise(B, n):
+    """The queued entry on pre-rounded BF16 rows gives the synchronous
+    forward's outputs bit for bit (the same kernel on the same rows)."""
+    import torch
+    P = _net(13)
+    rng = np.random.default_rng(300 + n)
+    X = bf16(rng.normal(size=(n, 40)))
+    m = B.Mlp(P)
+    Y = m.forward(X)
+    Xh = torch.zeros(n, 48, dtype=torch.bfloat16)
+    Xh[:, :40] = torch.from_numpy(X).to(torch.bfloat16)
+    Xb = Xh.view(torch.int32).cuda()
+    Yd = torch.empty(n, 8, device="cuda")
+    m.forward_bf16(Xb, Yd)
+    m.sync()
+    assert np.array_equal(Yd.cpu().numpy().view(np.uint32), Y.view(np.uint32))
+    with pytest.raises(B.BatsError):
+        m.forward_bf16(Xb.cpu(), Yd)  # host buffers are refused
+    m.close()
+
+
 def test_network_gradient_matches_oracle(B):
     P = _net(3)
     rng = np.random.default_rng(4)
