@@ -197,10 +197,11 @@ int bats_get_time(bats_t* h, int grid, double* t);
 
 /* Milliseconds of device time of the last bats_step call, by phase
  * (BATS_PHASE_*), from CUDA events on the handle's stream: ms[0] the stage
- * kernels (events bracket the two stage launches of each step; beyond 256
- * steps the first 256 are scaled), ms[1] everything else (time-step
- * bookkeeping kernels), ms[2] total.  With CUDA-graph replay the per-stage
- * events are not recorded and ms[0] = ms[1] = -1.  n = entries in ms. */
+ * kernels (events bracket the two stage launches of each step, the mixed
+ * form's ghost pre-pass included; beyond 256 steps the first 256 are
+ * scaled), ms[1] everything else (time-step bookkeeping kernels), ms[2]
+ * total.  Under CUDA-graph replay the stage events are event nodes of the
+ * graph, recorded by every replay.  n = entries in ms. */
 int bats_get_timings(bats_t* h, double* ms, int n);
 
 /* Debug view of the ghost fill (Section 4.1-4.2) for the current state:

@@ -103,6 +103,7 @@ struct bats {
   int graph_n = -1;
   double graph_cfl = 0, graph_dt = 0;
   long long graph_launches = 0;
+  int graph_timed = 0;                 // steps whose stage events the graph records
   // learned form
   bool learned_requested = false, learned = false;
   bool learned_last_only = false;  // the correction in the last stage of a step only
@@ -545,8 +546,10 @@ int ensure_stage_events(bats_t* h, int n) {
 }
 
 // Enqueue n steps (no synchronisation).  The stage launches of each of the
-// first kMaxTimedSteps steps are bracketed by an event pair.
-int enqueue_steps(bats_t* h, int n, double cfl, double fixed_dt, bool timed) {
+// first kMaxTimedSteps steps are bracketed by an event pair: recorded on the
+// stream (timed) or, while a CUDA graph is captured (captured), as event
+// nodes of the graph, which its every replay records.
+int enqueue_steps(bats_t* h, int n, double cfl, double fixed_dt, bool timed, bool captured = false) {
   const bool mixed = h->ph.precision == BATS_MIXED;
   const bool ssp = h->ph.rk == BATS_RK_SSP2;
   const bool euler = h->ph.rk == BATS_RK_EULER;
@@ -555,8 +558,11 @@ int enqueue_steps(bats_t* h, int n, double cfl, double fixed_dt, bool timed) {
     int rc0 = ensure_stage_events(h, n);
     if (rc0) return rc0;
   }
-  h->timed_steps = timed ? std::min(n, kMaxTimedSteps) : 0;
+  h->timed_steps = (timed || captured) ? std::min(n, kMaxTimedSteps) : 0;
   const int ntimed = h->timed_steps;
+  auto record = [&](cudaEvent_t ev) {
+    return captured ? cudaEventRecordWithFlags(ev, h->stream, cudaEventRecordExternal) : cudaEventRecord(ev, h->stream);
+  };
   if (lts && n > 0) {
     // every cell's dt from the current state (later steps take it from the
     // last stage of the step before)
@@ -574,7 +580,7 @@ int enqueue_steps(bats_t* h, int n, double cfl, double fixed_dt, bool timed) {
   for (int s = 0; s < n; s++) {
     CK(h, launch_dt(h->ngrids, 0, cfl, fixed_dt, h->dt, h->t, h->smax, h->smax_next, h->stream));
     h->launches++;
-    if (s < ntimed) CK(h, cudaEventRecord(h->stage_ev[2 * s], h->stream));
+    if (s < ntimed) CK(h, record(h->stage_ev[2 * s]));
     StageArgs a = base_args(h);
     a.dtc = lts ? h->dtc : nullptr;
     a.cfl = cfl;
@@ -620,7 +626,7 @@ int enqueue_steps(bats_t* h, int n, double cfl, double fixed_dt, bool timed) {
       rc = launch_stage(h, a);
       if (rc) return rc;
     }
-    if (s < ntimed) CK(h, cudaEventRecord(h->stage_ev[2 * s + 1], h->stream));
+    if (s < ntimed) CK(h, record(h->stage_ev[2 * s + 1]));
     CK(h, launch_dt(h->ngrids, 1, cfl, fixed_dt, h->dt, h->t, h->smax, h->smax_next, h->stream));
     h->launches++;
   }
@@ -654,10 +660,12 @@ int run_steps(bats_t* h, int n, double cfl, double fixed_dt, double* t_out) {
   if (h->use_graph && n > 0) {
     if (!h->graph || h->graph_n != n || h->graph_cfl != cfl || h->graph_dt != fixed_dt) {
       if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+      // the events the graph's event nodes record exist before the capture
+      if (int rc0 = ensure_stage_events(h, n)) return rc0;
       cudaGraph_t g;
       CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
       h->launches = 0;
-      int rc = enqueue_steps(h, n, cfl, fixed_dt, false);
+      int rc = enqueue_steps(h, n, cfl, fixed_dt, false, true);
       cudaError_t e = cudaStreamEndCapture(h->stream, &g);
       if (rc) return rc;
       if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
@@ -668,10 +676,11 @@ int run_steps(bats_t* h, int n, double cfl, double fixed_dt, double* t_out) {
       h->graph_cfl = cfl;
       h->graph_dt = fixed_dt;
       h->graph_launches = h->launches;
+      h->graph_timed = h->timed_steps;
     }
     CK(h, cudaGraphLaunch(h->graph, h->stream));
     h->launches = h->graph_launches;
-    h->timed_steps = 0;
+    h->timed_steps = h->graph_timed;
   } else {
     int rc = enqueue_steps(h, n, cfl, fixed_dt, true);
     if (rc) return rc;
@@ -690,7 +699,6 @@ int run_steps(bats_t* h, int n, double cfl, double fixed_dt, double* t_out) {
     stage_ms += m;
   }
   if (h->timed_steps > 0 && n > h->timed_steps) stage_ms *= static_cast<double>(n) / h->timed_steps;
-  // replayed graphs carry no per-stage events: the stage time is unmeasured
   h->ms_last[BATS_PHASE_STAGE] = h->timed_steps > 0 ? stage_ms : -1.0;
   h->ms_last[BATS_PHASE_DT] = h->timed_steps > 0 ? ms - stage_ms : -1.0;
   h->ms_last[BATS_PHASE_TOTAL] = ms;

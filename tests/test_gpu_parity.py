@@ -366,7 +366,8 @@ def test_device_tensors_in_and_out(B):
 
 def test_graph_replay_of_many_steps(B):
     """A 60-step graph, replayed twice, equals 120 eager steps (bitwise), and
-    eager runs report per-stage event timings."""
+    both eager runs and graph replays report per-stage event timings (the
+    replay's from the graph's own event nodes)."""
     q = W.orszag_tang()
     with B.Solver(q, precision=B.BATS_MIXED) as s:
         s.set_state(0, q.U0)
@@ -380,6 +381,11 @@ def test_graph_replay_of_many_steps(B):
         s.step(60, 0.8)
         assert np.array_equal(s.get_state(0), ref)
         assert s.launch_count() == 4 * 60
+        g = s.timings()
+        assert g[B.BATS_PHASE_STAGE] > 0 and g[B.BATS_PHASE_TOTAL] >= g[B.BATS_PHASE_STAGE]
+        assert g[B.BATS_PHASE_DT] >= 0
+        # the replay's stage time is that of its 60 steps (half the 120 eager ones, to a factor)
+        assert 0.2 * ms[B.BATS_PHASE_STAGE] < g[B.BATS_PHASE_STAGE] < 1.5 * ms[B.BATS_PHASE_STAGE]
 
 
 def test_batched_state_transfer_equals_per_grid_transfer(B):
