@@ -29,7 +29,10 @@ cudaError_t launch_init_grid_states(GridDev* grids, int ngrids, double inv_gm1, 
 cudaError_t launch_prim_mixed(const double* U, float* Wt, int b0, int nb, float gm1f, cudaStream_t st);
 cudaError_t launch_cfl(bool mixed, const double* U, const float* Wt, const GridDev* grids, const BlockDev* blocks,
                        const PhysDev& ph, int b0, int nb, unsigned long long* smax, cudaStream_t st);
-cudaError_t launch_amr_ghosts(const StageArgs& a, const GhostTask* tasks, int ntasks, cudaStream_t st);
+cudaError_t launch_amr_ghosts(const StageArgs& a, const GhostTask* tasks, const int32_t* gtab, int ntasks,
+                              cudaStream_t st);
+cudaError_t launch_amr_ghost_table(const StageArgs& a, const GhostTask* tasks, int32_t* gtab, int ntasks,
+                                   cudaStream_t st);
 cudaError_t launch_reflux(bool mixed, const StageArgs& a, const RefluxTask* tasks, const int32_t* rblocks, int nrb,
                           cudaStream_t st);
 cudaError_t launch_cfl_dt(bool mixed, const double* U, const float* Wt, const GridDev* grids,
@@ -87,6 +90,7 @@ struct bats {
   // mixed form: ghost slabs of faces at resolution changes, computed ahead of each stage
   std::vector<GhostTask> gtasks_h;
   GhostTask* gtasks_d = nullptr;
+  int32_t* gtab_d = nullptr;   // where each pre-pass thread's sample lies (built once per handle)
   float* gbuf = nullptr;
   // mixed form: tensor maps of W and W1 for the plain stage kernel's tile
   // staging (interior, x, y, z slab boxes), and the staging layout
@@ -402,6 +406,7 @@ void free_all(bats_t* h) {
   cudaFree(h->freg);
   cudaFree(h->gbuf);
   cudaFree(h->gtasks_d);
+  cudaFree(h->gtab_d);
   cudaFree(h->rtasks_d);
   cudaFree(h->rblocks_d);
   cudaFree(h->dt);
@@ -463,7 +468,7 @@ int launch_stage_one(bats_t* h, const StageArgs& a0, bool make_ghosts = true, bo
     a.gbuf = h->gbuf;
     if (make_ghosts) {
       h->launches++;
-      CK(h, launch_amr_ghosts(a, h->gtasks_d, static_cast<int>(h->gtasks_h.size()), h->stream));
+      CK(h, launch_amr_ghosts(a, h->gtasks_d, h->gtab_d, static_cast<int>(h->gtasks_h.size()), h->stream));
     }
   }
   int nitems = (a.nblocks + a.blocks_per_item - 1) / a.blocks_per_item;
@@ -849,7 +854,8 @@ int bats_create(const bats_grid_desc* grids, int n_grids, const bats_physics* ph
   }
   if (h->ph.precision == BATS_MIXED && !h->gtasks_h.empty() &&
       ((rc = dev_alloc(h, &h->gbuf, static_cast<size_t>(h->nslots) * GSLOT)) ||
-       (rc = dev_alloc(h, &h->gtasks_d, h->gtasks_h.size())))) {
+       (rc = dev_alloc(h, &h->gtasks_d, h->gtasks_h.size())) ||
+       (rc = dev_alloc(h, &h->gtab_d, h->gtasks_h.size() * 128)))) {
     free_all(h);
     g_create_error = h->err;
     delete h;
@@ -889,6 +895,9 @@ int bats_create(const bats_grid_desc* grids, int n_grids, const bats_physics* ph
   if (e == cudaSuccess) e = cudaMemsetAsync(h->smax, 0, sizeof(unsigned long long) * h->ngrids, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->U, 0, sizeof(double) * nstate, h->stream);
   if (e == cudaSuccess) e = launch_init_grid_states(h->grids_d, h->ngrids, h->ph.inv_gm1, h->ph.gm1, h->stream);
+  // the static tree: where every ghost-slab sample of the pre-pass lies
+  if (e == cudaSuccess && h->gtab_d)
+    e = launch_amr_ghost_table(base_args(h), h->gtasks_d, h->gtab_d, static_cast<int>(h->gtasks_h.size()), h->stream);
   if (e == cudaSuccess) e = cudaEventCreate(&h->ev0);
   if (e == cudaSuccess) e = cudaEventCreate(&h->ev1);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -1075,7 +1084,7 @@ int bats_debug_fill_ghosts_w(bats_t* h, int grid, double* T, size_t n) {
   for (int k = 0; k < 4; k++) a.tm[k] = h->tmW[k];
   int32_t init[3] = {0, INT_MAX, 0};
   CK(h, cudaMemcpyAsync(h->errw, init, sizeof(init), cudaMemcpyHostToDevice, h->stream));
-  if (h->gbuf) CK(h, launch_amr_ghosts(a, h->gtasks_d, static_cast<int>(h->gtasks_h.size()), h->stream));
+  if (h->gbuf) CK(h, launch_amr_ghosts(a, h->gtasks_d, h->gtab_d, static_cast<int>(h->gtasks_h.size()), h->stream));
   if (staged) CK(h, launch_debug_fill_mx(a, G.block0, G.nb, dst, h->stream));
   else CK(h, launch_debug_fill_w(a, G.block0, G.nb, dst, h->stream));
   if (!dev) CK(h, cudaMemcpyAsync(T, h->staging, need * sizeof(double), cudaMemcpyDeviceToHost, h->stream));

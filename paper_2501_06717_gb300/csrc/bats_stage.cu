@@ -8,43 +8,115 @@
 
 namespace batsk {
 
-// Mixed form: the face-slab ghosts of one face at a resolution change, one CTA
-// of 128 threads per face, one ghost cell per thread, into gbuf[slot][8][128].
-// Coarser neighbour: the coarse samples into a shared table, then every fine
-// ghost cell by the prolongation; finer neighbour: the restriction of each
-// ghost cell's 8 children.
-__global__ void __launch_bounds__(128) k_amr_ghosts(const StageArgs a, const GhostTask* __restrict__ tasks) {
-  __shared__ float tab[PSLOTS * PSTRIDE];
+// Mixed form: the face-slab ghosts of one face at a resolution change.  The
+// tree does not change, so where each ghost's source lies is found once per
+// handle (k_amr_ghost_table) and every stage's pre-pass (k_amr_ghosts) reads
+// it instead of locating the source again.  Per task and thread one entry:
+// the sample of thread k of a COARSER task (k < PSLOTS: coarse sample k of
+// the prolongation) or the ghost cell of thread k of a FINER task (its
+// restriction), encoded as leaf << 9 | cell (a leaf at the sample's level:
+// load its cell), 1 << 30 | leaf << 9 | cell (refined there: restrict the 8
+// cells of `leaf` from corner `cell`), -2 (an inflow face: the fixed state),
+// -3 (no sample) or -1 (anything else: locate as the generic path does).
+constexpr int32_t GT_RESTRICT = 1 << 30, GT_INFLOW = -2, GT_NONE = -3, GT_GENERIC = -1;
+__device__ __forceinline__ int ghost_sample(const GhostTask& T, const BlockDev& B, int tid, int g[3]) {
+  if (B.ftype[T.s] == FACE_COARSER) return tid < PSLOTS && psample(B, T.s, tid, g) ? B.level - 1 : -1;
+  const int d = T.s >> 1, side = T.s & 1;
+  const int layer = tid & 1, ta = (tid >> 1) & 7, tb = tid >> 4;
+  const int c = side ? NC + layer : layer - 2;
+  const int i = d == 0 ? c : ta, j = d == 1 ? c : (d == 0 ? ta : tb), k = d == 2 ? c : tb;
+  g[0] = B.bi * NC + i;
+  g[1] = B.bj * NC + j;
+  g[2] = B.bk * NC + k;
+  return B.level;
+}
+__global__ void __launch_bounds__(128) k_amr_ghost_table(const StageArgs a, const GhostTask* __restrict__ tasks,
+                                                         int32_t* __restrict__ tab) {
   const GhostTask T = tasks[blockIdx.x];
   const BlockDev& B = a.blocks[chki(T.blk, 0, a.nblocks)];
   const GridDev& G = a.grids[B.grid];
   const int tid = threadIdx.x;
-  float w[8];
-  if (B.ftype[T.s] == FACE_COARSER) {
-    if (tid < PSLOTS) {
-      int gc[3];
-      if (psample(B, T.s, tid, gc)) {
-        float ws[8], u[8];
-        sample_w(a.Win, G, a.blocks, a.levmap, B.level - 1, gc, a.ph.gm1f, ws, a.err);
-        cons_from_prim<float>(ws, a.ph.inv_gm1f, u);
-        float* e = tab + tid * PSTRIDE;
-#pragma unroll
-        for (int v = 0; v < NV; v++) e[v] = u[v];
-        e[8] = ws[7];
-        e[9] = ws[1];
-        e[10] = ws[2];
-        e[11] = ws[3];
+  int g[3];
+  const int lev = ghost_sample(T, B, tid, g);
+  int32_t e = GT_NONE;
+  if (lev >= 0) {
+    e = GT_GENERIC;
+    int ll;
+    if (bc_map(G, lev, g)) {
+      e = GT_INFLOW;
+    } else {
+      const int leaf = locate(G, a.levmap, lev, g, ll);
+      if (leaf >= 0 && ll == lev) {
+        const BlockDev& L = a.blocks[leaf];
+        const int li = g[0] - L.bi * NC, lj = g[1] - L.bj * NC, lk = g[2] - L.bk * NC;
+        if (li >= 0 && li < NC && lj >= 0 && lj < NC && lk >= 0 && lk < NC && leaf < (1 << 21))
+          e = leaf << 9 | ((lk * NC + lj) * NC + li);
+      } else if (leaf < 0) {
+        const int f[3] = {2 * g[0], 2 * g[1], 2 * g[2]};
+        const int fl = locate(G, a.levmap, lev + 1, f, ll);
+        if (fl >= 0 && ll == lev + 1) {
+          const BlockDev& L = a.blocks[fl];
+          const int li = f[0] - L.bi * NC, lj = f[1] - L.bj * NC, lk = f[2] - L.bk * NC;
+          if (li >= 0 && li < NC - 1 && lj >= 0 && lj < NC - 1 && lk >= 0 && lk < NC - 1 && fl < (1 << 21))
+            e = GT_RESTRICT | fl << 9 | ((lk * NC + lj) * NC + li);
+        }
       }
+    }
+  }
+  tab[static_cast<int64_t>(blockIdx.x) * 128 + tid] = e;
+}
+// The sample of entry e (the generic point location for GT_GENERIC).
+__device__ __forceinline__ void ghost_sample_w(const StageArgs& a, const GridDev& G, int32_t e, int lev, int g[3],
+                                               float w[8]) {
+  if (e >= 0) {
+    const float* p = a.Win + static_cast<int64_t>((e & (GT_RESTRICT - 1)) >> 9) * (NV * NCELL) + (e & 511);
+    if (e & GT_RESTRICT) {
+      restrict_at(p, a.ph.gm1f, w);
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; v++) w[v] = p[v * NCELL];
+    }
+  } else if (e == GT_INFLOW) {
+#pragma unroll
+    for (int v = 0; v < NV; v++) w[v] = G.Winflow32[v];
+  } else {
+    sample_w(a.Win, G, a.blocks, a.levmap, lev, g, a.ph.gm1f, w, a.err);
+  }
+}
+
+// One CTA of 128 threads per face, one ghost cell per thread, into
+// gbuf[slot].  Coarser neighbour: the coarse samples into a shared table,
+// then every fine ghost cell by the prolongation; finer neighbour: the
+// restriction of each ghost cell's 8 children.
+__global__ void __launch_bounds__(128) k_amr_ghosts(const StageArgs a, const GhostTask* __restrict__ tasks,
+                                                    const int32_t* __restrict__ gtab) {
+  __shared__ float tab[PSLOTS * PSTRIDE];
+  const GhostTask T = tasks[blockIdx.x];
+  const int tid = threadIdx.x;
+  const int32_t ent = gtab[static_cast<int64_t>(blockIdx.x) * 128 + tid];
+  const BlockDev& B = a.blocks[chki(T.blk, 0, a.nblocks)];
+  const GridDev& G = a.grids[B.grid];
+  float w[8];
+  int g[3];
+  if (B.ftype[T.s] == FACE_COARSER) {
+    if (ent != GT_NONE) {
+      const int lev = ghost_sample(T, B, tid, g);
+      float ws[8], u[8];
+      ghost_sample_w(a, G, ent, lev, g, ws);
+      cons_from_prim<float>(ws, a.ph.inv_gm1f, u);
+      float* e = tab + chki(tid, 0, PSLOTS) * PSTRIDE;
+#pragma unroll
+      for (int v = 0; v < NV; v++) e[v] = u[v];
+      e[8] = ws[7];
+      e[9] = ws[1];
+      e[10] = ws[2];
+      e[11] = ws[3];
     }
     __syncthreads();
     prolong_child_w(tab, T.s, tid, a.ph.gm1f, w);
   } else {
-    const int d = T.s >> 1, side = T.s & 1;
-    const int layer = tid & 1, ta = (tid >> 1) & 7, tb = tid >> 4;
-    const int c = side ? NC + layer : layer - 2;
-    const int i = d == 0 ? c : ta, j = d == 1 ? c : (d == 0 ? ta : tb), k = d == 2 ? c : tb;
-    int g[3] = {B.bi * NC + i, B.bj * NC + j, B.bk * NC + k};
-    sample_w(a.Win, G, a.blocks, a.levmap, B.level, g, a.ph.gm1f, w, a.err);
+    const int lev = ghost_sample(T, B, tid, g);
+    ghost_sample_w(a, G, ent, lev, g, w);
   }
   // slot layout: the generic tile's slab order [8][128] (layer fastest), or
   // the staged tile's slab layout of this face's axis
@@ -537,9 +609,16 @@ cudaError_t launch_cfl_dt(bool mixed, const double* U, const float* Wt, const Gr
   else k_cfl<false><<<nb, NCELL, 0, st>>>(U, Wt, grids, blocks, ph, b0, smax, dtc, cfl);
   return cudaGetLastError();
 }
-cudaError_t launch_amr_ghosts(const StageArgs& a, const GhostTask* tasks, int ntasks, cudaStream_t st) {
+cudaError_t launch_amr_ghost_table(const StageArgs& a, const GhostTask* tasks, int32_t* gtab, int ntasks,
+                                   cudaStream_t st) {
   if (ntasks <= 0) return cudaSuccess;
-  k_amr_ghosts<<<ntasks, 128, 0, st>>>(a, tasks);
+  k_amr_ghost_table<<<ntasks, 128, 0, st>>>(a, tasks, gtab);
+  return cudaGetLastError();
+}
+cudaError_t launch_amr_ghosts(const StageArgs& a, const GhostTask* tasks, const int32_t* gtab, int ntasks,
+                              cudaStream_t st) {
+  if (ntasks <= 0) return cudaSuccess;
+  k_amr_ghosts<<<ntasks, 128, 0, st>>>(a, tasks, gtab);
   return cudaGetLastError();
 }
 cudaError_t launch_reflux(bool mixed, const StageArgs& a, const RefluxTask* tasks, const int32_t* rblocks, int nrb,

@@ -651,22 +651,11 @@ __device__ __forceinline__ float sum8(const float c[8]) {
 // state is p~ = mean p_i + (gamma - 1) [mean(rho_i |u_i - u~|^2) + mean(|B_i - B~|^2)] / 2
 // (the kinetic and magnetic energies of the mean fall short of the mean
 // energies by those two variances), a sum of non-negative terms.
-static __device__ __noinline__ void restrict_w(const float* Wt, const GridDev& G, const BlockDev* blocks,
-                                        const int32_t* levmap, int lev, const int g[3], float gm1f, float w[8],
-                                        int32_t* err) {
-  const int f[3] = {2 * g[0], 2 * g[1], 2 * g[2]};
-  int ll;
-  const int leaf = locate(G, levmap, lev + 1, f, ll);
-  if (leaf < 0 || ll != lev + 1) {
-    atomicOr(err, ERR_BOUNDS);
-#pragma unroll
-    for (int v = 0; v < NV; v++) w[v] = 0.f;
-    return;
-  }
-  const BlockDev& B = blocks[leaf];
-  const int li = chki(f[0] - B.bi * NC, 0, NC - 1), lj = chki(f[1] - B.bj * NC, 0, NC - 1),
-            lk = chki(f[2] - B.bk * NC, 0, NC - 1);
-  const float* p = Wt + static_cast<int64_t>(leaf) * (NV * NCELL) + (lk * NC + lj) * NC + li;
+// The restriction of the 8 fine cells whose corner cell (lowest i, j, k) is
+// at p (a leaf's FP32 primitives, variable stride NCELL) to one coarse cell,
+// as primitives: density and field the means, velocity the mass-weighted
+// mean, pressure the mean plus the velocity and field variances.
+static __device__ __noinline__ void restrict_at(const float* p, float gm1f, float w[8]) {
   const int off[8] = {0, 1, NC, NC + 1, NC * NC, NC * NC + 1, NC * NC + NC, NC * NC + NC + 1};
   float rho[8], c[8];
 #pragma unroll
@@ -714,6 +703,25 @@ static __device__ __noinline__ void restrict_w(const float* Wt, const GridDev& G
   w[5] = bt[1];
   w[6] = bt[2];
   w[7] = 0.125f * sum8(c) + gm1f * (0.0625f * var);
+}
+
+static __device__ __noinline__ void restrict_w(const float* Wt, const GridDev& G, const BlockDev* blocks,
+                                        const int32_t* levmap, int lev, const int g[3], float gm1f, float w[8],
+                                        int32_t* err) {
+  const int f[3] = {2 * g[0], 2 * g[1], 2 * g[2]};
+  int ll;
+  const int leaf = locate(G, levmap, lev + 1, f, ll);
+  if (leaf < 0 || ll != lev + 1) {
+    atomicOr(err, ERR_BOUNDS);
+#pragma unroll
+    for (int v = 0; v < NV; v++) w[v] = 0.f;
+    return;
+  }
+  const BlockDev& B = blocks[leaf];
+  const int li = chki(f[0] - B.bi * NC, 0, NC - 1), lj = chki(f[1] - B.bj * NC, 0, NC - 1),
+            lk = chki(f[2] - B.bk * NC, 0, NC - 1);
+  const float* p = Wt + static_cast<int64_t>(leaf) * (NV * NCELL) + (lk * NC + lj) * NC + li;
+  restrict_at(p, gm1f, w);
 }
 
 // Primitives of the cell g (global, level lev): boundary mapping, then copy
