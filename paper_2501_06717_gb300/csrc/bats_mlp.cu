@@ -3,12 +3,14 @@
 // weights and activations, FP32 accumulation.
 //
 //  * k_mlp_infer: Y = MLP(X) for face feature rows X (BF16, 48 columns: the
-//    40 features and 8 zeros) on the 5th-generation tensor cores: per CTA a
-//    persistent loop over 128-row tiles; each layer is a tcgen05.mma chain
-//    (M = 128, K = 16 per instruction) from shared-memory operands into a
-//    tensor-memory accumulator, which eight warps read back (tcgen05.ld;
-//    two warps per row, 32 columns each), add the bias to, pass through GELU
-//    and store as the next layer's BF16 operand.
+//    40 features and 8 zeros) on the 5th-generation tensor cores: one
+//    persistent CTA per SM with four streams of 128-row tiles; each layer is
+//    a tcgen05.mma chain (M = 128, K = 16 per instruction) with the A operand
+//    (the inputs, then the activations) in tensor memory and the weights in
+//    shared memory, into a tensor-memory accumulator that the stream's
+//    threads read back (tcgen05.ld, one row per thread) and write over with
+//    the next layer's BF16 operand (tcgen05.st); biases folded into the
+//    products.
 //  * k_mlp_train_tc, k_mlp_grad_reduce: the mean-squared-error loss and its
 //    gradient for a batch, every product on tcgen05 (the weight gradients
 //    with the samples as K), per-CTA partial sums added in a fixed order.
