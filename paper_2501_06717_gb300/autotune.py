@@ -20,6 +20,7 @@ DEFAULT_CANDIDATES = [
     (0, 2, 0),
     (0, 4, 0),
     (0, 8, 0),
+    (0, 16, 0),
     (1, 1, 0),
     (1, 2, 0),
     (1, 4, 0),
