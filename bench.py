@@ -48,7 +48,7 @@ FP64_FLOPS_PER_CELL_UPDATE = 3404
 NCU_TRAFFIC = {
     # precision: (DRAM bytes per cell per launch, mean of the two stages, sha256 of the stage
     # kernel's sources -- bats_stage_kernel.h then bats_stage.cu -- at capture)
-    "mixed": (124.1, "66622765da25714d84c1ef95e1f6812e0f93cb17a8f0e8f1b9973d42cee733b0"),
+    "mixed": (124.1, "89f0bafa6f8eb8625294542708e29df3b6b08df41b618cbe746730ac0abf19e3"),
 }
 
 
