@@ -367,6 +367,13 @@ __device__ __forceinline__ double minmod_d(double a, double b) {
   long long r = ma < mb ? ia : ib;
   return same ? __longlong_as_double(r) : 0.0;
 }
+// The FP64 limiter's minmod by the same integer operations: the same value as
+// the comparison form for every finite argument, issued on the integer pipe
+// instead of the FP64 pipe (which bounds the FP64 form).
+template <>
+__device__ __forceinline__ double minmod_<double>(double a, double b) {
+  return minmod_d(a, b);
+}
 // Validity tests on bit patterns: finite, and finite and > 0.
 __device__ __forceinline__ bool finite_d(double x) {
   return (static_cast<unsigned>(__double2hiint(x)) & 0x7ff00000u) != 0x7ff00000u;
