@@ -48,7 +48,7 @@ FP64_FLOPS_PER_CELL_UPDATE = 3404
 NCU_TRAFFIC = {
     # precision: (DRAM bytes per cell per launch, mean of the two stages, sha256 of the stage
     # kernel's sources -- bats_stage_kernel.h then bats_stage.cu -- at capture)
-    "mixed": (124.1, "89f0bafa6f8eb8625294542708e29df3b6b08df41b618cbe746730ac0abf19e3"),
+    "mixed": (128.4, "90867d9f95dbf4e22ecec163994cb52b96c6ed3282052eeaeaee88e3465e496d"),
 }
 
 
