@@ -1272,6 +1272,17 @@ __device__ __forceinline__ void mx_stage_tile(const StageArgs& a, const BlockDev
 // down, a face's two sides come as (right, left): the dissipation's sign
 // flips with the lane's direction.  Writes twice the fluxes (un-rotated
 // components) and the sum of the two sides' normal B1 into sF[D][9][576].
+// The mixed plain kernel keeps each direction's face values in the face frame
+// (normal component first, then the next two axes cyclically), so that its
+// one runtime copy of the face code stores at fixed offsets: the slot of
+// variable v (x, y, z order) among the values of direction d.
+__host__ __device__ constexpr int frot(int v, int d) {
+  return (v >= 1 && v <= 6) ? ((v - 1) / 3) * 3 + 1 + (((v - 1) % 3 - d + 3) % 3) : v;
+}
+static_assert(frot(1, 0) == 1 && frot(2, 1) == 1 && frot(3, 2) == 1 && frot(1, 1) == 3 && frot(1, 2) == 2 &&
+                  frot(4, 1) == 6 && frot(6, 2) == 4 && frot(7, 1) == 7 && frot(8, 2) == 8,
+              "face-frame slots");
+
 template <int LIM, bool HAS_B0, int FLX>
 __device__ __forceinline__ void faces_mx(const int D, const StageArgs& a, const BlockDev& B, const float* sT, float* sF,
                                          int fline, int fhalf, float gamma, float inv_gm1, int gb0, int gb1, int gb2,
@@ -1344,15 +1355,9 @@ __device__ __forceinline__ void faces_mx(const int D, const StageArgs& a, const 
     face_flux2<HAS_B0, FLX>(W2, B0r, gamma, inv_gm1, dsgn, Fr2);
     const float bn2 = W2[4].x + W2[4].y;
     if (k == 4 && h1) continue;  // face 4 is half 0's
-    float* const o = fo + k * fstep;
-    o[0] = Fr2[0];
-    o[(1 + D) * NFACE] = Fr2[1];
-    o[(1 + D1) * NFACE] = Fr2[2];
-    o[(1 + D2) * NFACE] = Fr2[3];
-    o[(4 + D) * NFACE] = Fr2[4];
-    o[(4 + D1) * NFACE] = Fr2[5];
-    o[(4 + D2) * NFACE] = Fr2[6];
-    o[7 * NFACE] = Fr2[7];
+    float* const o = fo + k * fstep;  // in the face frame (frot)
+#pragma unroll
+    for (int v = 0; v < NV; v++) o[v * NFACE] = Fr2[v];
     o[8 * NFACE] = bn2;
     // refluxing: the block-face fluxes (face 0: half 0 step 0; face 8: half 1 step 0)
     if (k == 0 && a.freg) {
@@ -1408,9 +1413,9 @@ __device__ __forceinline__ float cells_mx_pair(const StageArgs& a, const GridDev
   float2 t[9];
 #pragma unroll
   for (int v = 0; v < 9; v++) {
-    const float* px = Fx + v * NFACE + tx;
-    const float* py = Fy + v * NFACE + ty;
-    const float* pz = Fz + v * NFACE + tz;
+    const float* px = Fx + frot(v, 0) * NFACE + tx;  // face-frame slots (the x frame is the identity)
+    const float* py = Fy + frot(v, 1) * NFACE + ty;
+    const float* pz = Fz + frot(v, 2) * NFACE + tz;
     const float2 x0 = make_float2(px[0], px[DX]), x1 = make_float2(px[1], px[DX + 1]);
     const float2 y0 = make_float2(py[0], py[DX]), y1 = make_float2(py[1], py[DX + 1]);
     const float2 z0 = make_float2(pz[0], pz[DZ]), z1 = make_float2(pz[1], pz[DZ + 1]);
@@ -2182,9 +2187,11 @@ __global__ void __launch_bounds__(StageCfg<MIXED>::THREADS, (MIXED && !LRN) ? 2 
           R res[8];
 #pragma unroll
           for (int v = 0; v < NV; v++) {
-            R r = -((Fx[v * NFACE + tx + 1] - Fx[v * NFACE + tx]) * fidx0);
-            r = r - (Fy[v * NFACE + ty + 1] - Fy[v * NFACE + ty]) * fidx1;
-            r = r - (Fz[v * NFACE + tz + 1] - Fz[v * NFACE + tz]) * fidx2;
+            // the mixed plain kernel's face values are in the face frame (frot)
+            const int vx = MX ? frot(v, 0) : v, vy = MX ? frot(v, 1) : v, vz = MX ? frot(v, 2) : v;
+            R r = -((Fx[vx * NFACE + tx + 1] - Fx[vx * NFACE + tx]) * fidx0);
+            r = r - (Fy[vy * NFACE + ty + 1] - Fy[vy * NFACE + ty]) * fidx1;
+            r = r - (Fz[vz * NFACE + tz + 1] - Fz[vz * NFACE + tz]) * fidx2;
             res[v] = r;
           }
           const R divb = ((Fx[8 * NFACE + tx + 1] - Fx[8 * NFACE + tx]) * fidx0 +
